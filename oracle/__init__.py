@@ -1,0 +1,7 @@
+"""Independent FP64 CPU oracle for the PP-WCNS-IS right-hand side.
+
+TEST INFRASTRUCTURE: only the test-suite, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import this package.  It shares no code with
+the CUDA library.
+"""
+from .oracle import Oracle, OracleStats, build_oracle  # noqa: F401

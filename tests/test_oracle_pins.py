@@ -1,0 +1,536 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+Every test here checks the oracle (oracle/) against something other than
+itself: values printed in the paper, closed forms from other equations of
+the paper, Taylor expansions printed in Appendix B, invariants and textbook
+properties.  No GPU is needed.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from oracle.oracle import hcs_recon, wcnsis_left
+from oracle import exact_riemann as ER
+from paper_2102_05287_gb300 import problems as P
+from tests.conftest import load_golden
+
+EOS = P.WORKLOAD_EOS
+PSI = 256.0 / 175.0
+
+
+def make(n, bcs=None, scheme="pp-wcns-is", eos=EOS, **kw):
+    ndim = len(n)
+    bcs = bcs or tuple(("periodic", "periodic") for _ in range(ndim))
+    return Oracle(n, (0.0,) * ndim, (1.0,) * ndim, bcs, scheme=scheme, **eos, **kw)
+
+
+def rand_state(rng, ndim, a1=None, p=None):
+    a1 = rng.uniform(1e-6, 1 - 1e-6) if a1 is None else a1
+    rho_w, rho_a = rng.uniform(900, 1100), rng.uniform(0.5, 100)
+    vel = list(rng.uniform(-300, 300, size=ndim))
+    p = rng.uniform(-1e7, 2e9) if p is None else p
+    W = P.conservative(EOS, np.array(a1 * rho_w), np.array((1 - a1) * rho_a), [np.array(v) for v in vel],
+                       np.array(p), np.array(a1))
+    return W.reshape(-1)
+
+
+# ---------------------------------------------------------------------------
+# Section 6.1 table: the strongest pin (both columns, printed values).
+# ---------------------------------------------------------------------------
+def _e1_error(N, scheme):
+    pr = P.advection_2d(N)
+    o = Oracle(pr.n, pr.lo, pr.hi, pr.bcs, scheme=scheme, **pr.eos)
+    W, t, steps = o.advance_to(pr.W, 0.0, pr.t_end, dt_fixed=pr.dt_fixed)
+    assert abs(t - pr.t_end) < 1e-18
+    return math.sqrt(np.mean((W[-1] - pr.extra["exact"](t)) ** 2)), o.stats.as_dict()
+
+
+@pytest.mark.parametrize("N", [8, 16, 32, 64])
+def test_e1_table_hllc_column(N):
+    table = {int(r[0]): r[1] for r in load_golden("e1_advection_l2.txt")}
+    err, _ = _e1_error(N, "hllc1")
+    # printed to 4 significant digits
+    assert abs(err - table[N]) <= 6e-4 * table[N], (err, table[N])
+
+
+@pytest.mark.parametrize("N", [8, 16, 32])
+def test_e1_table_pp_wcns_is_column(N):
+    table = {int(r[0]): r[2] for r in load_golden("e1_advection_l2.txt")}
+    err, st = _e1_error(N, "pp-wcns-is")
+    assert abs(err - table[N]) <= 1e-3 * table[N], (err, table[N])
+    # smooth data: the limiters never act
+    assert st["interp_limited"] == 0 and st["flux_limited"] == 0
+    assert st["interp_hard"] == 0 and st["flux_hard"] == 0
+
+
+# ---------------------------------------------------------------------------
+# Section 2: EOS and mixture rules.
+# ---------------------------------------------------------------------------
+def test_eos_pure_phase_limits():
+    o = make((8,))
+    rng = np.random.default_rng(1)
+    for a1, g, pi in ((1.0, EOS["gamma_l"], EOS["pinf_l"]), (0.0, EOS["gamma_g"], 0.0)):
+        for _ in range(5):
+            W = rand_state(rng, 1, a1=a1, p=rng.uniform(1e5, 1e9))
+            th = o.thermo(W)
+            rho = W[0] + W[1]
+            assert th["gamma_bar"] == pytest.approx(g, rel=1e-14)
+            assert th["pinf_bar"] == pytest.approx(pi, rel=1e-14, abs=1e-6)
+            # textbook stiffened-gas sound speed
+            assert th["c"] ** 2 == pytest.approx(g * (th["p"] + pi) / rho, rel=1e-12)
+
+
+def test_eos_phasic_energy_split_and_sound_speed_forms():
+    """rho e equals sum_k alpha_k (p + g_k pinf_k)/(g_k - 1) at the common
+    pressure (phase EOS times alpha, summed), and the two printed forms of
+    rho c^2 agree."""
+    o = make((8,), eos=EOS)
+    rng = np.random.default_rng(2)
+    g1, p1, g2 = EOS["gamma_l"], EOS["pinf_l"], EOS["gamma_g"]
+    for ndim in (1, 2, 3):
+        o = make((8,) * ndim)
+        for _ in range(20):
+            W = rand_state(rng, ndim)
+            th = o.thermo(W)
+            a1 = W[-1]
+            rho = W[0] + W[1]
+            rhoe = W[-2] - 0.5 * sum(W[2 + j] ** 2 for j in range(ndim)) / rho
+            split = a1 * (th["p"] + g1 * p1) / (g1 - 1) + (1 - a1) * th["p"] / (g2 - 1)
+            assert split == pytest.approx(rhoe, rel=1e-12)
+            gb, pb = th["gamma_bar"], th["pinf_bar"]
+            assert th["rho_c2"] == pytest.approx(gb * (gb - 1) * (rhoe - pb), rel=1e-10)
+            assert th["rho_ct2"] == pytest.approx(rhoe - pb, rel=1e-12)
+
+
+def test_prim_cons_round_trip():
+    rng = np.random.default_rng(3)
+    for ndim in (1, 2, 3):
+        o = make((8,) * ndim)
+        for _ in range(20):
+            W = rand_state(rng, ndim)
+            V = o.cons_to_prim(W)
+            W2 = o.prim_to_cons(V)
+            np.testing.assert_allclose(W2, W, rtol=1e-12, atol=1e-9)
+
+
+def test_lemma1_concavity_of_rho_ct2():
+    """Lemma 1: rho e - pbar is concave when the ideal gas has the smaller
+    gamma.  Random Jensen check on admissible pairs."""
+    o = make((8, 8))
+    rng = np.random.default_rng(4)
+    for _ in range(300):
+        A = rand_state(rng, 2)
+        B = rand_state(rng, 2)
+        lam = rng.uniform()
+        M = lam * A + (1 - lam) * B
+        fA, fB, fM = (o.thermo(X)["rho_ct2"] for X in (A, B, M))
+        assert fM >= lam * fA + (1 - lam) * fB - 1e-9 * max(abs(fA), abs(fB))
+
+
+# ---------------------------------------------------------------------------
+# Appendix A: characteristic decomposition.
+# ---------------------------------------------------------------------------
+def _numerical_primitive_jacobian(o, d, W):
+    """A(V) of the quasi-linear primitive system, by central differences of
+    the physical flux composed with V -> W; the alpha row is u_d e_alpha."""
+    nf = o.nf
+    V = o.cons_to_prim(W)
+    M = np.zeros((nf, nf))
+    JF = np.zeros((nf, nf))
+    for r in range(nf):
+        h = 1e-6 * max(abs(V[r]), 1e-3)
+        Vp, Vm = V.copy(), V.copy()
+        Vp[r] += h
+        Vm[r] -= h
+        Wp, Wm = o.prim_to_cons(Vp), o.prim_to_cons(Vm)
+        M[:, r] = (Wp - Wm) / (2 * h)
+        JF[:, r] = (o.phys_flux(d, Wp) - o.phys_flux(d, Wm)) / (2 * h)
+    B = JF.copy()
+    B[nf - 1, :] = 0.0
+    B[nf - 1, nf - 1] = V[2 + d]
+    # the alpha row of (dF/dV) also carries alpha1 u: replace it by u e_alpha
+    return np.linalg.solve(M, B), V
+
+
+@pytest.mark.parametrize("ndim", [1, 2, 3])
+def test_characteristic_matrices_diagonalise_the_jacobian(ndim):
+    o = make((8,) * ndim)
+    rng = np.random.default_rng(5 + ndim)
+    for d in range(ndim):
+        for _ in range(5):
+            W = rand_state(rng, ndim, p=rng.uniform(1e5, 1e9))
+            R, Ri = o.char_matrices(d, W, W)
+            np.testing.assert_allclose(R @ Ri, np.eye(o.nf), atol=1e-12)
+            A, V = _numerical_primitive_jacobian(o, d, W)
+            c = o.thermo(W)["c"]
+            u = V[2 + d]
+            lam = np.full(o.nf, u)
+            lam[0], lam[-1] = u - c, u + c
+            A_ana = R @ np.diag(lam) @ Ri
+            scale = np.abs(V) + 1e-3
+            As = A / scale[:, None] * scale[None, :]
+            Aas = A_ana / scale[:, None] * scale[None, :]
+            np.testing.assert_allclose(As, Aas, atol=2e-5 * np.abs(Aas).max())
+
+
+# ---------------------------------------------------------------------------
+# Section 4.3 and Appendix B: IS interpolation.
+# ---------------------------------------------------------------------------
+D_LIN = np.array([15 / 32, 5 / 32, 5 / 16, 1 / 16])
+
+
+def test_is_weights_linear_on_quadratics():
+    """tau5 vanishes on quadratics, so omega = d and the value is the exact
+    midpoint value."""
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        a, b, c = rng.normal(size=3)
+        x = np.arange(-2, 3, dtype=float)
+        u = a + b * x + c * x * x
+        r = wcnsis_left(u)
+        np.testing.assert_allclose(r["omega"], D_LIN, rtol=1e-12)
+        assert r["value"] == pytest.approx(a + b * 0.5 + c * 0.25, rel=1e-12, abs=1e-12)
+
+
+def test_linear_weights_give_printed_s5_and_quartic_exactness():
+    rng = np.random.default_rng(8)
+    for _ in range(20):
+        u = rng.normal(size=5)
+        r = wcnsis_left(u, eps=1e300)  # tau5/(beta+eps) -> 0: omega = d
+        s5 = (3 * u[0] - 20 * u[1] + 90 * u[2] + 60 * u[3] - 5 * u[4]) / 128
+        assert r["value"] == pytest.approx(s5, rel=1e-13, abs=1e-13)
+    co = rng.normal(size=5)
+    x = np.arange(-2, 3, dtype=float)
+    u = np.polyval(co, x)
+    r = wcnsis_left(u, eps=1e300)
+    assert r["value"] == pytest.approx(np.polyval(co, 0.5), rel=1e-12)
+
+
+def _taylor(dx, x0=0.3):
+    d = [math.sin(x0), math.cos(x0), -math.sin(x0), -math.cos(x0), math.sin(x0)]
+    u = np.sin(x0 + dx * np.arange(-2, 3))
+    return d, u
+
+
+def test_smoothness_indicators_match_appendix_b_expansions():
+    """Appendix B prints the Taylor series of beta0, beta1, beta01, beta2,
+    beta3 (to dx^5) and tau5 (to dx^6); the remainders must shrink at the
+    stated next order."""
+    def series(d, dx):
+        u1, u2, u3, u4 = d[1], d[2], d[3], d[4]
+        b0 = u1**2 * dx**2 + u1 * u2 * dx**3 + (u1 * u3 / 3 + u2**2 / 4) * dx**4 + (u1 * u4 / 12 + u2 * u3 / 6) * dx**5
+        b1 = u1**2 * dx**2 - u1 * u2 * dx**3 + (u1 * u3 / 3 + u2**2 / 4) * dx**4 + (-u1 * u4 / 12 - u2 * u3 / 6) * dx**5
+        b01 = u1**2 * dx**2 + (u1 * u3 / 3 + 13 * u2**2 / 12) * dx**4
+        b2 = u1**2 * dx**2 + (-2 * u1 * u3 / 3 + 13 * u2**2 / 12) * dx**4 + (-u1 * u4 / 2 + 13 * u2 * u3 / 6) * dx**5
+        b3 = u1**2 * dx**2 + (-2 * u1 * u3 / 3 + 13 * u2**2 / 12) * dx**4 + (u1 * u4 / 2 - 13 * u2 * u3 / 6) * dx**5
+        t5 = u3**2 * dx**6
+        return np.array([b0, b1, b01, b2, b3]), t5
+
+    errs, terrs = [], []
+    for dx in (0.02, 0.01):
+        d, u = _taylor(dx)
+        r = wcnsis_left(u)
+        b, t5 = series(d, dx)
+        errs.append(np.abs(r["beta"] - b))
+        terrs.append(abs(r["tau5"] - t5))
+    rate = np.log2(errs[0] / errs[1])
+    assert np.all(rate > 5.6), rate  # remainders are O(dx^6)
+    assert np.log2(terrs[0] / terrs[1]) > 7.5  # O(dx^8)
+
+
+def test_is_weights_approach_linear_at_fourth_order():
+    devs = []
+    for dx in (0.04, 0.02, 0.01):
+        _, u = _taylor(dx)
+        devs.append(np.abs(wcnsis_left(u)["omega"] - D_LIN).max())
+    rates = np.log2(np.array(devs[:-1]) / np.array(devs[1:]))
+    assert np.all(rates > 3.5), rates
+
+
+def test_is_weights_avoid_a_discontinuity():
+    # jump between u_i and u_{i+1}: only S1 and S3 lie on the smooth side
+    r = wcnsis_left(np.array([0.0, 0.0, 0.0, 1.0, 1.0]))
+    assert r["omega"][1] + r["omega"][3] > 1 - 1e-12
+    assert abs(r["value"]) < 1e-12
+    # jump between u_{i-1} and u_i: S0 and S2 lie on the smooth side
+    r = wcnsis_left(np.array([0.0, 0.0, 1.0, 1.0, 1.0]))
+    assert r["omega"][0] + r["omega"][2] > 1 - 1e-12
+    assert r["value"] == pytest.approx(1.0, abs=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Section 4.1: HCS flux-difference form.
+# ---------------------------------------------------------------------------
+def test_hcs_flux_difference_equals_printed_derivative_form():
+    rng = np.random.default_rng(9)
+    for _ in range(50):
+        g = rng.normal(size=7)      # G_{i-3} .. G_{i+3}
+        gt = rng.normal(size=2)     # Gt_{i-1/2}, Gt_{i+1/2}
+        right = hcs_recon(gt[1], g[1:7])
+        left = hcs_recon(gt[0], g[0:6])
+        deriv = (PSI * (gt[1] - gt[0]) - (175 * PSI - 192) / 256 * (g[4] - g[2])
+                 + (35 * PSI - 48) / 320 * (g[5] - g[1]) - (45 * PSI - 64) / 3840 * (g[6] - g[0]))
+        assert right - left == pytest.approx(deriv, rel=1e-12, abs=1e-12)
+    assert hcs_recon(1.0, np.ones(6)) == pytest.approx(1.0, rel=1e-15)
+
+
+def test_hcs_is_eighth_order_with_exact_midpoint_values():
+    errs = []
+    x0 = 0.37
+    for dx in (0.2, 0.1):
+        xs = x0 + dx * np.arange(-3, 4)
+        g = np.sin(xs)
+        gr = hcs_recon(math.sin(x0 + 0.5 * dx), g[1:7])
+        gl = hcs_recon(math.sin(x0 - 0.5 * dx), g[0:6])
+        errs.append(abs((gr - gl) / dx - math.cos(x0)))
+    assert math.log2(errs[0] / errs[1]) > 7.5
+
+
+# ---------------------------------------------------------------------------
+# Section 3: HLLC.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("ndim", [1, 2, 3])
+def test_hllc_consistency(ndim):
+    o = make((8,) * ndim)
+    rng = np.random.default_rng(10 + ndim)
+    for d in range(ndim):
+        for _ in range(10):
+            W = rand_state(rng, ndim)
+            G, us = o.hllc(d, W, W)
+            np.testing.assert_allclose(G, o.phys_flux(d, W), rtol=1e-12, atol=1e-6)
+            assert us == pytest.approx(W[2 + d] / (W[0] + W[1]), rel=1e-12, abs=1e-12)
+
+
+def test_hllc_resolves_an_isolated_contact():
+    """Equal p and u, different composition: HLLC returns the upwind flux."""
+    o = make((8,))
+    for u in (37.0, -21.0):
+        WL = P.conservative(EOS, np.array(999.0 * 0.9), np.array(0.1 * 3.0), [np.array(u)], np.array(2e5),
+                            np.array(0.9)).ravel()
+        WR = P.conservative(EOS, np.array(1001.0 * 1e-6), np.array(40.0), [np.array(u)], np.array(2e5),
+                            np.array(1e-6)).ravel()
+        G, us = o.hllc(0, WL, WR)
+        up = WL if u > 0 else WR
+        np.testing.assert_allclose(G, o.phys_flux(0, up), rtol=1e-9, atol=1e-6 * abs(G).max())
+        assert us == pytest.approx(u, rel=1e-9)
+
+
+def test_hllc_star_states_admissible():
+    """Section 3.3: with Einfeldt speeds the star states stay in G and
+    s_L < s* < s_R, for random admissible pairs with large jumps."""
+    rng = np.random.default_rng(12)
+    for ndim in (1, 2):
+        o = make((8,) * ndim)
+        for _ in range(400):
+            WL, WR = rand_state(rng, ndim), rand_state(rng, ndim)
+            for d in range(ndim):
+                s3, WsL, WsR = o.hllc_star(d, WL, WR)
+                thL, thR = o.thermo(WL), o.thermo(WR)
+                uL, uR = WL[2 + d] / (WL[0] + WL[1]), WR[2 + d] / (WR[0] + WR[1])
+                assert s3[0] < s3[1] < s3[2]
+                assert s3[0] <= uL - thL["c"] + 1e-9 and s3[2] >= uR + thR["c"] - 1e-9
+                for Ws in (WsL, WsR):
+                    assert Ws[0] >= 0 and Ws[1] >= 0
+                    assert o.thermo(Ws)["rho_ct2"] > 0
+
+
+# ---------------------------------------------------------------------------
+# Section 5: limiters.
+# ---------------------------------------------------------------------------
+def test_interp_limiter_inactive_on_admissible_states():
+    o = make((8,))
+    rng = np.random.default_rng(13)
+    for _ in range(50):
+        Wn, Wt = rand_state(rng, 1), rand_state(rng, 1)
+        out, lim, hard = o.interp_limit(Wn, Wt)
+        assert not lim and not hard
+        np.testing.assert_array_equal(out, Wt)
+
+
+def _collinear(Wn, Wt, out):
+    d1, d2 = Wt - Wn, out - Wn
+    th = np.dot(d1, d2) / np.dot(d1, d1)
+    assert -1e-12 <= th <= 1 + 1e-12
+    np.testing.assert_allclose(d2, th * d1, rtol=1e-9, atol=1e-9 * np.abs(Wn).max())
+
+
+@pytest.mark.parametrize("case", ["neg_a2r2", "alpha_above_one", "neg_rho_ct2"])
+def test_interp_limiter_restores_bounds(case):
+    o = make((8,))
+    Wn = rand_state(np.random.default_rng(14), 1, a1=0.3, p=1e6)
+    Wt = Wn.copy()
+    if case == "neg_a2r2":
+        Wt[1] = -0.5 * Wn[1]
+    elif case == "alpha_above_one":
+        Wt[-1] = 1.02
+    else:
+        Wt[3] = Wn[3] - 3.0 * o.thermo(Wn)["rho_ct2"]
+    out, lim, hard = o.interp_limit(Wn, Wt)
+    assert lim and not hard
+    # bounds hold up to the round-off of the theta solve, which cancels
+    # operands of size |W|; the hard-switch tolerances sit below for this
+    ra = 1e-13 * np.abs(np.concatenate([Wn, Wt])).max()
+    assert out[0] >= 1e-10 - ra and out[1] >= 1e-10 - ra
+    assert 1e-10 - 1e-15 <= out[-1] <= 1 - 1e-10 + 1e-15
+    assert o.thermo(out)["rho_ct2"] >= 1e-8 - 1e-13 * abs(Wn[3])
+    _collinear(Wn, Wt, out)
+
+
+def test_flux_limiter_blends_toward_hllc_until_half_states_are_admissible():
+    o = make((8,))
+    rng = np.random.default_rng(15)
+    Wi = rand_state(rng, 1, a1=0.5, p=1e6)
+    Wi1 = rand_state(rng, 1, a1=0.5, p=1e6)
+    GH, uH = o.hllc(0, Wi, Wi1)
+    GHm, GHp = GH.copy(), GH.copy()
+    GHm[-1] -= Wi[-1] * uH
+    GHp[-1] -= Wi1[-1] * uH
+    lam = 0.2 / 1500.0
+    # a high-order flux that empties cell i of phase 2 in the half step
+    Gm, Gp = GHm.copy(), GHp.copy()
+    bump = 5.0 * Wi[1] / (2 * lam)
+    Gm[1] += bump
+    Gp[1] += bump
+    gm, gp, lim, hard = o.flux_limit(0, Wi, Wi1, GHm, GHp, lam, Gm, Gp)
+    assert lim and not hard
+    Fi = o.phys_flux(0, Wi)
+    Fi[-1] = 0.0
+    Wplus = Wi - 2 * lam * (gm - Fi)
+    assert Wplus[1] >= 1e-10 * (1 - 1e-6)
+    # same theta on both fluxes: G*** = (1-th) G^HLLC + th G
+    th = (gm[1] - GHm[1]) / (Gm[1] - GHm[1])
+    assert 0 <= th < 1
+    np.testing.assert_allclose(gm, (1 - th) * GHm + th * Gm, rtol=1e-12, atol=1e-9)
+    np.testing.assert_allclose(gp, (1 - th) * GHp + th * Gp, rtol=1e-12, atol=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# Whole-scheme invariants.
+# ---------------------------------------------------------------------------
+def test_conservation_on_periodic_grid():
+    """Components 1..nf-1 telescope (Sections 3.2, 5.2): their grid sums are
+    unchanged by RK3 steps up to round-off, limiters included."""
+    W = P.random_admissible((24, 16), seed=16)
+    o = make((24, 16))
+    dt = 0.2 / o.max_wavespeed(W)[:2].sum() * (1 / 24)
+    s0 = W.reshape(6, -1).sum(1)
+    W1 = W
+    for _ in range(3):
+        W1 = o.rk3_step(W1, dt)
+    s1 = W1.reshape(6, -1).sum(1)
+    scale = np.abs(W).reshape(6, -1).sum(1)
+    np.testing.assert_allclose(s1[:5], s0[:5], atol=1e-13 * scale[:5].max(), rtol=0)
+    for k in range(5):
+        assert abs(s1[k] - s0[k]) <= 1e-13 * scale[k] * 10
+
+
+def test_interface_advection_keeps_pressure_velocity_equilibrium():
+    """Section 6.2: across an advected material interface p and u stay
+    uniform."""
+    pr = P.interface_advection_1d(200)
+    o = Oracle(pr.n, pr.lo, pr.hi, pr.bcs, **pr.eos)
+    W, t, steps = o.advance_to(pr.W, 0.0, 400 * pr.dt_fixed, dt_fixed=pr.dt_fixed)
+    rho = W[0] + W[1]
+    u = W[2] / rho
+    p = np.array([o.thermo(W[:, i])["p"] for i in range(W.shape[1])])
+    assert np.abs(u - 100.0).max() / 100.0 < 1e-8
+    assert np.abs(p - 101325.0).max() / 101325.0 < 1e-8
+
+
+def test_mirror_symmetry_of_the_rhs():
+    """Right-biased interpolation is the mirrored left-biased one: a
+    mirrored state (x -> -x, momentum negated) gives the mirrored RHS."""
+    W = P.random_admissible((40,), seed=17)
+    o = make((40,), bcs=(("transmissive", "transmissive"),))
+    dt = 0.3 / o.max_wavespeed(W)[0] / 40
+    L = o.rhs(W, dt)
+    Wm = W[:, ::-1].copy()
+    Wm[2] *= -1
+    Lm = o.rhs(Wm, dt)[:, ::-1].copy()
+    Lm[2] *= -1
+    scale = np.abs(L).max(axis=1, keepdims=True)
+    np.testing.assert_allclose(Lm, L, atol=1e-10 * scale.max(), rtol=0)
+    np.testing.assert_allclose(Lm / scale, L / scale, atol=1e-9)
+
+
+def _admissible(o, W):
+    a1 = W[-1]
+    rct = np.array([o.thermo(W[:, i])["rho_ct2"] for i in range(W.shape[1])])
+    return W[0].min() > 0 and W[1].min() > 0 and a1.min() > 0 and a1.max() < 1 and rct.min() > 0
+
+
+@pytest.mark.parametrize("name", ["sod_gas_liquid", "sedov_multimaterial"])
+def test_strong_1d_problems_stay_admissible(name):
+    """Sections 6.3-6.4: gas/liquid Sod and multi-material Sedov (negative
+    liquid pressure) stay in G at every step."""
+    pr = getattr(P, name)()
+    o = Oracle(pr.n, pr.lo, pr.hi, pr.bcs, **pr.eos)
+    W = pr.W
+    nsteps = 60 if name == "sod_gas_liquid" else 200
+    for _ in range(nsteps):
+        W = o.rk3_step(W, pr.dt_fixed)
+        assert np.all(np.isfinite(W))
+        assert _admissible(o, W)
+
+
+def test_water_air_shock_tube_converges_to_exact_solution():
+    """1D water-air shock tube against the exact two-stiffened-gas Riemann
+    solution: the L1 density error falls with the grid."""
+    errs = []
+    for N in (100, 200, 400):
+        pr = P.water_air_shock_tube(N)
+        o = Oracle(pr.n, pr.lo, pr.hi, pr.bcs, **pr.eos)
+        W, t, _ = o.advance_to(pr.W, 0.0, pr.t_end, cfl=0.5)
+        x = (np.arange(N) + 0.5) / N
+        ex, _ = ER.solve_five_equation(pr.eos, (999.999, 0.00005, 0.0, 1e9, 1 - 1e-6),
+                                       (0.001, 49.99995, 0.0, 1e5, 1e-6), 0.7, t, x)
+        errs.append(np.mean(np.abs((W[0] + W[1]) - (ex[0] + ex[1]))))
+    assert errs[1] < 0.8 * errs[0] and errs[2] < 0.8 * errs[1], errs
+    assert errs[1] / 1000.0 < 0.02
+
+
+# ---------------------------------------------------------------------------
+# The exact Riemann solver itself (test asset) against jump conditions.
+# ---------------------------------------------------------------------------
+def test_exact_riemann_satisfies_jump_conditions():
+    eos = EOS
+    left = (999.999, 0.00005, 0.0, 1e9, 1 - 1e-6)
+    right = (0.001, 49.99995, 0.0, 1e5, 1e-6)
+    gl, pl = ER.mixture(eos, left[4])
+    gr, pr_ = ER.mixture(eos, right[4])
+    L = ER.Side(left[0] + left[1], 0.0, 1e9, gl, pl)
+    R = ER.Side(right[0] + right[1], 0.0, 1e5, gr, pr_)
+    ps, us = ER.star_state(L, R)
+    assert 1e5 < ps < 1e9 and us > 0
+    # right shock: Rankine-Hugoniot in the shock frame
+    rho_s = ER.sample(L, R, ps, us, us + 1e-9)[0]
+    ratio = (ps + pr_) / (1e5 + pr_)
+    S = R.u + R.c * math.sqrt((gr + 1) / (2 * gr) * ratio + (gr - 1) / (2 * gr))
+    m0, m1 = R.rho * (R.u - S), rho_s * (us - S)
+    assert m1 == pytest.approx(m0, rel=1e-10)
+    assert 1e5 + m0 * (R.u - S) == pytest.approx(ps + m1 * (us - S), rel=1e-10)
+
+    def h(rho, p, g, pi):  # specific enthalpy of a stiffened gas
+        return g * (p + pi) / ((g - 1) * rho)
+    assert h(R.rho, 1e5, gr, pr_) + 0.5 * (R.u - S) ** 2 == pytest.approx(
+        h(rho_s, ps, gr, pr_) + 0.5 * (us - S) ** 2, rel=1e-10)
+    # left rarefaction: isentrope and Riemann invariant through the fan
+    for xi in np.linspace(L.u - L.c, us - L.c * ((ps + pl) / (1e9 + pl)) ** ((gl - 1) / (2 * gl)), 7)[1:-1]:
+        rho, u, p, side = ER.sample(L, R, ps, us, xi)
+        assert side == 0
+        assert (p + pl) / rho**gl == pytest.approx((1e9 + pl) / L.rho**gl, rel=1e-10)
+        c = math.sqrt(gl * (p + pl) / rho)
+        assert u + 2 * c / (gl - 1) == pytest.approx(L.u + 2 * L.c / (gl - 1), rel=1e-10)
+
+
+def test_op_counting_build_counts_work():
+    pr = P.advection_2d(8)
+    o = Oracle(pr.n, pr.lo, pr.hi, pr.bcs, counting=True, **pr.eos)
+    o.opcount_reset()
+    o.rhs(pr.W, pr.dt_fixed)
+    c = o.opcount()
+    per_cell = (c["add"] + c["mul"]) / 64
+    assert 1000 < per_cell < 20000
+    assert c["div"] > 0 and c["sqrt"] > 0
