@@ -1,0 +1,204 @@
+/*
+ * wcns.h - C ABI of the GB300 PP-WCNS-IS solver for the five-equation
+ * (Allaire) two-phase model with an ideal-gas phase and a stiffened-gas
+ * liquid phase.
+ *
+ * Method: Wong, Angel, Barad & Kiris, "A positivity-preserving high-order
+ * weighted compact nonlinear scheme for compressible gas-liquid flows"
+ * (arXiv 2102.05287).  Section numbers below refer to that paper.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Phase 1 is the liquid (stiffened gas: gamma_l, pinf_l >= 0), phase 2 the
+ *    gas (ideal: gamma_g, pinf = 0), as in the paper's fluid table (Sec. 6).
+ *  - State layout: conservative vector W = (a1r1, a2r2, rho*u_1 .. rho*u_ndim,
+ *    E, alpha1) (Sec. 2), nf = ndim + 4 fields, stored structure-of-arrays as
+ *    a contiguous double array [nf][n_z][n_y][n_x] (x fastest, interior cells
+ *    only; lower-dimensional grids drop the leading axes).
+ *  - Pointers named W / dWdt are DEVICE pointers owned by the caller (for
+ *    example torch CUDA tensors), 8-byte aligned.  The handle owns all
+ *    scratch it needs, allocated once in wcns_create; rhs / step / advance
+ *    calls allocate nothing.
+ *  - Work is ordered on the stream set with wcns_set_options (default: the
+ *    legacy default stream).  Calls returning host values synchronise that
+ *    stream.
+ *  - Every call returns a status code (WCNS_OK = 0, or a WCNS_E_* value);
+ *    nothing throws or aborts.  wcns_strerror gives a message.  Device-side
+ *    problems (non-finite values, inadmissible input, limiter hard switches)
+ *    are counted in the handle's statistics (wcns_get_stats), never trapped.
+ */
+#ifndef WCNS_H
+#define WCNS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wcns_handle wcns_handle;
+
+/* Status codes. */
+enum {
+  WCNS_OK = 0,
+  WCNS_E_INVALID_ARG = 1,   /* bad argument (null pointer, size, parameter) */
+  WCNS_E_CUDA = 2,          /* a CUDA runtime call failed */
+  WCNS_E_INADMISSIBLE = 3,  /* input state outside the admissible set G (Sec. 2) */
+  WCNS_E_NONFINITE = 4,     /* a non-finite value appeared */
+  WCNS_E_TIMEOUT = 5,       /* a bounded device wait gave up */
+  WCNS_E_UNSUPPORTED = 6    /* option combination not provided */
+};
+
+/* Boundary conditions per face (three ghost layers, Sec. 6 "extrapolation"):
+ *   TRANSMISSIVE - zero-gradient copy of the boundary cell;
+ *   PERIODIC     - wrap-around (both faces of an axis must be periodic);
+ *   SYMMETRY     - mirror image with the normal momentum negated (n >= 3);
+ *   DIRICHLET    - a fixed conservative state given in wcns_bcs.dirichlet. */
+enum { WCNS_BC_TRANSMISSIVE = 0, WCNS_BC_PERIODIC = 1, WCNS_BC_SYMMETRY = 2, WCNS_BC_DIRICHLET = 3 };
+
+/* Uniform Cartesian grid on [lo, hi] (Sec. 3: cells of width (hi-lo)/n). */
+typedef struct {
+  int ndim;       /* 1, 2 or 3 */
+  int n[3];       /* cells per axis (entries beyond ndim ignored), each >= 1 */
+  double lo[3];
+  double hi[3];
+} wcns_grid;
+
+typedef struct {
+  int kind[3][2];              /* [axis][0 = low face, 1 = high face] */
+  double dirichlet[3][2][7];   /* conservative ghost state for DIRICHLET faces */
+} wcns_bcs;
+
+/* Precision of the hot path. */
+enum {
+  WCNS_FP64 = 0,   /* every step in FP64 */
+  WCNS_MIXED = 1   /* FP32 characteristic projection, WCNS-IS interpolation and
+                      HLLC fluxes; FP64 pressure / sound speed, limiter
+                      blending-coefficient solve and state accumulation */
+};
+
+/* Spatial scheme. */
+enum {
+  WCNS_SCHEME_PP_WCNS_IS = 0,  /* WCNS-IS with both PP limiters (Secs. 4-5) */
+  WCNS_SCHEME_HLLC1 = 1,       /* first-order HLLC scheme (Sec. 3) */
+  WCNS_SCHEME_WCNS_IS = 2      /* WCNS-IS with the limiters switched off */
+};
+
+typedef struct {
+  int precision;        /* WCNS_FP64 (default) or WCNS_MIXED */
+  int scheme;           /* WCNS_SCHEME_* (default PP-WCNS-IS) */
+  double eps_is;        /* epsilon of the IS nonlinear weights (Sec. 4.3; the paper
+                           does not print it): default 1e-40 (FP64), the FP32
+                           stages of the mixed path use max(eps_is, 1e-30) */
+  double eps_ar, eps_a, eps_rc;  /* limiter tolerances, Sec. 5.1: 1e-10, 1e-10, 1e-8 */
+  double hs_ar, hs_a, hs_rc;     /* hard-switch tolerances, Sec. 5.1: 1e-11, 1e-11, 1e-9 */
+  void *stream;         /* cudaStream_t for all work of this handle (NULL = default) */
+} wcns_options;
+
+/* Counters accumulated on the device since the last reset. */
+typedef struct {
+  long long interp_limited;  /* interpolated states with some theta < 1 (Algs. 1-3) */
+  long long interp_hard;     /* interpolation hard switches (Sec. 5.1) */
+  long long flux_limited;    /* midpoints with some flux-limiter theta < 1 (Algs. 4-6) */
+  long long flux_hard;       /* flux hard switches (Sec. 5.2) */
+  long long nonfinite;       /* cells whose update was not finite */
+  long long inadmissible;    /* input cells outside G (Sec. 2) */
+  long long midpoints;       /* midpoint fluxes evaluated */
+} wcns_stats;
+
+/* Create a solver for one grid, boundary set and fluid pair.
+ * gamma_g > 1, gamma_l > 1, pinf_l >= 0 and gamma_g <= gamma_l (Lemma 1,
+ * Sec. 2: the admissible set is convex only then).  Periodic axes need both
+ * faces periodic; symmetry needs n >= 3 on that axis.  Allocates the
+ * handle's device scratch (three states) on the current device.
+ * Returns WCNS_E_INVALID_ARG on a bad argument, WCNS_E_CUDA on allocation
+ * failure; *out is NULL on error. */
+int wcns_create(const wcns_grid *grid, const wcns_bcs *bcs, double gamma_g, double gamma_l,
+                double pinf_l, wcns_handle **out);
+
+/* Default options (FP64, PP-WCNS-IS, paper tolerances, default stream). */
+void wcns_default_options(wcns_options *opt);
+int wcns_set_options(wcns_handle *h, const wcns_options *opt);
+int wcns_get_options(const wcns_handle *h, wcns_options *opt);
+
+/* Semi-discrete right-hand side L(W) = dW/dt of Sec. 4 (eq. for dW/dt with
+ * G^{x,-}_{i+1/2} - G^{x,+}_{i-1/2}, including the alpha1 div(u) term),
+ * summed over the ndim directions.  dt is the Euler step the flux limiter
+ * protects (Sec. 5.2): lambda_d = dt / (dx_d sigma_d), sigma_d = tau_d /
+ * sum(tau) with tau_d = max(|u_d| + c)/dx_d of W (Sec. 3.3).
+ * W and dWdt are device arrays of nf * ncells doubles; they must not
+ * overlap.  Asynchronous on the handle's stream. */
+int wcns_rhs(wcns_handle *h, const double *W, double *dWdt, double dt);
+
+/* max over cells of (|u_d| + c) for each direction d < ndim (Sec. 3.3);
+ * out[d] = 0 for d >= ndim.  out is a HOST array of 3 doubles; synchronises. */
+int wcns_max_wavespeed(wcns_handle *h, const double *W, double out[3]);
+
+/* One SSPRK3 (Shu-Osher) step of size dt, in place on the device array W
+ * (Sec. 5.3: each stage is a convex combination of Euler steps).
+ * Asynchronous. */
+int wcns_rk3_step(wcns_handle *h, double *W, double dt);
+
+/* Advance W in place by nsteps SSPRK3 steps.  With dt_fixed > 0 every step
+ * uses dt_fixed; otherwise dt = cfl / sum_d tau_d from the state at the
+ * start of each step (Sec. 3.3), computed and kept on the device.
+ * *t_io (host) holds the start time on entry and the final time on exit.
+ * Synchronises once at the end. */
+int wcns_advance_steps(wcns_handle *h, double *W, int nsteps, double cfl, double dt_fixed,
+                       double *t_io);
+
+/* Advance W in place from t0 to t_end with CFL-limited steps (dt as above,
+ * the last step clipped to land on t_end).  Returns the end time and the
+ * number of steps taken in the host outputs (either may be NULL). */
+int wcns_advance_to(wcns_handle *h, double *W, double t0, double t_end, double cfl,
+                    double *t_out, long *steps_out);
+
+/* As wcns_advance_steps, but W_host is a HOST array (pageable or pinned):
+ * it is copied to the handle's device state, advanced, and copied back,
+ * all on the handle's stream.  Synchronises. */
+int wcns_advance_steps_host(wcns_handle *h, double *W_host, int nsteps, double cfl,
+                            double dt_fixed, double *t_io);
+
+/* Statistics counted on the device since creation or the last reset;
+ * synchronises. */
+int wcns_get_stats(wcns_handle *h, wcns_stats *out);
+int wcns_reset_stats(wcns_handle *h);
+
+/* Number of fields nf = ndim + 4 and of cells of the handle's grid. */
+int wcns_nfields(const wcns_handle *h);
+long long wcns_ncells(const wcns_handle *h);
+
+/* Kernel launches issued by this handle since creation (host-side count). */
+long long wcns_launch_count(const wcns_handle *h);
+
+const char *wcns_strerror(int status);
+void wcns_destroy(wcns_handle *h);
+
+/* ------------------------------------------------------------------------
+ * Batched mode: many independent 1D problems advanced together.
+ * Each problem k has ncells[k] cells on [lo[k], hi[k]] with the boundary
+ * kinds bc_lo / bc_hi (TRANSMISSIVE or PERIODIC), and shares the fluid
+ * pair.  States are packed one after another: the packed device array has
+ * 5 rows of total = sum(ncells) doubles (SoA [5][total]); problem k
+ * occupies columns offsets[k] .. offsets[k] + ncells[k] - 1 with
+ * offsets[k] = sum_{j<k} ncells[j].  Every problem takes its own CFL time
+ * step dt_k = cfl * dx_k / max(|u| + c) (Sec. 3.3, 1D).
+ * ------------------------------------------------------------------------ */
+typedef struct wcns_batch wcns_batch;
+
+/* ncells: host array of nprob sizes (each >= 1); lo/hi: host arrays of
+ * nprob doubles.  Copies the problem table to the device. */
+int wcns_batch_create(int nprob, const int *ncells, const double *lo, const double *hi, int bc_lo,
+                      int bc_hi, double gamma_g, double gamma_l, double pinf_l, wcns_batch **out);
+int wcns_batch_set_options(wcns_batch *b, const wcns_options *opt);
+/* Advance every problem by nsteps SSPRK3 steps in place (device array
+ * W_packed).  t_out: optional DEVICE array of nprob doubles receiving each
+ * problem's accumulated time (added to its incoming value).  Asynchronous. */
+int wcns_batch_advance(wcns_batch *b, double *W_packed, int nsteps, double cfl, double *t_out);
+int wcns_batch_get_stats(wcns_batch *b, wcns_stats *out);
+long long wcns_batch_total_cells(const wcns_batch *b);
+long long wcns_batch_launch_count(const wcns_batch *b);
+void wcns_batch_destroy(wcns_batch *b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WCNS_H */

@@ -100,6 +100,7 @@ def _lib(counting=False):
         stp = P(OracleStats)
         lib.oc_rhs.argtypes = [cfgp, dp, dp, d, stp]
         lib.oc_max_wavespeed.argtypes = [cfgp, dp, dp]
+        lib.oc_rhs_smax.argtypes = [cfgp, dp, dp, d, dp, stp]
         lib.oc_rk3_step.argtypes = [cfgp, dp, d, stp]
         lib.oc_advance_to.argtypes = [cfgp, dp, d, d, d, d, C.c_long, dp, P(C.c_long), stp]
         lib.oc_thermo.argtypes = [cfgp, dp, dp]
@@ -175,6 +176,15 @@ class Oracle:
         W = self._check(W)
         out = np.empty_like(W)
         self.lib.oc_rhs(C.byref(self.cfg), _dptr(W), _dptr(out), float(dt), C.byref(self.stats))
+        return out
+
+    def rhs_smax(self, W, dt, smax):
+        """RHS with sigma_d set from the given maxima of (|u_d| + c)."""
+        W = self._check(W)
+        out = np.empty_like(W)
+        sm = np.ascontiguousarray(np.asarray(smax, dtype=np.float64).reshape(3))
+        self.lib.oc_rhs_smax(C.byref(self.cfg), _dptr(W), _dptr(out), float(dt), _dptr(sm),
+                             C.byref(self.stats))
         return out
 
     def max_wavespeed(self, W):

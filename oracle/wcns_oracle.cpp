@@ -735,7 +735,8 @@ static void max_wavespeed_impl(const oc_config &c, const double *W, double *out)
   }
 }
 
-static void rhs_impl(const oc_config &c, const double *W, double *dWdt, double dt, oc_stats *st) {
+static void rhs_impl(const oc_config &c, const double *W, double *dWdt, double dt, oc_stats *st,
+                     const double *smax_given = nullptr) {
   const int nf = c.ndim + 4;
   const long N = ncells(c);
   Eos e = make_eos(c);
@@ -743,7 +744,11 @@ static void rhs_impl(const oc_config &c, const double *W, double *dWdt, double d
   // Directional split (Section 3.3): sigma_d = tau_d / sum(tau), with
   // tau_d = (|u_d| + c)_max / dx_d, and lambda_d = dt / (dx_d sigma_d).
   double smax[3];
-  max_wavespeed_impl(c, W, smax);
+  if (smax_given) {
+    for (int d = 0; d < 3; ++d) smax[d] = smax_given[d];
+  } else {
+    max_wavespeed_impl(c, W, smax);
+  }
   double tau[3], tsum = 0.0;
   for (int d = 0; d < c.ndim; ++d) {
     tau[d] = smax[d] / spacing(c, d);
@@ -820,6 +825,13 @@ int oc_nfields(const oc_config *c) { return c->ndim + 4; }
 
 void oc_rhs(const oc_config *c, const double *W, double *dWdt, double dt, oc_stats *st) {
   rhs_impl(*c, W, dWdt, dt, st);
+}
+
+// As oc_rhs, with the maxima of (|u_d| + c) that set sigma_d supplied by the
+// caller (used to evaluate the RHS of a sub-box of a larger grid).
+void oc_rhs_smax(const oc_config *c, const double *W, double *dWdt, double dt, const double *smax3,
+                 oc_stats *st) {
+  rhs_impl(*c, W, dWdt, dt, st, smax3);
 }
 
 void oc_max_wavespeed(const oc_config *c, const double *W, double *out3) {

@@ -1,0 +1,477 @@
+// Host side of the C ABI declared in include/wcns.h: handle, scratch
+// buffers, time-step control and the SSPRK3 orchestration of the sweeps.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <cuda_runtime.h>
+
+#include "../../include/wcns.h"
+#include "wcns_internal.h"
+
+using namespace wcns;
+
+struct wcns_handle {
+  int ndim, nf;
+  int n[3];
+  long long N;
+  double dx[3], inv_dx[3];
+  int bc[3][2];
+  double dirichlet[3][2][7];
+  EosConst eos;
+  wcns_options opt;
+  cudaStream_t stream;
+  double *W1, *W2, *L, *Wh;  // stage states, RHS accumulator, host-API state
+  StepCtl *ctl;
+  DevStats *stats;
+  long long launches;
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Device helpers.
+// ---------------------------------------------------------------------------
+// max over cells of (|u_d| + c) (Sec. 3.3), FP64 mixture thermodynamics
+// (Sec. 2), into ctl->smax[slot][d].
+__global__ void reduce_wavespeed_kernel(const double *__restrict__ W, long long N, int ndim,
+                                        EosConst e, StepCtl *ctl, int slot) {
+  double smax[3] = {0.0, 0.0, 0.0};
+  const int E = 2 + ndim, A = 3 + ndim;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double rho = W[i] + W[N + i];
+    const double ir = 1.0 / rho;
+    double m2 = 0.0, v[3] = {0.0, 0.0, 0.0};
+    for (int j = 0; j < ndim; ++j) {
+      const double m = W[(2 + j) * N + i];
+      v[j] = m * ir;
+      m2 = fma(m, v[j], m2);
+    }
+    const double rhoe = W[E * N + i] - 0.5 * m2;
+    const double a1 = W[A * N + i];
+    const double Gam = fma(a1, e.r1 - e.r2, e.r2);
+    const double Pi = a1 * e.q1;
+    const double iG = 1.0 / Gam;
+    const double p = (rhoe - Pi) * iG;
+    const double pb = Pi / (Gam + 1.0);
+    const double c = sqrt((1.0 + iG) * (p + pb) * ir);
+    for (int j = 0; j < ndim; ++j) {
+      const double s = fabs(v[j]) + c;
+      smax[j] = (s > smax[j] || s != s) ? s : smax[j];
+    }
+  }
+  for (int j = 0; j < ndim; ++j) {
+    unsigned long long b = __double_as_longlong(smax[j]);
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long ob = __shfl_xor_sync(0xffffffffu, b, o);
+      b = ob > b ? ob : b;
+    }
+    if ((threadIdx.x & 31) == 0 && b) atomicMax(&ctl->smax[slot][j], b);
+  }
+}
+
+__global__ void init_ctl_kernel(StepCtl *ctl, double t, double t_end) {
+  for (int k = 0; k < 4; ++k)
+    for (int d = 0; d < 3; ++d) ctl->smax[k][d] = 0ull;
+  ctl->dt = 0.0;
+  ctl->t = t;
+  ctl->t_end = t_end;
+  ctl->steps = 0;
+  ctl->active = t < t_end ? 1 : 0;
+}
+
+// Start of a step: take max(|u_d|+c) of W^n (left in smax[3] by the previous
+// step's last combine or by a reduction), choose dt (fixed, or CFL / sum_d
+// tau_d, Sec. 3.3), clip to t_end, and clear the accumulators of the stages.
+__global__ void step_begin_kernel(StepCtl *ctl, int ndim, double ix0, double ix1, double ix2,
+                                  double dt_fixed, double cfl, int advance_time) {
+  const double ix[3] = {ix0, ix1, ix2};
+  double tsum = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    ctl->smax[0][d] = ctl->smax[3][d];
+    if (d < ndim) tsum += __longlong_as_double(ctl->smax[0][d]) * ix[d];
+  }
+  for (int k = 1; k < 4; ++k)
+    for (int d = 0; d < 3; ++d) ctl->smax[k][d] = 0ull;
+  double dt = dt_fixed > 0.0 ? dt_fixed : cfl / tsum;
+  if (!advance_time) {
+    ctl->dt = dt;
+    ctl->active = 1;
+    return;
+  }
+  if (!ctl->active || !(ctl->t < ctl->t_end)) {
+    ctl->active = 0;
+    ctl->dt = 0.0;
+    return;
+  }
+  if (ctl->t + dt >= ctl->t_end) {
+    dt = ctl->t_end - ctl->t;
+    ctl->t = ctl->t_end;
+  } else {
+    ctl->t = ctl->t + dt;
+  }
+  ctl->dt = dt;
+  ctl->steps += 1;
+}
+
+// ---------------------------------------------------------------------------
+// Host helpers.
+// ---------------------------------------------------------------------------
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? WCNS_OK : WCNS_E_CUDA; }
+
+#define CK(x)                                   \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) return WCNS_E_CUDA; \
+  } while (0)
+
+int launch_reduce(wcns_handle *h, const double *W, int slot) {
+  const int threads = 256;
+  long long blocks = (h->N + threads - 1) / threads;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks < 1) blocks = 1;
+  reduce_wavespeed_kernel<<<(int)blocks, threads, 0, h->stream>>>(W, h->N, h->ndim, h->eos, h->ctl, slot);
+  h->launches++;
+  return cuda_status(cudaGetLastError());
+}
+
+int launch_init(wcns_handle *h, double t, double t_end) {
+  init_ctl_kernel<<<1, 1, 0, h->stream>>>(h->ctl, t, t_end);
+  h->launches++;
+  return cuda_status(cudaGetLastError());
+}
+
+int launch_begin(wcns_handle *h, double dt_fixed, double cfl, int advance_time) {
+  step_begin_kernel<<<1, 1, 0, h->stream>>>(h->ctl, h->ndim, h->inv_dx[0], h->inv_dx[1], h->inv_dx[2],
+                                            dt_fixed, cfl, advance_time);
+  h->launches++;
+  return cuda_status(cudaGetLastError());
+}
+
+SweepArgs base_args(wcns_handle *h, int d) {
+  SweepArgs a;
+  memset(&a, 0, sizeof(a));
+  for (int k = 0; k < 3; ++k) {
+    a.n[k] = h->n[k];
+    a.inv_dx_all[k] = h->inv_dx[k];
+  }
+  a.ncell = h->N;
+  a.bc_lo = h->bc[d][0];
+  a.bc_hi = h->bc[d][1];
+  for (int q = 0; q < 7; ++q) {
+    a.dir_lo[q] = h->dirichlet[d][0][q];
+    a.dir_hi[q] = h->dirichlet[d][1][q];
+  }
+  a.inv_dx = h->inv_dx[d];
+  a.eos = h->eos;
+  a.tol.eps_ar = h->opt.eps_ar;
+  a.tol.eps_a = h->opt.eps_a;
+  a.tol.eps_rc = h->opt.eps_rc;
+  a.tol.hs_ar = h->opt.hs_ar;
+  a.tol.hs_a = h->opt.hs_a;
+  a.tol.hs_rc = h->opt.hs_rc;
+  a.eps_is = h->opt.eps_is;
+  a.scheme = h->opt.scheme;
+  a.ctl = h->ctl;
+  a.stats = h->stats;
+  return a;
+}
+
+int launch_sweep(wcns_handle *h, int d, const SweepArgs &a) {
+  cudaError_t e = h->opt.precision == WCNS_MIXED ? launch_sweep_mixed(h->ndim, d, a, h->stream)
+                                                 : launch_sweep_fp64(h->ndim, d, a, h->stream);
+  h->launches++;
+  return cuda_status(e);
+}
+
+// dW/dt of W into L for every direction (stage 0 lambda).
+int enqueue_rhs(wcns_handle *h, const double *W, double *L) {
+  for (int d = 0; d < h->ndim; ++d) {
+    SweepArgs a = base_args(h, d);
+    a.epilogue = d == 0 ? EPI_WRITE : EPI_ACCUM;
+    a.stage = 0;
+    a.W_in = W;
+    a.L = L;
+    int st = launch_sweep(h, d, a);
+    if (st) return st;
+  }
+  return WCNS_OK;
+}
+
+// One SSPRK3 step in place on W (Shu-Osher form, Sec. 5.3):
+//   W1 = W + dt L(W);  W2 = 3/4 W + 1/4 (W1 + dt L(W1));
+//   W  = 1/3 W + 2/3 (W2 + dt L(W2)).
+int enqueue_step(wcns_handle *h, double *W, double dt_fixed, double cfl) {
+  int st = launch_begin(h, dt_fixed, cfl, 1);
+  if (st) return st;
+  const double ra[3] = {0.0, 0.75, 1.0 / 3.0};
+  const double rb[3] = {1.0, 0.25, 2.0 / 3.0};
+  for (int s = 0; s < 3; ++s) {
+    const double *Win = s == 0 ? W : (s == 1 ? h->W1 : h->W2);
+    double *Wout = s == 0 ? h->W1 : (s == 1 ? h->W2 : W);
+    for (int d = 0; d < h->ndim; ++d) {
+      SweepArgs a = base_args(h, d);
+      a.stage = s;
+      a.W_in = Win;
+      a.Wn = W;
+      a.L = h->L;
+      if (d < h->ndim - 1) {
+        a.epilogue = d == 0 ? EPI_WRITE : EPI_ACCUM;
+      } else {
+        a.epilogue = EPI_COMBINE;
+        a.read_L = h->ndim > 1;
+        a.rk_a = ra[s];
+        a.rk_b = rb[s];
+        a.W_out = Wout;
+      }
+      st = launch_sweep(h, d, a);
+      if (st) return st;
+    }
+  }
+  return WCNS_OK;
+}
+
+bool valid_bc(int k) { return k >= 0 && k <= 3; }
+
+}  // namespace
+
+extern "C" {
+
+void wcns_default_options(wcns_options *o) {
+  if (!o) return;
+  o->precision = WCNS_FP64;
+  o->scheme = WCNS_SCHEME_PP_WCNS_IS;
+  o->eps_is = 1e-40;
+  o->eps_ar = 1e-10;
+  o->eps_a = 1e-10;
+  o->eps_rc = 1e-8;
+  o->hs_ar = 1e-11;
+  o->hs_a = 1e-11;
+  o->hs_rc = 1e-9;
+  o->stream = NULL;
+}
+
+int wcns_create(const wcns_grid *g, const wcns_bcs *bcs, double gamma_g, double gamma_l, double pinf_l,
+                wcns_handle **out) {
+  if (!out) return WCNS_E_INVALID_ARG;
+  *out = NULL;
+  if (!g || !bcs) return WCNS_E_INVALID_ARG;
+  if (g->ndim < 1 || g->ndim > 3) return WCNS_E_INVALID_ARG;
+  if (!(gamma_g > 1.0) || !(gamma_l > 1.0) || !(pinf_l >= 0.0) || !(gamma_g <= gamma_l) ||
+      !isfinite(gamma_g) || !isfinite(gamma_l) || !isfinite(pinf_l))
+    return WCNS_E_INVALID_ARG;
+  long long N = 1;
+  for (int d = 0; d < g->ndim; ++d) {
+    if (g->n[d] < 1 || !(g->hi[d] > g->lo[d]) || !isfinite(g->hi[d] - g->lo[d])) return WCNS_E_INVALID_ARG;
+    for (int s = 0; s < 2; ++s)
+      if (!valid_bc(bcs->kind[d][s])) return WCNS_E_INVALID_ARG;
+    if ((bcs->kind[d][0] == WCNS_BC_PERIODIC) != (bcs->kind[d][1] == WCNS_BC_PERIODIC))
+      return WCNS_E_INVALID_ARG;
+    if ((bcs->kind[d][0] == WCNS_BC_SYMMETRY || bcs->kind[d][1] == WCNS_BC_SYMMETRY) && g->n[d] < 3)
+      return WCNS_E_INVALID_ARG;
+    N *= g->n[d];
+    if (g->n[d] > (1 << 30) || N > (1ll << 40)) return WCNS_E_INVALID_ARG;
+  }
+  // launch-grid limits of the sweeps (gridDim.y / gridDim.z <= 65535)
+  {
+    const long long ny = g->ndim > 1 ? g->n[1] : 1, nz = g->ndim > 2 ? g->n[2] : 1;
+    if ((ny + 1) / 2 > 65535 || nz > 65535 || (g->ndim > 2 && ny > 65535) ||
+        ((long long)g->n[0] + 31) / 32 > 65535)
+      return WCNS_E_INVALID_ARG;
+  }
+  wcns_handle *h = (wcns_handle *)calloc(1, sizeof(wcns_handle));
+  if (!h) return WCNS_E_CUDA;
+  h->ndim = g->ndim;
+  h->nf = g->ndim + 4;
+  h->N = N;
+  for (int d = 0; d < 3; ++d) {
+    h->n[d] = d < g->ndim ? g->n[d] : 1;
+    h->dx[d] = d < g->ndim ? (g->hi[d] - g->lo[d]) / g->n[d] : 1.0;
+    h->inv_dx[d] = d < g->ndim ? 1.0 / h->dx[d] : 0.0;
+    for (int s = 0; s < 2; ++s) {
+      h->bc[d][s] = d < g->ndim ? bcs->kind[d][s] : WCNS_BC_TRANSMISSIVE;
+      for (int q = 0; q < 7; ++q) h->dirichlet[d][s][q] = bcs->dirichlet[d][s][q];
+    }
+  }
+  h->eos.r1 = 1.0 / (gamma_l - 1.0);
+  h->eos.r2 = 1.0 / (gamma_g - 1.0);
+  h->eos.q1 = gamma_l * pinf_l / (gamma_l - 1.0);
+  wcns_default_options(&h->opt);
+  h->stream = 0;
+  const size_t bytes = sizeof(double) * (size_t)h->nf * (size_t)N;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMalloc(&h->W1, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&h->W2, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&h->L, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&h->ctl, sizeof(StepCtl));
+  if (e == cudaSuccess) e = cudaMalloc(&h->stats, sizeof(DevStats));
+  if (e == cudaSuccess) e = cudaMemset(h->stats, 0, sizeof(DevStats));
+  if (e == cudaSuccess) e = cudaMemset(h->ctl, 0, sizeof(StepCtl));
+  if (e != cudaSuccess) {
+    wcns_destroy(h);
+    return WCNS_E_CUDA;
+  }
+  *out = h;
+  return WCNS_OK;
+}
+
+int wcns_set_options(wcns_handle *h, const wcns_options *o) {
+  if (!h || !o) return WCNS_E_INVALID_ARG;
+  if (o->precision != WCNS_FP64 && o->precision != WCNS_MIXED) return WCNS_E_INVALID_ARG;
+  if (o->scheme < 0 || o->scheme > 2) return WCNS_E_INVALID_ARG;
+  if (!(o->eps_is > 0.0) || !(o->eps_ar >= 0.0) || !(o->eps_a >= 0.0) || !(o->eps_rc >= 0.0))
+    return WCNS_E_INVALID_ARG;
+  h->opt = *o;
+  h->stream = (cudaStream_t)o->stream;
+  return WCNS_OK;
+}
+
+int wcns_get_options(const wcns_handle *h, wcns_options *o) {
+  if (!h || !o) return WCNS_E_INVALID_ARG;
+  *o = h->opt;
+  return WCNS_OK;
+}
+
+int wcns_rhs(wcns_handle *h, const double *W, double *dWdt, double dt) {
+  if (!h || !W || !dWdt || !(dt >= 0.0) || !isfinite(dt)) return WCNS_E_INVALID_ARG;
+  const size_t bytes = sizeof(double) * (size_t)h->nf * (size_t)h->N;
+  if ((const char *)W < (const char *)dWdt + bytes && (const char *)dWdt < (const char *)W + bytes)
+    return WCNS_E_INVALID_ARG;
+  int st = launch_init(h, 0.0, INFINITY);
+  if (!st && h->ndim > 1) st = launch_reduce(h, W, 3);
+  if (!st) st = launch_begin(h, dt > 0.0 ? dt : 1e-300, 0.0, 0);
+  if (!st) st = enqueue_rhs(h, W, dWdt);
+  return st;
+}
+
+int wcns_max_wavespeed(wcns_handle *h, const double *W, double out[3]) {
+  if (!h || !W || !out) return WCNS_E_INVALID_ARG;
+  int st = launch_init(h, 0.0, INFINITY);
+  if (!st) st = launch_reduce(h, W, 3);
+  if (st) return st;
+  StepCtl c;
+  CK(cudaMemcpyAsync(&c, h->ctl, sizeof(StepCtl), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (int d = 0; d < 3; ++d) {
+    unsigned long long b = c.smax[3][d];
+    double v;
+    memcpy(&v, &b, sizeof(v));
+    out[d] = d < h->ndim ? v : 0.0;
+  }
+  return WCNS_OK;
+}
+
+int wcns_rk3_step(wcns_handle *h, double *W, double dt) {
+  if (!h || !W || !(dt > 0.0) || !isfinite(dt)) return WCNS_E_INVALID_ARG;
+  int st = launch_init(h, 0.0, INFINITY);
+  if (!st && h->ndim > 1) st = launch_reduce(h, W, 3);
+  if (!st) st = enqueue_step(h, W, dt, 0.0);
+  return st;
+}
+
+int wcns_advance_steps(wcns_handle *h, double *W, int nsteps, double cfl, double dt_fixed, double *t_io) {
+  if (!h || !W || nsteps < 0 || !(dt_fixed >= 0.0) || !isfinite(dt_fixed)) return WCNS_E_INVALID_ARG;
+  if (dt_fixed == 0.0 && !(cfl > 0.0 && cfl <= 1.0)) return WCNS_E_INVALID_ARG;
+  const double t0 = t_io ? *t_io : 0.0;
+  int st = launch_init(h, t0, INFINITY);
+  if (!st && (h->ndim > 1 || dt_fixed == 0.0)) st = launch_reduce(h, W, 3);
+  for (int k = 0; k < nsteps && !st; ++k) st = enqueue_step(h, W, dt_fixed, cfl);
+  if (st) return st;
+  if (t_io) {
+    StepCtl c;
+    CK(cudaMemcpyAsync(&c, h->ctl, sizeof(StepCtl), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *t_io = c.t;
+  }
+  return WCNS_OK;
+}
+
+int wcns_advance_to(wcns_handle *h, double *W, double t0, double t_end, double cfl, double *t_out,
+                    long *steps_out) {
+  if (!h || !W || !isfinite(t0) || !isfinite(t_end) || !(cfl > 0.0 && cfl <= 1.0)) return WCNS_E_INVALID_ARG;
+  int st = launch_init(h, t0, t_end);
+  if (!st) st = launch_reduce(h, W, 3);
+  if (st) return st;
+  StepCtl c;
+  int batch = 8;
+  for (;;) {
+    for (int k = 0; k < batch && !st; ++k) st = enqueue_step(h, W, 0.0, cfl);
+    if (st) return st;
+    CK(cudaMemcpyAsync(&c, h->ctl, sizeof(StepCtl), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (!c.active || !(c.t < t_end)) break;
+    if (!isfinite(c.t) || !isfinite(c.dt) || c.dt <= 0.0) return WCNS_E_NONFINITE;
+    if (batch < 256) batch *= 2;
+  }
+  if (t_out) *t_out = c.t;
+  if (steps_out) *steps_out = (long)c.steps;
+  return WCNS_OK;
+}
+
+int wcns_advance_steps_host(wcns_handle *h, double *W_host, int nsteps, double cfl, double dt_fixed,
+                            double *t_io) {
+  if (!h || !W_host) return WCNS_E_INVALID_ARG;
+  const size_t bytes = sizeof(double) * (size_t)h->nf * (size_t)h->N;
+  if (!h->Wh) CK(cudaMalloc(&h->Wh, bytes));
+  CK(cudaMemcpyAsync(h->Wh, W_host, bytes, cudaMemcpyHostToDevice, h->stream));
+  double t = t_io ? *t_io : 0.0;
+  int st = wcns_advance_steps(h, h->Wh, nsteps, cfl, dt_fixed, &t);
+  if (st) return st;
+  CK(cudaMemcpyAsync(W_host, h->Wh, bytes, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (t_io) *t_io = t;
+  return WCNS_OK;
+}
+
+int wcns_get_stats(wcns_handle *h, wcns_stats *out) {
+  if (!h || !out) return WCNS_E_INVALID_ARG;
+  DevStats s;
+  CK(cudaMemcpyAsync(&s, h->stats, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  out->interp_limited = (long long)s.interp_limited;
+  out->interp_hard = (long long)s.interp_hard;
+  out->flux_limited = (long long)s.flux_limited;
+  out->flux_hard = (long long)s.flux_hard;
+  out->nonfinite = (long long)s.nonfinite;
+  out->inadmissible = (long long)s.inadmissible;
+  out->midpoints = (long long)s.midpoints;
+  return WCNS_OK;
+}
+
+int wcns_reset_stats(wcns_handle *h) {
+  if (!h) return WCNS_E_INVALID_ARG;
+  CK(cudaMemsetAsync(h->stats, 0, sizeof(DevStats), h->stream));
+  return WCNS_OK;
+}
+
+int wcns_nfields(const wcns_handle *h) { return h ? h->nf : 0; }
+long long wcns_ncells(const wcns_handle *h) { return h ? h->N : 0; }
+long long wcns_launch_count(const wcns_handle *h) { return h ? h->launches : 0; }
+
+const char *wcns_strerror(int s) {
+  switch (s) {
+    case WCNS_OK: return "ok";
+    case WCNS_E_INVALID_ARG: return "invalid argument";
+    case WCNS_E_CUDA: return "CUDA runtime error";
+    case WCNS_E_INADMISSIBLE: return "input state outside the admissible set";
+    case WCNS_E_NONFINITE: return "non-finite value";
+    case WCNS_E_TIMEOUT: return "bounded device wait timed out";
+    case WCNS_E_UNSUPPORTED: return "unsupported option combination";
+    default: return "unknown status";
+  }
+}
+
+void wcns_destroy(wcns_handle *h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  cudaFree(h->W1);
+  cudaFree(h->W2);
+  cudaFree(h->L);
+  cudaFree(h->Wh);
+  cudaFree(h->ctl);
+  cudaFree(h->stats);
+  free(h);
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// Internal declarations shared by the CUDA translation units of libwcns.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wcns {
+
+// Per-phase EOS constants (Sec. 2): with Gamma(a1) = 1/(gbar-1) and
+// Pi(a1) = gbar pbar/(gbar-1),
+//   Gamma = a1 * r1 + (1 - a1) * r2,   Pi = a1 * q1   (the gas has pinf = 0).
+struct EosConst {
+  double r1;  // 1/(gamma_l - 1)
+  double r2;  // 1/(gamma_g - 1)
+  double q1;  // gamma_l pinf_l / (gamma_l - 1)
+};
+
+struct LimTol {
+  double eps_ar, eps_a, eps_rc;  // Algorithms 1-6 tolerances
+  double hs_ar, hs_a, hs_rc;     // hard-switch tolerances
+};
+
+// Device counters (accumulated with integer atomics: order-independent).
+struct DevStats {
+  unsigned long long interp_limited;
+  unsigned long long interp_hard;
+  unsigned long long flux_limited;
+  unsigned long long flux_hard;
+  unsigned long long nonfinite;
+  unsigned long long inadmissible;
+  unsigned long long midpoints;
+};
+
+// Time-step control kept in device memory so that whole steps can run (and
+// be captured in a CUDA graph) without host round trips.
+//   smax[k][d]: bit patterns of max(|u_d| + c) of stage-input state k
+//   (k = 0: W^n, 1: W^(1), 2: W^(2), 3: W^(n+1)); non-negative doubles
+//   order like their bit patterns, so atomicMax on the bits is exact.
+struct StepCtl {
+  unsigned long long smax[4][3];
+  double dt;        // step size of the current step
+  double t;         // time after the current step
+  double t_end;     // advance-to target (or +inf)
+  long long steps;  // steps taken
+  int active;       // 0 once t has reached t_end: remaining kernels do nothing
+};
+
+enum Epilogue {
+  EPI_WRITE = 0,     // L  = contribution
+  EPI_ACCUM = 1,     // L += contribution
+  EPI_COMBINE = 2,   // W_out = a W^n + b (W_in + dt (L? + contribution)), plus wave-speed max
+};
+
+enum { SCHEME_PP = 0, SCHEME_HLLC1 = 1, SCHEME_WCNS = 2 };
+enum { BC_TRANS = 0, BC_PERIODIC = 1, BC_SYMMETRY = 2, BC_DIRICHLET = 3 };
+
+struct SweepArgs {
+  int n[3];                 // cells per axis (1 beyond ndim)
+  long long ncell;          // product of n
+  int bc_lo, bc_hi;         // boundary kinds of the swept axis
+  double dir_lo[7], dir_hi[7];  // Dirichlet ghost states of the swept axis
+  double inv_dx;            // 1/dx of the swept axis
+  double inv_dx_all[3];     // 1/dx of every axis
+  EosConst eos;
+  LimTol tol;
+  double eps_is;
+  int scheme;
+  int epilogue;
+  int read_L;               // EPI_COMBINE: add the L array (earlier directions)
+  double rk_a, rk_b;        // combine coefficients
+  int stage;                // 0, 1, 2: lambda from ctl->smax[stage]; the combine
+                            // epilogue reduces into ctl->smax[stage + 1]
+  const double *W_in;       // stage input state
+  const double *Wn;         // W^n (combine with rk_a != 0)
+  double *W_out;            // combine output
+  double *L;                // RHS accumulator
+  StepCtl *ctl;             // device step control (dt, wave-speed maxima)
+  DevStats *stats;
+};
+
+// Launchers (defined per precision in wcns_fp64.cu / wcns_mixed.cu).
+cudaError_t launch_sweep_fp64(int ndim, int dir, const SweepArgs &a, cudaStream_t s);
+cudaError_t launch_sweep_mixed(int ndim, int dir, const SweepArgs &a, cudaStream_t s);
+
+}  // namespace wcns

@@ -1,0 +1,975 @@
+// Fused directional sweep of the PP-WCNS-IS right-hand side (Wong et al.,
+// arXiv 2102.05287) for GB300 (sm_103a).
+//
+// One launch handles one direction d of one RHS evaluation.  A thread block
+// owns a tile of TL lines x TM midpoints along d:
+//   1. stage the conservative states of the tile's TM+5 nodes per line
+//      (three-cell halo on each side) into shared memory, applying the
+//      boundary conditions by index remapping (no ghost arrays in HBM);
+//   2. node work, once per node: pressure and sound speed (Sec. 2), the
+//      flux G^d including alpha1*u_d (Sec. 3.2);
+//   3. one thread per midpoint i+1/2: characteristic projection (App. A),
+//      left/right WCNS-IS interpolation (Sec. 4.3), back-projection and
+//      V -> W, interpolation limiter (Sec. 5.1, Algs. 1-3), midpoint HLLC
+//      (Sec. 3.1-3.2), HCS flux reconstruction (Sec. 4.1), the split
+//      G^-/G^+ (Sec. 3.2), first-order HLLC fluxes and the flux limiter
+//      (Sec. 5.2, Algs. 4-6);
+//   4. cell update dW/dt -= (G^-_{i+1/2} - G^+_{i-1/2})/dx, written to the
+//      RHS array or fused with the SSPRK3 stage combine (Sec. 5.3), whose
+//      epilogue also reduces max(|u_d| + c) of the new state for the next
+//      stage's directional split (Sec. 3.3).
+// Consecutive tiles overlap by one midpoint so that every cell's two faces
+// are computed inside one block.
+//
+// Precision: R is the type of the projection, interpolation and HLLC
+// arithmetic (double for the FP64 path, float for the mixed path).  Node
+// pressure / sound speed, the limiters and all state arithmetic are FP64.
+// The interpolation works on deviations from node i: WCNS-IS is exactly
+// shift invariant (sub-stencil weights sum to one, smoothness indicators
+// use differences), so U~ = U_i + WCNS-IS(U - U_i) and FP32 rounding then
+// scales with the local variation instead of the magnitude of the fields.
+#pragma once
+#include <math.h>
+#include <stdint.h>
+
+#include "wcns_internal.h"
+
+namespace wcns {
+
+// ---------------------------------------------------------------------------
+// Tile shapes: TL lines x TM midpoints, THREADS threads per block.  The
+// x sweep takes rows of 128 midpoints (coalesced along x); the y/z sweeps
+// take 32 consecutive x columns per block (coalesced across lines).
+// ---------------------------------------------------------------------------
+template <int NDIM, int DIR>
+struct Tile {
+  static constexpr int TL = (DIR == 0) ? (NDIM == 1 ? 1 : 2) : 32;
+  static constexpr int TM = (DIR == 0) ? 128 : 16;
+  static constexpr int THREADS = (DIR == 0) ? TL * TM : 256;
+  static constexpr int NS = TM + 5;      // nodes per line
+  static constexpr int NN = TL * NS;     // nodes per block
+  static constexpr int NM = TL * TM;     // midpoints per block
+};
+
+template <class R>
+struct Prec;
+template <>
+struct Prec<double> {
+  static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+  static __device__ __forceinline__ double clampratio(double r) { return r; }
+  static __device__ __forceinline__ double sqrt_(double a) { return sqrt(a); }
+};
+template <>
+struct Prec<float> {
+  static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+  // keep tau5/(beta+eps) products finite in FP32
+  static __device__ __forceinline__ float clampratio(float r) { return fminf(r, 1e15f); }
+  static __device__ __forceinline__ float sqrt_(float a) { return sqrtf(a); }
+};
+
+// ---------------------------------------------------------------------------
+// Sec. 4.3: incremental-stencil WENO interpolation, left-biased to i+1/2 from
+// u_{i-2} .. u_{i+2}.  The right-biased value is the same formula on the
+// mirrored stencil.
+// ---------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ R wenois(R um2, R um1, R u0, R up1, R up2, R eps) {
+  const R s0 = R(0.5) * (u0 + up1);
+  const R s1 = R(0.5) * (R(3) * u0 - um1);
+  const R s2 = R(0.125) * (R(3) * u0 + R(6) * up1 - up2);
+  const R s3 = R(0.125) * (R(3) * um2 - R(10) * um1 + R(15) * u0);
+  const R e0 = u0 - up1, e1 = um1 - u0;
+  const R b0 = e0 * e0;
+  const R b1 = e1 * e1;
+  const R a01 = um1 - R(2) * u0 + up1, c01 = um1 - up1;
+  const R b01 = R(13.0 / 12.0) * a01 * a01 + R(0.25) * c01 * c01;
+  const R a2 = u0 - R(2) * up1 + up2, c2 = R(3) * u0 - R(4) * up1 + up2;
+  const R b2 = R(13.0 / 12.0) * a2 * a2 + R(0.25) * c2 * c2;
+  const R a3 = um2 - R(2) * um1 + u0, c3 = um2 - R(4) * um1 + R(3) * u0;
+  const R b3 = R(13.0 / 12.0) * a3 * a3 + R(0.25) * c3 * c3;
+  const R t5a = up2 - R(4) * up1 + R(6) * u0 - R(4) * um1 + um2;
+  const R t5b = up2 - R(2) * up1 + R(2) * um1 - um2;
+  const R tau = R(13.0 / 12.0) * t5a * t5a + R(0.25) * t5b * t5b;
+  const R r01 = Prec<R>::clampratio(Prec<R>::div(tau, b01 + eps));
+  const R r0 = Prec<R>::clampratio(Prec<R>::div(tau, b0 + eps));
+  const R r1 = Prec<R>::clampratio(Prec<R>::div(tau, b1 + eps));
+  const R r2 = Prec<R>::clampratio(Prec<R>::div(tau, b2 + eps));
+  const R r3 = Prec<R>::clampratio(Prec<R>::div(tau, b3 + eps));
+  const R w0 = R(15.0 / 32.0) * (R(1) + r0 * r01);
+  const R w1 = R(5.0 / 32.0) * (R(1) + r1 * r01);
+  const R w2 = R(5.0 / 16.0) * (R(1) + r2);
+  const R w3 = R(1.0 / 16.0) * (R(1) + r3);
+  return Prec<R>::div(w0 * s0 + w1 * s1 + w2 * s2 + w3 * s3, (w0 + w1) + (w2 + w3));
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 3.1-3.2: HLLC flux in direction DIR from two states given by their
+// conservative vector, velocity, pressure, density and sound speed.
+// Returns G (nf components, alpha flux last) and s* (= u-hat).
+// The star-state jumps W*_K - W_K are evaluated in a cancellation-free form
+// (algebraically identical to the paper's W*_K minus W_K), with
+// chi - 1 = (s* - u_K)/(s_K - s*):
+//   d(a_k rho_k) = (chi-1) a_k rho_k,   d(rho u_n) = rho s_K (chi-1),
+//   d(rho u_t)   = (chi-1) rho u_t,
+//   dE = (chi-1)(E + p) + chi rho s* (s* - u_K).
+// ---------------------------------------------------------------------------
+template <int NDIM, int DIR, class R>
+__device__ __forceinline__ void hllc(const R *WL, const R *vL, R pL, R rL, R cL, const R *WR,
+                                     const R *vR, R pR, R rR, R cR, R *G, R &sstar) {
+  constexpr int NF = NDIM + 4, E = 2 + NDIM, A = 3 + NDIM;
+  const R uL = vL[DIR], uR = vR[DIR];
+  const R ubar = R(0.5) * (uL + uR), cbar = R(0.5) * (cL + cR);
+  const R sL = fmin(ubar - cbar, uL - cL);
+  const R sR = fmax(ubar + cbar, uR + cR);
+  const R mL = rL * (sL - uL), mR = rR * (sR - uR);
+  const R ss = Prec<R>::div(pR - pL + mL * uL - mR * uR, mL - mR);
+  sstar = ss;
+  // One side's flux F_K + s_(-/+) (W*_K - W_K); at s* = 0 the mean of both.
+  R GL[NF], GR[NF];
+  const bool needL = !(ss < R(0));
+  const bool needR = !(ss > R(0));
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    if ((side == 0 && !needL) || (side == 1 && !needR)) continue;
+    const R *W = side ? WR : WL;
+    const R *v = side ? vR : vL;
+    const R p = side ? pR : pL;
+    const R rho = side ? rR : rL;
+    const R u = side ? uR : uL;
+    const R sK = side ? sR : sL;
+    const R sw = side ? fmax(R(0), sR) : fmin(R(0), sL);
+    R *Gs = side ? GR : GL;
+    const R chim1 = Prec<R>::div(ss - u, sK - ss);
+    Gs[0] = W[0] * u + sw * (chim1 * W[0]);
+    Gs[1] = W[1] * u + sw * (chim1 * W[1]);
+#pragma unroll
+    for (int j = 0; j < NDIM; ++j) {
+      const R m = W[2 + j];
+      const R dm = (j == DIR) ? rho * sK * chim1 : chim1 * (rho * v[j]);
+      Gs[2 + j] = m * u + ((j == DIR) ? p : R(0)) + sw * dm;
+    }
+    const R dE = chim1 * (W[E] + p) + (R(1) + chim1) * rho * ss * (ss - u);
+    Gs[E] = (W[E] + p) * u + sw * dE;
+    Gs[A] = W[A] * ss;
+  }
+  if (needL && needR) {
+#pragma unroll
+    for (int q = 0; q < NF; ++q) G[q] = R(0.5) * (GL[q] + GR[q]);
+  } else if (needL) {
+#pragma unroll
+    for (int q = 0; q < NF; ++q) G[q] = GL[q];
+  } else {
+#pragma unroll
+    for (int q = 0; q < NF; ++q) G[q] = GR[q];
+  }
+}
+
+// Reference node state for the deviation form (mixed path): the large
+// quantities of node i, rounded to R; they only ever multiply deviations or
+// enter quantities needed to relative precision (wave speeds, star jumps).
+template <int NDIM, class R>
+struct RefNode {
+  R r1, r2, rho, u[NDIM], p, Ep, a1;  // a1r1, a2r2, rho, velocity, p, E + p, alpha1
+};
+
+// One state K described by its deviation from the reference node:
+// (d a1r1, d a2r2, d u_1..d u_ndim, d p, d alpha1) and its sound speed.
+// HLLC flux deviation dG = G^HLLC(L, R) - G(ref) (Sec. 3.2) and s*.  The
+// physical-flux deviations F(ref + d) - F(ref) are expanded exactly, e.g.
+//   d(rho u_n^2 + p) = d rho u_n,K^2 + rho_ref d u_n (2 u_n,ref + d u_n) + d p,
+//   d((E + p) u_n)   = (dE + dp) u_n,K + (E + p)_ref d u_n,
+//   dE = dp Gamma_K + (p_ref (r1 - r2) + q1) d alpha1
+//        + (d rho |u_K|^2 + rho_ref sum_j d u_j (2 u_j,ref + d u_j)) / 2,
+// so that FP32 rounding scales with the deviations, not with |G|.
+template <int NDIM, int DIR, class R>
+__device__ __forceinline__ void hllc_dev(const RefNode<NDIM, R> &ref, const EosConst &eos, const R *dL, R cL,
+                                         const R *dR, R cR, R *dG, R &sstar) {
+  constexpr int NF = NDIM + 4, E = 2 + NDIM, A = 3 + NDIM;
+  const R *dv[2] = {dL, dR};
+  R rho[2], un[2], a1r1[2], a2r2[2], al[2], pdev[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    a1r1[k] = ref.r1 + dv[k][0];
+    a2r2[k] = ref.r2 + dv[k][1];
+    rho[k] = a1r1[k] + a2r2[k];
+    un[k] = ref.u[DIR] + dv[k][2 + DIR];
+    pdev[k] = dv[k][E];
+    al[k] = ref.a1 + dv[k][A];
+  }
+  const R cK[2] = {cL, cR};
+  const R ubar = R(0.5) * (un[0] + un[1]), cbar = R(0.5) * (cL + cR);
+  const R sL = fmin(ubar - cbar, un[0] - cL);
+  const R sR = fmax(ubar + cbar, un[1] + cR);
+  const R mL = rho[0] * (sL - un[0]), mR = rho[1] * (sR - un[1]);
+  const R ss = Prec<R>::div(pdev[1] - pdev[0] + mL * un[0] - mR * un[1], mL - mR);
+  sstar = ss;
+  R Gs[2][NF];
+  const bool need[2] = {!(ss < R(0)), !(ss > R(0))};
+  const R rdiff = (R)(eos.r1 - eos.r2), q1 = (R)eos.q1;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    if (!need[k]) continue;
+    const R *d = dv[k];
+    const R u = un[k];
+    const R sK = k ? sR : sL;
+    const R sw = k ? fmax(R(0), sR) : fmin(R(0), sL);
+    const R chim1 = Prec<R>::div(ss - u, sK - ss);
+    const R drho = d[0] + d[1];
+    // velocity of K and |u_K|^2 deviation
+    R uK[NDIM], du2 = R(0), uk2 = R(0);
+#pragma unroll
+    for (int j = 0; j < NDIM; ++j) {
+      uK[j] = ref.u[j] + d[2 + j];
+      du2 += d[2 + j] * (R(2) * ref.u[j] + d[2 + j]);
+      uk2 += uK[j] * uK[j];
+    }
+    const R GammaK = (R)eos.r2 + rdiff * al[k];
+    const R dE = d[E] * GammaK + (ref.p * rdiff + q1) * d[A] + R(0.5) * (drho * uk2 + ref.rho * du2);
+    const R EpK = ref.Ep + dE + d[E];  // (E + p)_K
+    // physical-flux deviations
+    Gs[k][0] = d[0] * u + ref.r1 * d[2 + DIR] + sw * (chim1 * a1r1[k]);
+    Gs[k][1] = d[1] * u + ref.r2 * d[2 + DIR] + sw * (chim1 * a2r2[k]);
+#pragma unroll
+    for (int j = 0; j < NDIM; ++j) {
+      R dF;
+      if (j == DIR)
+        dF = drho * u * u + ref.rho * d[2 + DIR] * (R(2) * ref.u[DIR] + d[2 + DIR]) + d[E];
+      else
+        dF = drho * uK[j] * u + ref.rho * (d[2 + j] * u + ref.u[j] * d[2 + DIR]);
+      const R dm = (j == DIR) ? rho[k] * sK * chim1 : chim1 * (rho[k] * uK[j]);
+      Gs[k][2 + j] = dF + sw * dm;
+    }
+    const R dEstar = chim1 * EpK + (R(1) + chim1) * rho[k] * ss * (ss - u);
+    Gs[k][E] = (dE + d[E]) * u + ref.Ep * d[2 + DIR] + sw * dEstar;
+    Gs[k][A] = al[k] * ss - ref.a1 * ref.u[DIR];
+  }
+  if (need[0] && need[1]) {
+#pragma unroll
+    for (int q = 0; q < NF; ++q) dG[q] = R(0.5) * (Gs[0][q] + Gs[1][q]);
+  } else {
+    const int k = need[0] ? 0 : 1;
+#pragma unroll
+    for (int q = 0; q < NF; ++q) dG[q] = Gs[k][q];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 2: mixture EOS helpers (FP64).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double mixGamma(const EosConst &e, double a1) { return fma(a1, e.r1 - e.r2, e.r2); }
+__device__ __forceinline__ double mixPi(const EosConst &e, double a1) { return a1 * e.q1; }
+// pbar = Pi (gbar - 1)/gbar = Pi / (Gamma + 1)
+__device__ __forceinline__ double mixPinf(const EosConst &e, double a1) {
+  return mixPi(e, a1) / (mixGamma(e, a1) + 1.0);
+}
+
+// rho*ctilde^2 = rho e - pbar (Sec. 5.1 helper) of a conservative state.
+template <int NDIM>
+__device__ __forceinline__ double rho_ct2(const EosConst &e, const double *W) {
+  constexpr int E = 2 + NDIM, A = 3 + NDIM;
+  const double rho = W[0] + W[1];
+  double m2 = 0.0;
+#pragma unroll
+  for (int j = 0; j < NDIM; ++j) m2 = fma(W[2 + j], W[2 + j], m2);
+  return W[E] - 0.5 * m2 / rho - mixPinf(e, W[A]);
+}
+
+// theta solving (1-theta) fA + theta fB = eps with the paper's three cases.
+__device__ __forceinline__ double lim_theta(double fA, double fB, double eps) {
+  if (fA < eps) return 0.0;
+  if (fB < eps) return (fA - eps) / (fA - fB);
+  return 1.0;
+}
+
+template <int NDIM>
+__device__ __forceinline__ double lim_quantity(const EosConst &e, const double *W, int which) {
+  constexpr int A = 3 + NDIM;
+  switch (which) {
+    case 0: return W[0];
+    case 1: return W[1];
+    case 2: return W[A];
+    case 3: return 1.0 - W[A];
+    default: return rho_ct2<NDIM>(e, W);
+  }
+}
+
+// Sec. 5.1, Algorithms 1-3 + hard switch: limit Wt toward the node state Wn.
+// Returns bit 0 = some theta < 1, bit 1 = hard switch.
+template <int NDIM>
+__device__ int interp_limit(const EosConst &e, const LimTol &t, const double *Wn, double rctn,
+                            double *Wt) {
+  constexpr int NF = NDIM + 4;
+  int flags = 0;
+#pragma unroll 1
+  for (int which = 0; which < 5; ++which) {
+    const double eps = which < 2 ? t.eps_ar : (which < 4 ? t.eps_a : t.eps_rc);
+    const double fA = which == 4 ? rctn : lim_quantity<NDIM>(e, Wn, which);
+    const double th = lim_theta(fA, lim_quantity<NDIM>(e, Wt, which), eps);
+    if (th < 1.0) {
+      flags |= 1;
+#pragma unroll
+      for (int q = 0; q < NF; ++q) Wt[q] = (1.0 - th) * Wn[q] + th * Wt[q];
+    }
+  }
+  constexpr int A = 3 + NDIM;
+  if (Wt[0] < t.hs_ar || Wt[1] < t.hs_ar || Wt[A] < t.hs_a || 1.0 - Wt[A] < t.hs_a ||
+      rho_ct2<NDIM>(e, Wt) < t.hs_rc) {
+    flags |= 2;
+#pragma unroll
+    for (int q = 0; q < NF; ++q) Wt[q] = Wn[q];
+  }
+  return flags;
+}
+
+// Sec. 5.2, Algorithms 4-6 + hard switch at one midpoint.  Gm/Gp: high-order
+// split fluxes in, limited fluxes out.  Returns bit 0 = some theta < 1,
+// bit 1 = hard switch.
+template <int NDIM>
+__device__ int flux_limit(const EosConst &e, const LimTol &t, const double *Wi, const double *Wi1,
+                          const double *Fi, const double *Fi1, const double *GHm, const double *GHp,
+                          double lam, double *Gm, double *Gp) {
+  constexpr int NF = NDIM + 4, A = 3 + NDIM;
+  const double l2 = 2.0 * lam;
+  double Ap[NF], Am[NF], Bp[NF], Bm[NF];
+#pragma unroll
+  for (int q = 0; q < NF; ++q) {
+    Ap[q] = Wi[q] - l2 * (GHm[q] - Fi[q]);
+    Am[q] = Wi1[q] + l2 * (GHp[q] - Fi1[q]);
+    Bp[q] = Wi[q] - l2 * (Gm[q] - Fi[q]);
+    Bm[q] = Wi1[q] + l2 * (Gp[q] - Fi1[q]);
+  }
+  int flags = 0;
+#pragma unroll 1
+  for (int which = 0; which < 5; ++which) {
+    const double eps = which < 2 ? t.eps_ar : (which < 4 ? t.eps_a : t.eps_rc);
+    const double thp = lim_theta(lim_quantity<NDIM>(e, Ap, which), lim_quantity<NDIM>(e, Bp, which), eps);
+    const double thm = lim_theta(lim_quantity<NDIM>(e, Am, which), lim_quantity<NDIM>(e, Bm, which), eps);
+    const double th = fmin(thp, thm);
+    if (th < 1.0) {
+      flags |= 1;
+#pragma unroll
+      for (int q = 0; q < NF; ++q) {
+        Gp[q] = (1.0 - th) * GHp[q] + th * Gp[q];
+        Gm[q] = (1.0 - th) * GHm[q] + th * Gm[q];
+        Bp[q] = Wi[q] - l2 * (Gm[q] - Fi[q]);
+        Bm[q] = Wi1[q] + l2 * (Gp[q] - Fi1[q]);
+      }
+    }
+  }
+  bool hard = false;
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const double *X = s ? Bm : Bp;
+    if (X[0] < t.hs_ar || X[1] < t.hs_ar || X[A] < t.hs_a || 1.0 - X[A] < t.hs_a ||
+        rho_ct2<NDIM>(e, X) < t.hs_rc)
+      hard = true;
+  }
+  if (hard) {
+    flags |= 2;
+#pragma unroll
+    for (int q = 0; q < NF; ++q) {
+      Gp[q] = GHp[q];
+      Gm[q] = GHm[q];
+    }
+  }
+  return flags;
+}
+
+// HCS reconstruction weights (Sec. 4.1, psi = 256/175):
+//   G^ = psi G~ - (101/420)(G_i + G_{i+1}) + (1/105)(G_{i-1} + G_{i+2})
+//        - (1/2100)(G_{i-2} + G_{i+3})
+template <class R>
+__device__ __forceinline__ R hcs(R gt, R gm2, R gm1, R g0, R gp1, R gp2, R gp3) {
+  return R(256.0 / 175.0) * gt - R(101.0 / 420.0) * (g0 + gp1) + R(1.0 / 105.0) * (gm1 + gp2) -
+         R(1.0 / 2100.0) * (gm2 + gp3);
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory layout of one tile.
+// ---------------------------------------------------------------------------
+template <int NDIM, int DIR>
+struct Smem {
+  using T = Tile<NDIM, DIR>;
+  static constexpr int NF = NDIM + 4;
+  // per node: W (NF), velocity (NDIM), p, c, rho*ctilde^2, G (NF)
+  static constexpr int NODE_DOUBLES = 2 * NF + NDIM + 3;
+  // per midpoint: shared flux components (NF-1), alpha flux of G^- and G^+
+  static constexpr int MID_DOUBLES = NF + 1;
+  static constexpr size_t BYTES = sizeof(double) * (size_t)(NODE_DOUBLES * T::NN + MID_DOUBLES * T::NM);
+  double *W, *vel, *p, *c, *rct, *G, *F, *am, *ap;
+  __device__ Smem(double *base) {
+    W = base;
+    vel = W + NF * T::NN;
+    p = vel + NDIM * T::NN;
+    c = p + T::NN;
+    rct = c + T::NN;
+    G = rct + T::NN;
+    F = G + NF * T::NN;
+    am = F + (NF - 1) * T::NM;
+    ap = am + T::NM;
+  }
+  // node slot of (line l, node s): consecutive threads get consecutive slots
+  static __device__ __forceinline__ int nslot(int l, int s) {
+    return DIR == 0 ? l * T::NS + s : s * T::TL + l;
+  }
+  static __device__ __forceinline__ int mslot(int l, int m) {
+    return DIR == 0 ? l * T::TM + m : m * T::TL + l;
+  }
+};
+
+// Line geometry of one block: base cell index and stride along DIR.
+template <int NDIM, int DIR>
+struct Lines {
+  long long base;
+  long long stride;
+  int n;
+  bool valid;
+  __device__ Lines(const SweepArgs &a, int l) {
+    using T = Tile<NDIM, DIR>;
+    const int nx = a.n[0], ny = a.n[1];
+    if (DIR == 0) {
+      int y = blockIdx.y * T::TL + l;
+      valid = y < ny;
+      y = min(y, ny - 1);
+      base = ((long long)blockIdx.z * ny + y) * nx;
+      stride = 1;
+      n = nx;
+    } else {
+      int x = blockIdx.y * T::TL + l;
+      valid = x < nx;
+      x = min(x, nx - 1);
+      if (DIR == 1) {
+        base = (long long)blockIdx.z * nx * ny + x;
+        stride = nx;
+        n = ny;
+      } else {
+        base = (long long)blockIdx.z * nx + x;
+        stride = (long long)nx * ny;
+        n = a.n[2];
+      }
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// The sweep kernel.
+// ---------------------------------------------------------------------------
+template <int NDIM, int DIR, class R>
+__global__ void __launch_bounds__(Tile<NDIM, DIR>::THREADS, 1) sweep_kernel(const SweepArgs a) {
+  using T = Tile<NDIM, DIR>;
+  using S = Smem<NDIM, DIR>;
+  constexpr int NF = NDIM + 4, E = 2 + NDIM, A = 3 + NDIM;
+  // The FP32 path works in deviation form about node i (see the file header).
+  constexpr bool DEV = sizeof(R) == 4;
+  extern __shared__ double smem_raw[];
+  if (!a.ctl->active) return;  // a finished advance: the step is a no-op
+  S sm(smem_raw);
+  const int tid = threadIdx.x;
+  const int tile0 = blockIdx.x * (T::TM - 1);  // first midpoint (= left face of cell tile0)
+  const long long N = a.ncell;
+  const EosConst eos = a.eos;
+
+  // ---- 1+2: stage nodes and node work --------------------------------------
+  for (int q = tid; q < T::NN; q += T::THREADS) {
+    const int l = DIR == 0 ? q / T::NS : q % T::TL;
+    const int s = DIR == 0 ? q % T::NS : q / T::TL;
+    const Lines<NDIM, DIR> ln(a, l);
+    const int n = ln.n;
+    int pos = tile0 - 3 + s;
+    double w[NF];
+    bool dirichlet = false, flip = false;
+    int src = pos;
+    if (pos < -3 || pos > n + 2) {
+      src = min(max(pos, 0), n - 1);  // outside every stencil: any valid cell
+    } else if (pos < 0 || pos >= n) {
+      const int kind = pos < 0 ? a.bc_lo : a.bc_hi;
+      if (kind == BC_TRANS) {
+        src = pos < 0 ? 0 : n - 1;
+      } else if (kind == BC_PERIODIC) {
+        src = ((pos % n) + n) % n;
+      } else if (kind == BC_SYMMETRY) {
+        src = pos < 0 ? -1 - pos : 2 * n - 1 - pos;
+        flip = true;
+      } else {
+        dirichlet = true;
+      }
+    }
+    if (dirichlet) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) w[f] = pos < 0 ? a.dir_lo[f] : a.dir_hi[f];
+    } else {
+      const long long idx = ln.base + (long long)src * ln.stride;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) w[f] = __ldg(a.W_in + (long long)f * N + idx);
+      if (flip) w[2 + DIR] = -w[2 + DIR];
+    }
+    // Sec. 2: p from rho e, rho c^2 = gbar (p + pbar), rho ctilde^2 = rho e - pbar.
+    const double rho = w[0] + w[1];
+    const double ir = 1.0 / rho;
+    double v[NDIM], m2 = 0.0;
+#pragma unroll
+    for (int j = 0; j < NDIM; ++j) {
+      v[j] = w[2 + j] * ir;
+      m2 = fma(w[2 + j], v[j], m2);
+    }
+    const double rhoe = w[E] - 0.5 * m2;
+    const double Gam = mixGamma(eos, w[A]);
+    const double Pi = mixPi(eos, w[A]);
+    const double iG = 1.0 / Gam;
+    const double p = (rhoe - Pi) * iG;
+    const double pbar = Pi / (Gam + 1.0);
+    const double rc2 = (1.0 + iG) * (p + pbar);
+    const double c = sqrt(rc2 * ir);
+    const double rct = rhoe - pbar;
+    const int slot = S::nslot(l, s);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) sm.W[f * T::NN + slot] = w[f];
+#pragma unroll
+    for (int j = 0; j < NDIM; ++j) sm.vel[j * T::NN + slot] = v[j];
+    sm.p[slot] = p;
+    sm.c[slot] = c;
+    sm.rct[slot] = rct;
+    const double un = v[DIR];
+    sm.G[0 * T::NN + slot] = w[0] * un;
+    sm.G[1 * T::NN + slot] = w[1] * un;
+#pragma unroll
+    for (int j = 0; j < NDIM; ++j) sm.G[(2 + j) * T::NN + slot] = w[2 + j] * un + (j == DIR ? p : 0.0);
+    sm.G[E * T::NN + slot] = (w[E] + p) * un;
+    sm.G[A * T::NN + slot] = w[A] * un;
+    // input admissibility (Sec. 2), counted once per interior cell
+    if (DIR == 0 && ln.valid && s >= 3 && s < 3 + T::TM - 1 && pos < n) {
+      const bool ok = w[0] >= 0.0 && w[1] >= 0.0 && w[A] >= 0.0 && w[A] <= 1.0 && rct > 0.0 &&
+                      isfinite(rhoe) && isfinite(c);
+      if (!ok) atomicAdd(&a.stats->inadmissible, 1ull);
+    }
+  }
+  __syncthreads();
+
+  // Directional split (Sec. 3.3): lambda_d = dt / (dx_d sigma_d) with
+  // sigma_d = tau_d / sum(tau), tau = max(|u_d| + c)/dx_d of the stage input.
+  const double dt = a.ctl->dt;
+  double lam;
+  if (NDIM == 1) {
+    lam = dt * a.inv_dx;
+  } else {
+    double tsum = 0.0;
+#pragma unroll
+    for (int j = 0; j < NDIM; ++j) tsum += __longlong_as_double(a.ctl->smax[a.stage][j]) * a.inv_dx_all[j];
+    lam = dt * tsum / __longlong_as_double(a.ctl->smax[a.stage][DIR]);
+  }
+  R epsR = (R)a.eps_is;
+  if (sizeof(R) == 4) epsR = fmax(epsR, R(1e-30));
+
+  // ---- 3: midpoint fluxes ---------------------------------------------------
+  int nlim_i = 0, nhard_i = 0, nlim_f = 0, nhard_f = 0;
+  for (int q = tid; q < T::NM; q += T::THREADS) {
+    const int l = DIR == 0 ? q / T::TM : q % T::TL;
+    const int m = DIR == 0 ? q % T::TM : q / T::TL;
+    const int si = m + 2;  // node i; node i+1 is m + 3
+    // Tiles overlap by one midpoint: count limiter events once per midpoint.
+    const int cnt = (m < T::TM - 1 || tile0 + m == Lines<NDIM, DIR>(a, l).n) &&
+                    tile0 + m <= Lines<NDIM, DIR>(a, l).n && Lines<NDIM, DIR>(a, l).valid;
+    const int ni = S::nslot(l, si), ni1 = S::nslot(l, si + 1);
+    double Wi[NF], Wi1[NF], vi[NDIM], Gi[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      Wi[f] = sm.W[f * T::NN + ni];
+      Wi1[f] = sm.W[f * T::NN + ni1];
+      Gi[f] = sm.G[f * T::NN + ni];
+    }
+#pragma unroll
+    for (int j = 0; j < NDIM; ++j) vi[j] = sm.vel[j * T::NN + ni];
+    const double pi_ = sm.p[ni];
+    const double ui = vi[DIR];
+
+    // Deviation of node (l, s) from node i in primitive variables
+    // (a1r1, a2r2, u_1..u_ndim, p, alpha1), rounded to R.
+    auto node_dev = [&](int s, R *dv) {
+      const int sl = S::nslot(l, s);
+      dv[0] = (R)(sm.W[0 * T::NN + sl] - Wi[0]);
+      dv[1] = (R)(sm.W[1 * T::NN + sl] - Wi[1]);
+#pragma unroll
+      for (int k = 0; k < NDIM; ++k) dv[2 + k] = (R)(sm.vel[k * T::NN + sl] - vi[k]);
+      dv[E] = (R)(sm.p[sl] - pi_);
+      dv[A] = (R)(sm.W[A * T::NN + sl] - Wi[A]);
+    };
+    RefNode<NDIM, R> ref;
+    if (DEV) {
+      ref.r1 = (R)Wi[0];
+      ref.r2 = (R)Wi[1];
+      ref.rho = (R)(Wi[0] + Wi[1]);
+#pragma unroll
+      for (int j = 0; j < NDIM; ++j) ref.u[j] = (R)vi[j];
+      ref.p = (R)pi_;
+      ref.Ep = (R)(Wi[E] + pi_);
+      ref.a1 = (R)Wi[A];
+    }
+
+    // First-order HLLC flux from the nodes (Sec. 3.2), in R.
+    double GH[NF], uH;
+    if (DEV) {
+      R d0[NF], d1[NF], dG[NF], ss;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) d0[f] = R(0);
+      node_dev(si + 1, d1);
+      hllc_dev<NDIM, DIR, R>(ref, eos, d0, (R)sm.c[ni], d1, (R)sm.c[ni1], dG, ss);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) GH[f] = Gi[f] + (double)dG[f];
+      uH = (double)ss;
+    } else {
+      R wl[NF], wr[NF], vl[NDIM], vr[NDIM], G[NF], ss;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        wl[f] = (R)Wi[f];
+        wr[f] = (R)Wi1[f];
+      }
+#pragma unroll
+      for (int j = 0; j < NDIM; ++j) {
+        vl[j] = (R)vi[j];
+        vr[j] = (R)sm.vel[j * T::NN + ni1];
+      }
+      hllc<NDIM, DIR, R>(wl, vl, (R)pi_, wl[0] + wl[1], (R)sm.c[ni], wr, vr, (R)sm.p[ni1], wr[0] + wr[1],
+                         (R)sm.c[ni1], G, ss);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) GH[f] = (double)G[f];
+      uH = (double)ss;
+    }
+    double GHm[NF], GHp[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) GHm[f] = GHp[f] = GH[f];
+    GHm[A] = GH[A] - Wi[A] * uH;
+    GHp[A] = GH[A] - Wi1[A] * uH;
+
+    double Gm[NF], Gp[NF];
+    if (a.scheme == SCHEME_HLLC1) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        Gm[f] = GHm[f];
+        Gp[f] = GHp[f];
+      }
+    } else {
+      // Steps 1-2: primitive deviations from node i, projected with
+      // Rinv_{i+1/2} (App. A; means of a1r1, a2r2, rho and c of nodes i, i+1).
+      const R ar1 = R(0.5) * (R)(Wi[0] + Wi1[0]);
+      const R ar2 = R(0.5) * (R)(Wi[1] + Wi1[1]);
+      const R rb = ar1 + ar2;
+      const R cb = R(0.5) * (R)(sm.c[ni] + sm.c[ni1]);
+      const R irc = Prec<R>::div(R(1), rb * cb);
+      const R k1 = ar1 * irc / cb, k2 = ar2 * irc / cb;
+      R U[6][NF];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        R dv[NF];
+        if (j == 2) {
+#pragma unroll
+          for (int f = 0; f < NF; ++f) dv[f] = R(0);
+        } else {
+          node_dev(m + j, dv);
+        }
+        U[j][0] = dv[2 + DIR] - irc * dv[E];
+        U[j][1] = dv[0] - k1 * dv[E];
+        U[j][2] = dv[1] - k2 * dv[E];
+        int row = 3;
+#pragma unroll
+        for (int k = 0; k < NDIM; ++k)
+          if (k != DIR) U[j][row++] = dv[2 + k];
+        U[j][NF - 2] = dv[A];
+        U[j][NF - 1] = dv[2 + DIR] + irc * dv[E];
+      }
+      // Step 3: left/right WCNS-IS per characteristic field.
+      R UL[NF], UR[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        UL[f] = wenois<R>(U[0][f], U[1][f], R(0), U[3][f], U[4][f], epsR);
+        UR[f] = wenois<R>(U[5][f], U[4][f], U[3][f], R(0), U[1][f], epsR);
+      }
+      // Step 4: back-project to primitive deviations.
+      R dV[2][NF];
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const R *Us = side ? UR : UL;
+        R *d = dV[side];
+        const R dac = Us[NF - 1] - Us[0];
+        d[0] = Us[1] + Prec<R>::div(ar1, R(2) * cb) * dac;
+        d[1] = Us[2] + Prec<R>::div(ar2, R(2) * cb) * dac;
+        int row = 3;
+#pragma unroll
+        for (int k = 0; k < NDIM; ++k) {
+          if (k == DIR) {
+            d[2 + k] = R(0.5) * (Us[0] + Us[NF - 1]);
+          } else {
+            d[2 + k] = Us[row];
+            ++row;
+          }
+        }
+        d[E] = R(0.5) * rb * cb * dac;
+        d[A] = Us[NF - 2];
+      }
+      // Step 5: V -> W in FP64 (node i plus deviation).
+      double WL[NF], WR[NF], VL[NF], VR[NF];  // V: (a1r1, a2r2, vel.., p, a1)
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const R *d = dV[side];
+        double *V = side ? VR : VL;
+        double *W = side ? WR : WL;
+        V[0] = Wi[0] + (double)d[0];
+        V[1] = Wi[1] + (double)d[1];
+#pragma unroll
+        for (int k = 0; k < NDIM; ++k) V[2 + k] = vi[k] + (double)d[2 + k];
+        V[E] = pi_ + (double)d[E];
+        V[A] = Wi[A] + (double)d[A];
+        const double rho = V[0] + V[1];
+        double k2s = 0.0;
+#pragma unroll
+        for (int k = 0; k < NDIM; ++k) {
+          W[2 + k] = rho * V[2 + k];
+          k2s = fma(V[2 + k], V[2 + k], k2s);
+        }
+        W[0] = V[0];
+        W[1] = V[1];
+        W[E] = fma(V[E], mixGamma(eos, V[A]), mixPi(eos, V[A])) + 0.5 * rho * k2s;
+        W[A] = V[A];
+      }
+      // Interpolation limiter (Sec. 5.1): left toward W_i, right toward W_{i+1}.
+      bool changed[2] = {false, false};
+      if (a.scheme == SCHEME_PP) {
+        const int fl = interp_limit<NDIM>(eos, a.tol, Wi, sm.rct[ni], WL);
+        const int fr = interp_limit<NDIM>(eos, a.tol, Wi1, sm.rct[ni1], WR);
+        nlim_i += cnt * ((fl & 1) + (fr & 1));
+        nhard_i += cnt * ((fl >> 1) + (fr >> 1));
+        changed[0] = fl != 0;
+        changed[1] = fr != 0;
+      }
+      // A limited state: primitive values again from its conservative vector.
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        if (!changed[side]) continue;
+        const double *W = side ? WR : WL;
+        double *V = side ? VR : VL;
+        const double rho = W[0] + W[1];
+        const double ir = 1.0 / rho;
+        double m2 = 0.0;
+#pragma unroll
+        for (int k = 0; k < NDIM; ++k) {
+          V[2 + k] = W[2 + k] * ir;
+          m2 = fma(W[2 + k], V[2 + k], m2);
+        }
+        V[0] = W[0];
+        V[1] = W[1];
+        V[E] = (W[E] - 0.5 * m2 - mixPi(eos, W[A])) / mixGamma(eos, W[A]);
+        V[A] = W[A];
+        if (DEV) {
+          R *d = dV[side];
+          d[0] = (R)(V[0] - Wi[0]);
+          d[1] = (R)(V[1] - Wi[1]);
+#pragma unroll
+          for (int k = 0; k < NDIM; ++k) d[2 + k] = (R)(V[2 + k] - vi[k]);
+          d[E] = (R)(V[E] - pi_);
+          d[A] = (R)(V[A] - Wi[A]);
+        }
+      }
+      // Step 6: midpoint HLLC (sound speeds from the mixture EOS, Sec. 2).
+      R cs[2];
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const double *V = side ? VR : VL;
+        if (DEV) {
+          const R *d = dV[side];
+          const R a1 = ref.a1 + d[A];
+          const R Gam = (R)eos.r2 + (R)(eos.r1 - eos.r2) * a1;
+          const R pb = Prec<R>::div((R)eos.q1 * a1, Gam + R(1));
+          const R rho = ref.rho + d[0] + d[1];
+          cs[side] = Prec<R>::sqrt_(Prec<R>::div((R(1) + Prec<R>::div(R(1), Gam)) * (ref.p + d[E] + pb), rho));
+        } else {
+          const double Gam = mixGamma(eos, V[A]);
+          const double pb = mixPi(eos, V[A]) / (Gam + 1.0);
+          cs[side] = (R)sqrt((1.0 + 1.0 / Gam) * (V[E] + pb) / (V[0] + V[1]));
+        }
+      }
+      // Steps 7-8: HCS reconstruction of G-hat, u-hat (node fluxes, velocities).
+      double Gh[NF], uh;
+      if (DEV) {
+        R dGt[NF], ut;
+        hllc_dev<NDIM, DIR, R>(ref, eos, dV[0], cs[0], dV[1], cs[1], dGt, ut);
+        // G^ - G_i = psi (G~ - G_i) + sum_k c_k (G_k - G_i)  (weights sum to 1)
+        const int sm2 = S::nslot(l, m), sm1 = S::nslot(l, m + 1), sp2 = S::nslot(l, m + 4),
+                  sp3 = S::nslot(l, m + 5);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          const double *g = sm.G + f * T::NN;
+          const R dh = hcs<R>(dGt[f], (R)(g[sm2] - Gi[f]), (R)(g[sm1] - Gi[f]), R(0), (R)(g[ni1] - Gi[f]),
+                              (R)(g[sp2] - Gi[f]), (R)(g[sp3] - Gi[f]));
+          Gh[f] = Gi[f] + (double)dh;
+        }
+        const double *un = sm.vel + DIR * T::NN;
+        const R duh = hcs<R>(ut - ref.u[DIR], (R)(un[sm2] - ui), (R)(un[sm1] - ui), R(0), (R)(un[ni1] - ui),
+                             (R)(un[sp2] - ui), (R)(un[sp3] - ui));
+        uh = ui + (double)duh;
+      } else {
+        R wl[NF], wr[NF], vl[NDIM], vr[NDIM], Gt[NF], ut;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          wl[f] = (R)WL[f];
+          wr[f] = (R)WR[f];
+        }
+#pragma unroll
+        for (int k = 0; k < NDIM; ++k) {
+          vl[k] = (R)VL[2 + k];
+          vr[k] = (R)VR[2 + k];
+        }
+        hllc<NDIM, DIR, R>(wl, vl, (R)VL[E], wl[0] + wl[1], cs[0], wr, vr, (R)VR[E], wr[0] + wr[1], cs[1], Gt,
+                           ut);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          const double *g = sm.G + f * T::NN;
+          Gh[f] = (double)hcs<R>(Gt[f], (R)g[S::nslot(l, m)], (R)g[S::nslot(l, m + 1)], (R)g[ni], (R)g[ni1],
+                                 (R)g[S::nslot(l, m + 4)], (R)g[S::nslot(l, m + 5)]);
+        }
+        const double *un = sm.vel + DIR * T::NN;
+        uh = (double)hcs<R>(ut, (R)un[S::nslot(l, m)], (R)un[S::nslot(l, m + 1)], (R)un[ni], (R)un[ni1],
+                            (R)un[S::nslot(l, m + 4)], (R)un[S::nslot(l, m + 5)]);
+      }
+      // Step 9: G^-_{i+1/2} and G^+_{i+1/2}.
+#pragma unroll
+      for (int f = 0; f < NF; ++f) Gm[f] = Gp[f] = Gh[f];
+      Gm[A] = Gh[A] - Wi[A] * uh;
+      Gp[A] = Gh[A] - Wi1[A] * uh;
+      // Flux limiter (Sec. 5.2).
+      if (a.scheme == SCHEME_PP) {
+        double Fi[NF], Fi1[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          Fi[f] = Gi[f];
+          Fi1[f] = sm.G[f * T::NN + ni1];
+        }
+        Fi[A] = 0.0;
+        Fi1[A] = 0.0;
+        const int fl = flux_limit<NDIM>(eos, a.tol, Wi, Wi1, Fi, Fi1, GHm, GHp, lam, Gm, Gp);
+        nlim_f += cnt * (fl & 1);
+        nhard_f += cnt * (fl >> 1);
+      }
+    }
+    const int ms = S::mslot(l, m);
+#pragma unroll
+    for (int f = 0; f < NF - 1; ++f) sm.F[f * T::NM + ms] = Gm[f];
+    sm.am[ms] = Gm[A];
+    sm.ap[ms] = Gp[A];
+  }
+  if (nlim_i) atomicAdd(&a.stats->interp_limited, (unsigned long long)nlim_i);
+  if (nhard_i) atomicAdd(&a.stats->interp_hard, (unsigned long long)nhard_i);
+  if (nlim_f) atomicAdd(&a.stats->flux_limited, (unsigned long long)nlim_f);
+  if (nhard_f) atomicAdd(&a.stats->flux_hard, (unsigned long long)nhard_f);
+  __syncthreads();
+
+  // ---- 4: cell update ------------------------------------------------------
+  double smax_local[NDIM];
+#pragma unroll
+  for (int j = 0; j < NDIM; ++j) smax_local[j] = 0.0;
+  int midpoints_done = 0;
+  for (int q = tid; q < T::TL * (T::TM - 1); q += T::THREADS) {
+    const int l = DIR == 0 ? q / (T::TM - 1) : q % T::TL;
+    const int m = DIR == 0 ? q % (T::TM - 1) : q / T::TL;
+    const Lines<NDIM, DIR> ln(a, l);
+    const int pos = tile0 + m;
+    if (!ln.valid || pos >= ln.n) continue;
+    ++midpoints_done;
+    const long long idx = ln.base + (long long)pos * ln.stride;
+    const int ml = S::mslot(l, m), mr = S::mslot(l, m + 1);
+    double upd[NF];
+#pragma unroll
+    for (int f = 0; f < NF - 1; ++f) upd[f] = (sm.F[f * T::NM + ml] - sm.F[f * T::NM + mr]) * a.inv_dx;
+    upd[A] = (sm.ap[ml] - sm.am[mr]) * a.inv_dx;
+    if (a.epilogue == EPI_WRITE) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) a.L[(long long)f * N + idx] = upd[f];
+    } else if (a.epilogue == EPI_ACCUM) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) a.L[(long long)f * N + idx] += upd[f];
+    } else {
+      const int ns = S::nslot(l, m + 3);
+      double w[NF];
+      bool finite = true;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const double tot = a.read_L ? a.L[(long long)f * N + idx] + upd[f] : upd[f];
+        const double wn = a.rk_a != 0.0 ? a.Wn[(long long)f * N + idx] : 0.0;
+        w[f] = a.rk_a * wn + a.rk_b * (sm.W[f * T::NN + ns] + dt * tot);
+        finite = finite && isfinite(w[f]);
+        a.W_out[(long long)f * N + idx] = w[f];
+      }
+      if (!finite) atomicAdd(&a.stats->nonfinite, 1ull);
+      // max(|u_d| + c) of the new state (Sec. 3.3) for the next stage
+      const double rho = w[0] + w[1];
+      const double ir = 1.0 / rho;
+      double m2 = 0.0;
+#pragma unroll
+      for (int j = 0; j < NDIM; ++j) m2 = fma(w[2 + j], w[2 + j], m2);
+      const double rhoe = w[E] - 0.5 * m2 * ir;
+      const double Gam = mixGamma(eos, w[A]);
+      const double iG = 1.0 / Gam;
+      const double pb = mixPi(eos, w[A]) / (Gam + 1.0);
+      // rho c^2 = gbar (gbar - 1)(rho e - pbar), gbar - 1 = 1/Gamma
+      const double c = sqrt((1.0 + iG) * iG * (rhoe - pb) * ir);
+#pragma unroll
+      for (int j = 0; j < NDIM; ++j) {
+        const double sj = fabs(w[2 + j] * ir) + c;
+        smax_local[j] = (sj > smax_local[j] || sj != sj) ? sj : smax_local[j];
+      }
+    }
+  }
+  if (a.epilogue == EPI_COMBINE && a.ctl) {
+#pragma unroll
+    for (int j = 0; j < NDIM; ++j) {
+      unsigned long long b = __double_as_longlong(smax_local[j]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ob = __shfl_xor_sync(0xffffffffu, b, o);
+        b = ob > b ? ob : b;
+      }
+      if ((tid & 31) == 0 && b) atomicMax(&a.ctl->smax[a.stage + 1][j], b);
+    }
+  }
+  // midpoint count (one per cell updated)
+  for (int o = 16; o > 0; o >>= 1) midpoints_done += __shfl_xor_sync(0xffffffffu, midpoints_done, o);
+  if ((tid & 31) == 0 && midpoints_done) atomicAdd(&a.stats->midpoints, (unsigned long long)midpoints_done);
+}
+
+// Launch one sweep: grid = (tiles along DIR, line blocks, third axis).
+template <int NDIM, int DIR, class R>
+cudaError_t launch_sweep_t(const SweepArgs &a, cudaStream_t st) {
+  using T = Tile<NDIM, DIR>;
+  const size_t bytes = Smem<NDIM, DIR>::BYTES;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<NDIM, DIR, R>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const int nd = a.n[DIR];
+  dim3 grid((nd + T::TM - 2) / (T::TM - 1), 1, 1);
+  if (DIR == 0) {
+    grid.y = (a.n[1] + T::TL - 1) / T::TL;
+    grid.z = a.n[2];
+  } else {
+    grid.y = (a.n[0] + T::TL - 1) / T::TL;
+    grid.z = DIR == 1 ? a.n[2] : a.n[1];
+  }
+  sweep_kernel<NDIM, DIR, R><<<grid, T::THREADS, bytes, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_sweep_any(int ndim, int dir, const SweepArgs &a, cudaStream_t s) {
+  switch (ndim * 4 + dir) {
+    case 4: return launch_sweep_t<1, 0, R>(a, s);
+    case 8: return launch_sweep_t<2, 0, R>(a, s);
+    case 9: return launch_sweep_t<2, 1, R>(a, s);
+    case 12: return launch_sweep_t<3, 0, R>(a, s);
+    case 13: return launch_sweep_t<3, 1, R>(a, s);
+    case 14: return launch_sweep_t<3, 2, R>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace wcns
