@@ -1,0 +1,404 @@
+"""Benchmark: cell-stage updates/s of the PP-WCNS-IS solver on one GB300.
+
+Workload: the 2D shock / air-bubble interaction in water on a 1024 x 512
+grid ([0,2] x [0,1], symmetry at y = 0, transmissive elsewhere), FP64, with
+SSPRK3 steps at CFL 0.5.  One bench step is one SSPRK3 step (three RHS
+evaluations, i.e. 3 x 524,288 cell-stage updates, all directions fused per
+stage).  Inputs are synthetic and seeded (paper_2102_05287_gb300.problems).
+
+Arms:
+  default           this library (FP64 headline, mixed FP32/FP64 variant)
+  --impl reference  the FP64 C++ oracle on the host cores (a deliberately
+                    slow, plain reference; bounded sample of the same
+                    workload)
+
+Multi-GPU (torchrun, one rank per GPU): independent replicas of the
+workload, one per rank (weak scaling; no data-path collective).  Rank 0
+prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-stage updates/s per GB300 (FP64 vs mixed) at stated error; % of stencil roofline"
+UNIT = "cell-stage updates/s"
+WORKLOAD = "shock_bubble_2d_1024x512"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--nx", type=int, default=1024)
+    ap.add_argument("--ny", type=int, default=512)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "gb300" else "gloo"
+        if args.impl == "gb300":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier_and_max(world, value):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline inputs
+# ---------------------------------------------------------------------------
+def load_peaks():
+    """Vector-pipe peaks: measured FP64/FP32 FMA and division/sqrt rates of
+    this GPU (csrc/peaks.cu, run live), HBM copy from MEASURED_PEAKS.json
+    when present."""
+    out = {}
+    exe = os.path.join(ROOT, "paper_2102_05287_gb300", "_build", "peaks")
+    try:
+        r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+        out.update(json.loads(r.stdout.strip().splitlines()[-1]))
+        out["source"] = "measured live (csrc/peaks.cu)"
+    except Exception as e:  # keep the bench running
+        out["error"] = "peaks microbenchmark failed: %s" % e
+    mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(mp):
+        try:
+            out["measured_peaks_json"] = json.load(open(mp))
+        except Exception:
+            pass
+    return out
+
+
+def algorithmic_ops(nx, ny):
+    """Per-cell, per-direction operation mix of one RHS evaluation, from the
+    oracle's op-counting build on a 1/8-resolution copy of the workload
+    (the mix is per cell; limiters idle on the initial state either way)."""
+    from oracle import Oracle
+    from paper_2102_05287_gb300 import problems as P
+    pr = P.shock_bubble_2d(max(nx // 8, 16), max(ny // 8, 8))
+    o = Oracle(pr.n, pr.lo, pr.hi, pr.bcs, counting=True, **pr.eos)
+    sm = o.max_wavespeed(pr.W)
+    dt = 0.5 / (sm[0] * pr.n[0] / 2.0 + sm[1] * pr.n[1])
+    o.opcount_reset()
+    o.rhs(pr.W, dt)
+    c = o.opcount()
+    units = pr.ncells * pr.ndim  # cell-direction updates
+    return {k: v / units for k, v in c.items()}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from oracle import Oracle
+    from paper_2102_05287_gb300 import problems as P
+    pr = P.shock_bubble_2d(args.nx, args.ny)
+    o = Oracle(pr.n, pr.lo, pr.hi, pr.bcs, **pr.eos)
+    W = pr.W
+    for _ in range(min(args.warmup, 1)):
+        o.rhs(W, 1e-9)
+    # each timed step is one SSPRK3 step of the full workload (3 RHS)
+    steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        sm = o.max_wavespeed(W)
+        dt = 0.5 / (sm[0] * pr.n[0] / 2.0 + sm[1] * pr.n[1])
+        W = o.rk3_step(W, dt)
+    el = time.perf_counter() - t0
+    value = 3 * pr.ncells * steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": steps, "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * el / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [pr.n[0], pr.n[1]], "precision": "fp64",
+                   "step": "one SSPRK3 step (3 RHS evaluations)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d SSPRK3 steps of the full %dx%d workload, single thread" %
+                                   (steps, pr.n[0], pr.n[1])},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(nx, ny):
+    from oracle import Oracle
+    from paper_2102_05287_gb300 import problems as P
+    pr = P.shock_bubble_2d(nx, ny)
+    o = Oracle(pr.n, pr.lo, pr.hi, pr.bcs, **pr.eos)
+    W = pr.W
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        sm = o.max_wavespeed(W)
+        dt = 0.5 / (sm[0] * pr.n[0] / 2.0 + sm[1] * pr.n[1])
+        W = o.rk3_step(W, dt)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > 10.0 or steps >= 5:
+            break
+    return {"value": 3 * pr.ncells * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d SSPRK3 steps of the full %dx%d workload, single thread, %.1f s" %
+                      (steps, pr.n[0], pr.n[1], el)}
+
+
+# ---------------------------------------------------------------------------
+# this library
+# ---------------------------------------------------------------------------
+def timed_steps(torch, solver, W, steps, flush):
+    """Per-step device time with CUDA events on the solver's stream; the L2
+    is flushed (a 256 MiB write) between steps, outside the events."""
+    stream = solver.stream
+    times = []
+    launches0 = solver.launches()
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solver.advance_steps(W, 1, cfl=0.5)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return times, solver.launches() - launches0
+
+
+def run_gb300(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2102_05287_gb300 import problems as P
+    from paper_2102_05287_gb300.wcns import Solver
+
+    torch.cuda.set_device(local)
+    pr = P.shock_bubble_2d(args.nx, args.ny, seed=1 + rank)
+    ncell = pr.ncells
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    # ---------------- FP64 (the workload's precision) -----------------------
+    s64 = Solver(pr.n, pr.lo, pr.hi, pr.bcs, precision="fp64", stream=stream, **pr.eos)
+    W64 = torch.from_numpy(pr.W).cuda()
+    for _ in range(args.warmup):
+        s64.advance_steps(W64, 1, cfl=0.5)
+    torch.cuda.synchronize()
+    s64.profile_enable(16 * args.steps + 16)
+    s64.profile_read()
+    barrier(world)
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with ClockSampler(local) as clk:
+        times64, launches = timed_steps(torch, s64, W64, args.steps, flush)
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - wall0
+    prof = s64.profile_read()
+    clocks = clk.summary()
+    ms64 = barrier_and_max(world, sum(times64)) / args.steps
+    value = world * 3 * ncell / (ms64 * 1e-3)
+    stats64 = s64.stats()
+
+    # ---------------- mixed FP32/FP64 variant -------------------------------
+    mixed = None
+    if not args.no_mixed:
+        sm_ = Solver(pr.n, pr.lo, pr.hi, pr.bcs, precision="mixed", stream=stream, **pr.eos)
+        Wm = torch.from_numpy(pr.W).cuda()
+        for _ in range(args.warmup):
+            sm_.advance_steps(Wm, 1, cfl=0.5)
+        torch.cuda.synchronize()
+        tm, _ = timed_steps(torch, sm_, Wm, args.steps, flush)
+        msm = barrier_and_max(world, sum(tm)) / args.steps
+        # error of the mixed run against the FP64 run after the same steps
+        a, b = Wm.double(), W64
+        rho_m, rho_d = a[0] + a[1], b[0] + b[1]
+        l1 = lambda x, y: float((x - y).abs().sum() / y.abs().sum())
+        linf = lambda x, y: float((x - y).abs().max() / y.abs().max())
+        mixed = {"value": world * 3 * ncell / (msm * 1e-3), "ms_per_step": msm,
+                 "speedup_vs_fp64": ms64 / msm,
+                 "error_vs_fp64_after_steps": {
+                     "steps": args.warmup + args.steps,
+                     "l1_rel": {"rho": l1(rho_m, rho_d), "E": l1(a[4], b[4]), "alpha1": l1(a[5], b[5])},
+                     "linf_rel": {"rho": linf(rho_m, rho_d), "E": linf(a[4], b[4]), "alpha1": linf(a[5], b[5])}},
+                 "stats": sm_.stats()}
+        sm_.close()
+
+    # ---------------- end to end through the host-buffer entry point --------
+    Wh = torch.from_numpy(pr.W).pin_memory()
+    s64.advance_steps_host(Wh, 1, cfl=0.5)
+    e2e_steps = max(2, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s64.advance_steps_host(Wh, 1, cfl=0.5)
+    e2e_el = barrier_and_max(world, time.perf_counter() - t0)
+    nbytes = Wh.numel() * 8
+    e2e = {"value": world * 3 * ncell * e2e_steps / e2e_el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes, "steps": e2e_steps,
+           "note": "wcns_advance_steps_host: pinned host state copied in, one SSPRK3 step, copied out"}
+
+    if rank != 0:
+        s64.close()
+        return
+
+    # ---------------- roofline of the dominant kernel -----------------------
+    peaks = load_peaks()
+    ops = algorithmic_ops(args.nx, args.ny)
+    dirs = [d for d in range(2) if prof["launches"][d] > 0]
+    dom = max(dirs, key=lambda d: prof["ms"][d])
+    avg_ms = prof["ms"][dom] / prof["launches"][dom]
+    p64 = peaks.get("fp64_fma_tflops", 1.25)
+    div_eq = (p64 * 1e12) / (peaks.get("fp64_div_gops", 67.0) * 1e9)
+    sqrt_eq = (p64 * 1e12) / (peaks.get("fp64_sqrt_gops", 58.5) * 1e9)
+    flop_eq = ops["add"] + ops["mul"] + ops["minmax"] + div_eq * ops["div"] + sqrt_eq * ops["sqrt"]
+    achieved = flop_eq * ncell / (avg_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": p64, "unit": "TFLOP/s", "frac": achieved / p64,
+                "traffic": None,
+                "kernel": "sweep_kernel<2,%d,double> (%s sweep)" % (dom, "xy"[dom]),
+                "avg_launch_ms": avg_ms,
+                "flop_eq_per_cell_dir": flop_eq,
+                "ops_per_cell_dir": ops,
+                "peak_source": peaks.get("source", "nominal FP64 1.25 TFLOP/s (fallback)"),
+                "note": "FP64-pipe roofline: add/mul/minmax count 1 flop, div/sqrt count their measured "
+                        "cost in FMA-flop equivalents; peak = measured FP64 FMA rate of this GPU"}
+    traffic_file = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+    if os.path.exists(traffic_file):
+        try:
+            tr = json.load(open(traffic_file))
+            k = "fp64_dir%d" % dom
+            if k in tr and tr[k].get("grid") == [args.nx, args.ny]:
+                roofline["traffic"] = tr[k]["bytes_per_launch"]
+        except Exception:
+            pass
+    cpu = None if args.no_cpu_baseline else cpu_baseline(args.nx, args.ny)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [args.nx, args.ny], "cells": ncell, "precision": "fp64",
+                   "scheme": "PP-WCNS-IS + SSPRK3, CFL 0.5",
+                   "step": "one SSPRK3 step = 3 RHS evaluations (x and y sweeps fused with the stage combine)",
+                   "l2": "flushed between timed steps (256 MiB write outside the timed events)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "wall_s_timed_region": wall,
+        "variants": {"mixed": mixed} if mixed else {},
+        "stats_fp64": stats64,
+        "peaks": {k: peaks.get(k) for k in ("fp64_fma_tflops", "fp32_fma_tflops", "fp64_div_gops",
+                                           "fp64_sqrt_gops", "fp64_copy_gbs", "device")},
+    }
+    print(json.dumps(line), flush=True)
+    s64.close()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_gb300(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -169,6 +169,21 @@ long long wcns_ncells(const wcns_handle *h);
 /* Kernel launches issued by this handle since creation (host-side count). */
 long long wcns_launch_count(const wcns_handle *h);
 
+/* Per-kernel timing (tracing aid, not part of the method).  When enabled,
+ * every directional sweep launch is bracketed by CUDA events on the
+ * handle's stream; wcns_profile_read synchronises, sums the durations per
+ * sweep direction since the previous read, and clears them.  capacity is
+ * the number of launches that can be recorded between reads (events are
+ * created here, once); 0 disables.  Returns WCNS_E_CUDA if the events
+ * cannot be created. */
+typedef struct {
+  long long launches[3];  /* sweep launches per direction x, y, z */
+  double ms[3];           /* summed device time per direction, milliseconds */
+  long long dropped;      /* launches beyond capacity, not timed */
+} wcns_profile;
+int wcns_profile_enable(wcns_handle *h, int capacity);
+int wcns_profile_read(wcns_handle *h, wcns_profile *out);
+
 const char *wcns_strerror(int status);
 void wcns_destroy(wcns_handle *h);
 

@@ -25,6 +25,11 @@ struct wcns_handle {
   StepCtl *ctl;
   DevStats *stats;
   long long launches;
+  // per-kernel timing
+  int prof_cap, prof_n;
+  long long prof_dropped;
+  cudaEvent_t *prof_ev;  // 2 * prof_cap events
+  int *prof_dir;
 };
 
 namespace {
@@ -179,10 +184,33 @@ SweepArgs base_args(wcns_handle *h, int d) {
 }
 
 int launch_sweep(wcns_handle *h, int d, const SweepArgs &a) {
+  int slot = -1;
+  if (h->prof_cap > 0) {
+    if (h->prof_n < h->prof_cap) {
+      slot = h->prof_n++;
+      h->prof_dir[slot] = d;
+      cudaEventRecord(h->prof_ev[2 * slot], h->stream);
+    } else {
+      h->prof_dropped++;
+    }
+  }
   cudaError_t e = h->opt.precision == WCNS_MIXED ? launch_sweep_mixed(h->ndim, d, a, h->stream)
                                                  : launch_sweep_fp64(h->ndim, d, a, h->stream);
+  if (slot >= 0) cudaEventRecord(h->prof_ev[2 * slot + 1], h->stream);
   h->launches++;
   return cuda_status(e);
+}
+
+void profile_free(wcns_handle *h) {
+  if (h->prof_ev) {
+    for (int k = 0; k < 2 * h->prof_cap; ++k) cudaEventDestroy(h->prof_ev[k]);
+    free(h->prof_ev);
+    free(h->prof_dir);
+  }
+  h->prof_ev = NULL;
+  h->prof_dir = NULL;
+  h->prof_cap = h->prof_n = 0;
+  h->prof_dropped = 0;
 }
 
 // dW/dt of W into L for every direction (stage 0 lambda).
@@ -445,6 +473,47 @@ int wcns_reset_stats(wcns_handle *h) {
   return WCNS_OK;
 }
 
+int wcns_profile_enable(wcns_handle *h, int capacity) {
+  if (!h || capacity < 0) return WCNS_E_INVALID_ARG;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  profile_free(h);
+  if (capacity == 0) return WCNS_OK;
+  h->prof_ev = (cudaEvent_t *)calloc(2 * (size_t)capacity, sizeof(cudaEvent_t));
+  h->prof_dir = (int *)calloc((size_t)capacity, sizeof(int));
+  if (!h->prof_ev || !h->prof_dir) {
+    free(h->prof_ev);
+    free(h->prof_dir);
+    h->prof_ev = NULL;
+    h->prof_dir = NULL;
+    return WCNS_E_INVALID_ARG;
+  }
+  for (int k = 0; k < 2 * capacity; ++k) {
+    if (cudaEventCreate(&h->prof_ev[k]) != cudaSuccess) {
+      h->prof_cap = k / 2;
+      profile_free(h);
+      return WCNS_E_CUDA;
+    }
+  }
+  h->prof_cap = capacity;
+  return WCNS_OK;
+}
+
+int wcns_profile_read(wcns_handle *h, wcns_profile *out) {
+  if (!h || !out) return WCNS_E_INVALID_ARG;
+  memset(out, 0, sizeof(*out));
+  CK(cudaStreamSynchronize(h->stream));
+  for (int k = 0; k < h->prof_n; ++k) {
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, h->prof_ev[2 * k], h->prof_ev[2 * k + 1]));
+    out->launches[h->prof_dir[k]] += 1;
+    out->ms[h->prof_dir[k]] += ms;
+  }
+  out->dropped = h->prof_dropped;
+  h->prof_n = 0;
+  h->prof_dropped = 0;
+  return WCNS_OK;
+}
+
 int wcns_nfields(const wcns_handle *h) { return h ? h->nf : 0; }
 long long wcns_ncells(const wcns_handle *h) { return h ? h->N : 0; }
 long long wcns_launch_count(const wcns_handle *h) { return h ? h->launches : 0; }
@@ -465,6 +534,7 @@ const char *wcns_strerror(int s) {
 void wcns_destroy(wcns_handle *h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  profile_free(h);
   cudaFree(h->W1);
   cudaFree(h->W2);
   cudaFree(h->L);

@@ -27,7 +27,7 @@ EXPORTS = [
     "wcns_create", "wcns_default_options", "wcns_set_options", "wcns_get_options", "wcns_rhs",
     "wcns_max_wavespeed", "wcns_rk3_step", "wcns_advance_steps", "wcns_advance_to",
     "wcns_advance_steps_host", "wcns_get_stats", "wcns_reset_stats", "wcns_nfields", "wcns_ncells",
-    "wcns_launch_count", "wcns_strerror", "wcns_destroy", "wcns_batch_create", "wcns_batch_set_options",
+    "wcns_launch_count", "wcns_profile_enable", "wcns_profile_read", "wcns_strerror", "wcns_destroy", "wcns_batch_create", "wcns_batch_set_options",
     "wcns_batch_advance", "wcns_batch_get_stats", "wcns_batch_total_cells", "wcns_batch_launch_count",
     "wcns_batch_destroy",
 ]
@@ -54,6 +54,10 @@ class wcns_stats(C.Structure):
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class wcns_profile(C.Structure):
+    _fields_ = [("launches", C.c_longlong * 3), ("ms", C.c_double * 3), ("dropped", C.c_longlong)]
 
 
 class WcnsError(RuntimeError):
@@ -91,6 +95,8 @@ def load(path=LIB_PATH):
         "wcns_nfields": ([vp], i),
         "wcns_ncells": ([vp], ll),
         "wcns_launch_count": ([vp], ll),
+        "wcns_profile_enable": ([vp, i], i),
+        "wcns_profile_read": ([vp, P(wcns_profile)], i),
         "wcns_strerror": ([i], C.c_char_p),
         "wcns_destroy": ([vp], None),
         "wcns_batch_create": ([i, P(i), P(d), P(d), i, i, d, d, d, P(vp)], i),
@@ -253,6 +259,14 @@ class Solver:
 
     def launches(self):
         return int(self.lib.wcns_launch_count(self.h))
+
+    def profile_enable(self, capacity=4096):
+        _check(self.lib.wcns_profile_enable(self.h, int(capacity)), "wcns_profile_enable")
+
+    def profile_read(self):
+        p = wcns_profile()
+        _check(self.lib.wcns_profile_read(self.h, C.byref(p)), "wcns_profile_read")
+        return {"launches": list(p.launches), "ms": list(p.ms), "dropped": int(p.dropped)}
 
 
 class Batch:
