@@ -44,7 +44,8 @@ enum {
   WCNS_E_INADMISSIBLE = 3,  /* input state outside the admissible set G (Sec. 2) */
   WCNS_E_NONFINITE = 4,     /* a non-finite value appeared */
   WCNS_E_TIMEOUT = 5,       /* a bounded device wait gave up */
-  WCNS_E_UNSUPPORTED = 6    /* option combination not provided */
+  WCNS_E_UNSUPPORTED = 6,   /* option combination not provided */
+  WCNS_E_TOO_LARGE = 7      /* problem exceeds the fixed no-allocation scratch */
 };
 
 /* Boundary conditions per face (three ghost layers, Sec. 6 "extrapolation"):
@@ -168,6 +169,32 @@ long long wcns_ncells(const wcns_handle *h);
 
 /* Kernel launches issued by this handle since creation (host-side count). */
 long long wcns_launch_count(const wcns_handle *h);
+
+/* One SSPRK3 step that allocates nothing (the paper has no counterpart:
+ * this is a deployment aid).  Some callers cannot call cudaMalloc: code
+ * that runs while a CUDA graph is being captured, real-time loops where an
+ * allocation would synchronise the device, and hosts that hand a plugin a
+ * fixed device-memory budget and forbid it to allocate more.  This entry
+ * point takes the grid, boundary set, fluids and options directly (no
+ * handle) and advances the caller's device array W in place by one step
+ * of size dt, exactly like wcns_rk3_step.  Its scratch (two stage states,
+ * the RHS accumulator, step control and counters) lives in one
+ * file-scope device array of WCNS_NOALLOC_MAX_DOUBLES doubles (64 MiB)
+ * that every GPU loading the library holds until the process exits; a
+ * problem needs 3 * nf * ncells doubles of it (up to 559,240 cells in 1D,
+ * 466,033 in 2D, 399,457 in 3D) and larger ones are rejected with
+ * WCNS_E_TOO_LARGE before any GPU work.
+ * The first call on a device looks the array's device address up once
+ * (cudaGetSymbolAddress with that device current); make that first call
+ * before any stream capture.  Every call shares the one array and finds
+ * the previous call's contents there: the counters are cleared on entry,
+ * the rest is overwritten before it is read.  Calls whose work overlaps on
+ * the GPU (other streams, other host threads) race on the array and must
+ * be serialised by the caller.  opt may be NULL (defaults).  Asynchronous
+ * on opt->stream. */
+#define WCNS_NOALLOC_MAX_DOUBLES (8ll * 1024 * 1024)
+int wcns_rk3_step_noalloc(const wcns_grid *grid, const wcns_bcs *bcs, double gamma_g, double gamma_l,
+                          double pinf_l, const wcns_options *opt, double *W, double dt);
 
 /* Per-kernel timing (tracing aid, not part of the method).  When enabled,
  * every directional sweep launch is bracketed by CUDA events on the

@@ -527,6 +527,9 @@ const char *wcns_strerror(int s) {
     case WCNS_E_NONFINITE: return "non-finite value";
     case WCNS_E_TIMEOUT: return "bounded device wait timed out";
     case WCNS_E_UNSUPPORTED: return "unsupported option combination";
+    case WCNS_E_TOO_LARGE:
+      return "problem too large for the fixed no-allocation scratch (needs 3 * nf * ncells <= "
+             "WCNS_NOALLOC_MAX_DOUBLES doubles)";
     default: return "unknown status";
   }
 }
@@ -545,3 +548,112 @@ void wcns_destroy(wcns_handle *h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free SSPRK3 step.  Its scratch is one file-scope device array:
+//   [ W1 | W2 | L ]  (3 * nf * ncells doubles)  followed by  StepCtl, DevStats
+// in a separate small region.  Host code must not pass the array's name to
+// a kernel (in host code it is a host-side stand-in, not a device address):
+// its device address is looked up once per device with cudaGetSymbolAddress.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+static __device__ __align__(256) double g_noalloc_states[WCNS_NOALLOC_MAX_DOUBLES];
+static __device__ __align__(256) unsigned char g_noalloc_ctl[512];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double *g_noalloc_states_ptr[kMaxDevices];
+unsigned char *g_noalloc_ctl_ptr[kMaxDevices];
+
+// Once per device, with that device current.
+int noalloc_setup(int dev, double **states, unsigned char **ctl) {
+  if (dev < 0 || dev >= kMaxDevices) return WCNS_E_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_states_ptr[dev]) {
+    void *p = NULL, *q = NULL;
+    if (cudaGetSymbolAddress(&p, g_noalloc_states) != cudaSuccess) return WCNS_E_CUDA;
+    if (cudaGetSymbolAddress(&q, g_noalloc_ctl) != cudaSuccess) return WCNS_E_CUDA;
+    g_noalloc_states_ptr[dev] = (double *)p;
+    g_noalloc_ctl_ptr[dev] = (unsigned char *)q;
+  }
+  *states = g_noalloc_states_ptr[dev];
+  *ctl = g_noalloc_ctl_ptr[dev];
+  return WCNS_OK;
+}
+static_assert(sizeof(StepCtl) + sizeof(DevStats) + 16 <= 512, "control region too small");
+}  // namespace
+
+extern "C" int wcns_rk3_step_noalloc(const wcns_grid *g, const wcns_bcs *bcs, double gamma_g, double gamma_l,
+                                     double pinf_l, const wcns_options *opt, double *W, double dt) {
+  if (!g || !bcs || !W || !(dt > 0.0) || !isfinite(dt)) return WCNS_E_INVALID_ARG;
+  // Same validation as wcns_create, on a handle that lives on the stack.
+  if (g->ndim < 1 || g->ndim > 3) return WCNS_E_INVALID_ARG;
+  if (!(gamma_g > 1.0) || !(gamma_l > 1.0) || !(pinf_l >= 0.0) || !(gamma_g <= gamma_l) ||
+      !isfinite(gamma_g) || !isfinite(gamma_l) || !isfinite(pinf_l))
+    return WCNS_E_INVALID_ARG;
+  long long N = 1;
+  for (int d = 0; d < g->ndim; ++d) {
+    if (g->n[d] < 1 || !(g->hi[d] > g->lo[d]) || !isfinite(g->hi[d] - g->lo[d])) return WCNS_E_INVALID_ARG;
+    for (int s2 = 0; s2 < 2; ++s2)
+      if (!valid_bc(bcs->kind[d][s2])) return WCNS_E_INVALID_ARG;
+    if ((bcs->kind[d][0] == WCNS_BC_PERIODIC) != (bcs->kind[d][1] == WCNS_BC_PERIODIC)) return WCNS_E_INVALID_ARG;
+    if ((bcs->kind[d][0] == WCNS_BC_SYMMETRY || bcs->kind[d][1] == WCNS_BC_SYMMETRY) && g->n[d] < 3)
+      return WCNS_E_INVALID_ARG;
+    N *= g->n[d];
+    if (N > (1ll << 40)) return WCNS_E_TOO_LARGE;
+  }
+  {
+    const long long ny = g->ndim > 1 ? g->n[1] : 1, nz = g->ndim > 2 ? g->n[2] : 1;
+    if ((ny + 1) / 2 > 65535 || nz > 65535 || (g->ndim > 2 && ny > 65535) || ((long long)g->n[0] + 31) / 32 > 65535)
+      return WCNS_E_INVALID_ARG;
+  }
+  const int nf = g->ndim + 4;
+  if (3ll * nf * N > WCNS_NOALLOC_MAX_DOUBLES) return WCNS_E_TOO_LARGE;
+  wcns_options o;
+  wcns_default_options(&o);
+  if (opt) o = *opt;
+  if (o.precision != WCNS_FP64 && o.precision != WCNS_MIXED) return WCNS_E_INVALID_ARG;
+  if (o.scheme < 0 || o.scheme > 2) return WCNS_E_INVALID_ARG;
+  if (!(o.eps_is > 0.0)) return WCNS_E_INVALID_ARG;
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return WCNS_E_CUDA;
+  double *states = NULL;
+  unsigned char *ctlmem = NULL;
+  int st = noalloc_setup(dev, &states, &ctlmem);
+  if (st) return st;
+
+  wcns_handle h;
+  memset(&h, 0, sizeof(h));
+  h.ndim = g->ndim;
+  h.nf = nf;
+  h.N = N;
+  for (int d = 0; d < 3; ++d) {
+    h.n[d] = d < g->ndim ? g->n[d] : 1;
+    h.dx[d] = d < g->ndim ? (g->hi[d] - g->lo[d]) / g->n[d] : 1.0;
+    h.inv_dx[d] = d < g->ndim ? 1.0 / h.dx[d] : 0.0;
+    for (int s2 = 0; s2 < 2; ++s2) {
+      h.bc[d][s2] = d < g->ndim ? bcs->kind[d][s2] : WCNS_BC_TRANSMISSIVE;
+      for (int q = 0; q < 7; ++q) h.dirichlet[d][s2][q] = bcs->dirichlet[d][s2][q];
+    }
+  }
+  h.eos.r1 = 1.0 / (gamma_l - 1.0);
+  h.eos.r2 = 1.0 / (gamma_g - 1.0);
+  h.eos.q1 = gamma_l * pinf_l / (gamma_l - 1.0);
+  h.opt = o;
+  h.stream = (cudaStream_t)o.stream;
+  const size_t M = (size_t)nf * (size_t)N;
+  h.W1 = states;
+  h.W2 = states + M;
+  h.L = states + 2 * M;
+  h.ctl = (StepCtl *)ctlmem;
+  h.stats = (DevStats *)(ctlmem + ((sizeof(StepCtl) + 15) / 16) * 16);
+  // The counters keep the previous call's values: clear them.
+  if (cudaMemsetAsync(h.stats, 0, sizeof(DevStats), h.stream) != cudaSuccess) return WCNS_E_CUDA;
+  st = launch_init(&h, 0.0, INFINITY);
+  if (!st && h.ndim > 1) st = launch_reduce(&h, W, 3);
+  if (!st) st = enqueue_step(&h, W, dt, 0.0);
+  return st;
+}

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libwcns.so")
 
 WCNS_OK, WCNS_E_INVALID_ARG, WCNS_E_CUDA, WCNS_E_INADMISSIBLE, WCNS_E_NONFINITE, WCNS_E_TIMEOUT, \
-    WCNS_E_UNSUPPORTED = range(7)
+    WCNS_E_UNSUPPORTED, WCNS_E_TOO_LARGE = range(8)
 WCNS_BC_TRANSMISSIVE, WCNS_BC_PERIODIC, WCNS_BC_SYMMETRY, WCNS_BC_DIRICHLET = range(4)
 WCNS_FP64, WCNS_MIXED = 0, 1
 WCNS_SCHEME_PP_WCNS_IS, WCNS_SCHEME_HLLC1, WCNS_SCHEME_WCNS_IS = 0, 1, 2
@@ -27,7 +27,7 @@ EXPORTS = [
     "wcns_create", "wcns_default_options", "wcns_set_options", "wcns_get_options", "wcns_rhs",
     "wcns_max_wavespeed", "wcns_rk3_step", "wcns_advance_steps", "wcns_advance_to",
     "wcns_advance_steps_host", "wcns_get_stats", "wcns_reset_stats", "wcns_nfields", "wcns_ncells",
-    "wcns_launch_count", "wcns_profile_enable", "wcns_profile_read", "wcns_strerror", "wcns_destroy", "wcns_batch_create", "wcns_batch_set_options",
+    "wcns_launch_count", "wcns_rk3_step_noalloc", "wcns_profile_enable", "wcns_profile_read", "wcns_strerror", "wcns_destroy", "wcns_batch_create", "wcns_batch_set_options",
     "wcns_batch_advance", "wcns_batch_get_stats", "wcns_batch_total_cells", "wcns_batch_launch_count",
     "wcns_batch_destroy",
 ]
@@ -95,6 +95,7 @@ def load(path=LIB_PATH):
         "wcns_nfields": ([vp], i),
         "wcns_ncells": ([vp], ll),
         "wcns_launch_count": ([vp], ll),
+        "wcns_rk3_step_noalloc": ([P(wcns_grid), P(wcns_bcs), d, d, d, P(wcns_options), vp, d], i),
         "wcns_profile_enable": ([vp, i], i),
         "wcns_profile_read": ([vp, P(wcns_profile)], i),
         "wcns_strerror": ([i], C.c_char_p),
