@@ -138,6 +138,13 @@ int wcns_max_wavespeed(wcns_handle *h, const double *W, double out[3]);
  * Asynchronous. */
 int wcns_rk3_step(wcns_handle *h, double *W, double dt);
 
+/* Stage tracing (verification aid, not part of the method): with W1_out
+ * and W2_out non-NULL device arrays of the state's size, every SSPRK3 step
+ * of this handle also copies its intermediate stage states W^(1) and W^(2)
+ * there (device-to-device on the handle's stream, no allocation); a later
+ * step overwrites them.  NULL, NULL switches tracing off. */
+int wcns_set_stage_trace(wcns_handle *h, double *W1_out, double *W2_out);
+
 /* Advance W in place by nsteps SSPRK3 steps.  With dt_fixed > 0 every step
  * uses dt_fixed; otherwise dt = cfl / sum_d tau_d from the state at the
  * start of each step (Sec. 3.3), computed and kept on the device.
@@ -227,14 +234,26 @@ void wcns_destroy(wcns_handle *h);
 typedef struct wcns_batch wcns_batch;
 
 /* ncells: host array of nprob sizes (each >= 1); lo/hi: host arrays of
- * nprob doubles.  Copies the problem table to the device. */
+ * nprob doubles; bc_lo/bc_hi: TRANSMISSIVE or PERIODIC (both periodic or
+ * neither).  Copies the problem table and one (problem, tile) work list per
+ * candidate tile length to the device and allocates the stage states and a
+ * tuning copy (four packed states in all). */
 int wcns_batch_create(int nprob, const int *ncells, const double *lo, const double *hi, int bc_lo,
                       int bc_hi, double gamma_g, double gamma_l, double pinf_l, wcns_batch **out);
 int wcns_batch_set_options(wcns_batch *b, const wcns_options *opt);
 /* Advance every problem by nsteps SSPRK3 steps in place (device array
- * W_packed).  t_out: optional DEVICE array of nprob doubles receiving each
- * problem's accumulated time (added to its incoming value).  Asynchronous. */
+ * W_packed).  Each stage is one persistent launch over all problems; one
+ * step (dt update + three stages) is captured once into a CUDA graph and
+ * replayed.  The first call tunes the tile length (63, 127 or 255 cells)
+ * and the persistent grid (1, 2, 4 or 8 blocks per SM) by timing trial
+ * steps on the tuning copy; make it before any stream capture of the
+ * caller's.  t_out: optional DEVICE array of nprob doubles; each problem's
+ * step sizes are added to it.  Asynchronous: ordered after the caller's
+ * pending work on the options' stream, and that stream waits for it. */
 int wcns_batch_advance(wcns_batch *b, double *W_packed, int nsteps, double cfl, double *t_out);
+/* The autotuner's choice: cells per tile and persistent grid size;
+ * WCNS_E_UNSUPPORTED before the first advance. */
+int wcns_batch_tuning(const wcns_batch *b, int *tile_cells, int *grid);
 int wcns_batch_get_stats(wcns_batch *b, wcns_stats *out);
 long long wcns_batch_total_cells(const wcns_batch *b);
 long long wcns_batch_launch_count(const wcns_batch *b);

@@ -22,6 +22,7 @@ struct wcns_handle {
   wcns_options opt;
   cudaStream_t stream;
   double *W1, *W2, *L, *Wh;  // stage states, RHS accumulator, host-API state
+  double *trace_W1, *trace_W2;  // optional copies of the stage states
   StepCtl *ctl;
   DevStats *stats;
   long long launches;
@@ -256,6 +257,10 @@ int enqueue_step(wcns_handle *h, double *W, double dt_fixed, double cfl) {
       st = launch_sweep(h, d, a);
       if (st) return st;
     }
+    double *trace = s == 0 ? h->trace_W1 : (s == 1 ? h->trace_W2 : NULL);
+    if (trace && cudaMemcpyAsync(trace, Wout, sizeof(double) * (size_t)h->nf * (size_t)h->N,
+                                 cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+      return WCNS_E_CUDA;
   }
   return WCNS_OK;
 }
@@ -358,6 +363,13 @@ int wcns_set_options(wcns_handle *h, const wcns_options *o) {
 int wcns_get_options(const wcns_handle *h, wcns_options *o) {
   if (!h || !o) return WCNS_E_INVALID_ARG;
   *o = h->opt;
+  return WCNS_OK;
+}
+
+int wcns_set_stage_trace(wcns_handle *h, double *W1_out, double *W2_out) {
+  if (!h || (!W1_out) != (!W2_out)) return WCNS_E_INVALID_ARG;
+  h->trace_W1 = W1_out;
+  h->trace_W2 = W2_out;
   return WCNS_OK;
 }
 

@@ -1,16 +1,498 @@
-// Batched mode of the C ABI (placeholder until the batched kernels land).
+// Batched mode of the C ABI: many independent 1D problems of uneven sizes
+// advanced together.  Every SSPRK3 stage is ONE persistent launch over a
+// work list of (problem, tile) pairs; each problem keeps its own CFL time
+// step (Sec. 3.3 in 1D: dt_k = cfl dx_k / max(|u| + c)); a whole step
+// (dt update + three stages) is captured once into a CUDA graph and
+// replayed.  The tile length and the persistent grid's blocks per SM are
+// chosen by a small autotuner on the first advance.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
 #include "../../include/wcns.h"
+#include "wcns_sweep.cuh"
+
+using namespace wcns;
+
+namespace {
+
+struct BatchArgs {
+  const long long *offsets;   // first cell of each problem in the packed array
+  const int *ncell;           // cells per problem
+  const double *inv_dx;       // 1/dx per problem
+  const double *dt;           // current step size per problem
+  unsigned long long *smax;   // max(|u|+c) bits of each problem's newest state
+  const int *tile_prob;       // problem of each tile
+  const int *tile_first;      // first midpoint of each tile
+  int ntiles;
+};
+
+// Geometry policy: one tile of one problem (a single 1D line).
+template <class T>
+struct BatchGeo {
+  const BatchArgs &b;
+  int prob, tile0, n;
+  long long base;
+  __device__ BatchGeo(const BatchArgs &b_, int t) : b(b_) {
+    prob = b.tile_prob[t];
+    tile0 = b.tile_first[t];
+    base = b.offsets[prob];
+    n = b.ncell[prob];
+  }
+  __device__ Line line(int) const {
+    Line r;
+    r.base = base;
+    r.stride = 1;
+    r.n = n;
+    r.valid = true;
+    return r;
+  }
+  __device__ double dt() const { return b.dt[prob]; }
+  __device__ double inv_dx() const { return b.inv_dx[prob]; }
+  __device__ double lam() const { return b.dt[prob] * b.inv_dx[prob]; }  // 1D: sigma = 1
+  __device__ unsigned long long *smax_slot(int) const { return &b.smax[prob]; }
+};
+
+template <class R, class T>
+__global__ void __launch_bounds__(T::THREADS) batch_sweep_kernel(const SweepArgs a, const BatchArgs b) {
+  extern __shared__ double smem_raw[];
+  for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
+    sweep_body<1, 0, R, T>(a, BatchGeo<T>(b, t), smem_raw);
+    __syncthreads();
+  }
+}
+
+// max(|u| + c) per problem (FP64 EOS, Sec. 2), one block per tile.
+__global__ void batch_reduce_kernel(const double *__restrict__ W, long long total, EosConst e, BatchArgs b,
+                                    int tile_cells) {
+  for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
+    const int prob = b.tile_prob[t];
+    const int first = b.tile_first[t];
+    const int n = b.ncell[prob];
+    double smax = 0.0;
+    for (int i = first + threadIdx.x; i < min(first + tile_cells, n); i += blockDim.x) {
+      const long long idx = b.offsets[prob] + i;
+      const double rho = W[idx] + W[total + idx];
+      const double ir = 1.0 / rho;
+      const double u = W[2 * total + idx] * ir;
+      const double rhoe = W[3 * total + idx] - 0.5 * W[2 * total + idx] * u;
+      const double a1 = W[4 * total + idx];
+      const double Gam = fma(a1, e.r1 - e.r2, e.r2);
+      const double Pi = a1 * e.q1;
+      const double iG = 1.0 / Gam;
+      const double p = (rhoe - Pi) * iG;
+      const double pb = Pi / (Gam + 1.0);
+      const double s = fabs(u) + sqrt((1.0 + iG) * (p + pb) * ir);
+      smax = (s > smax || s != s) ? s : smax;
+    }
+    unsigned long long bits = __double_as_longlong(smax);
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long ob = __shfl_xor_sync(0xffffffffu, bits, o);
+      bits = ob > bits ? ob : bits;
+    }
+    if ((threadIdx.x & 31) == 0 && bits) atomicMax(&b.smax[prob], bits);
+  }
+}
+
+// Start of a step for every problem: dt_k from the newest max(|u|+c), then
+// clear the accumulator that the step's last stage refills.
+__global__ void batch_begin_kernel(int nprob, const double *inv_dx, double *dt, unsigned long long *smax,
+                                   double cfl, double *t_acc) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nprob) return;
+  const double s = __longlong_as_double(smax[k]);
+  const double d = cfl / (s * inv_dx[k]);
+  dt[k] = d;
+  smax[k] = 0ull;
+  if (t_acc) t_acc[k] += d;
+}
+
+typedef cudaError_t (*BatchLauncher)(const SweepArgs &, const BatchArgs &, int grid, cudaStream_t);
+
+template <class R, int TM>
+cudaError_t launch_batch(const SweepArgs &a, const BatchArgs &b, int grid, cudaStream_t s) {
+  using T = TileT<1, TM, TM>;
+  const size_t bytes = Smem<1, 0, T>::BYTES;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(batch_sweep_kernel<R, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  batch_sweep_kernel<R, T><<<grid, T::THREADS, bytes, s>>>(a, b);
+  return cudaGetLastError();
+}
+
+template <class R, int TM>
+int max_blocks_per_sm() {
+  using T = TileT<1, TM, TM>;
+  int nb = 0;
+  cudaFuncSetAttribute(batch_sweep_kernel<R, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)Smem<1, 0, T>::BYTES);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_sweep_kernel<R, T>, T::THREADS,
+                                                    Smem<1, 0, T>::BYTES) != cudaSuccess)
+    return 1;
+  return nb > 0 ? nb : 1;
+}
+
+struct Variant {
+  int tm;
+  BatchLauncher fp64, mixed;
+  int (*occ64)(), (*occm)();
+};
+const Variant kVariants[] = {
+    {64, launch_batch<double, 64>, launch_batch<float, 64>, max_blocks_per_sm<double, 64>,
+     max_blocks_per_sm<float, 64>},
+    {128, launch_batch<double, 128>, launch_batch<float, 128>, max_blocks_per_sm<double, 128>,
+     max_blocks_per_sm<float, 128>},
+    {256, launch_batch<double, 256>, launch_batch<float, 256>, max_blocks_per_sm<double, 256>,
+     max_blocks_per_sm<float, 256>},
+};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+}  // namespace
+
+struct wcns_batch {
+  int nprob;
+  long long total;
+  EosConst eos;
+  int bc_lo, bc_hi;
+  wcns_options opt;
+  cudaStream_t stream;      // caller's stream
+  cudaStream_t cap;         // private stream for graph capture and replay
+  cudaEvent_t ev_in, ev_out;
+  int sms;
+  // device tables
+  long long *offsets;
+  int *ncell;
+  double *inv_dx, *dt;
+  unsigned long long *smax, *smax_scratch;
+  double *W1, *W2, *Wtrial;
+  DevStats *stats;
+  StepCtl *ctl;  // unused by the batch geometry; keeps SweepArgs complete
+  // per tile length: work list
+  int *tile_prob[kNumVariants], *tile_first[kNumVariants];
+  int ntiles[kNumVariants];
+  // autotuned choice
+  int tuned, variant, grid;
+  // captured step
+  cudaGraphExec_t graph;
+  double *graph_W;
+  double graph_cfl;
+  double *graph_t;
+  long long launches;
+};
+
+namespace {
+
+BatchArgs batch_args(wcns_batch *b, int v, unsigned long long *smax_out) {
+  BatchArgs a;
+  a.offsets = b->offsets;
+  a.ncell = b->ncell;
+  a.inv_dx = b->inv_dx;
+  a.dt = b->dt;
+  a.smax = smax_out;
+  a.tile_prob = b->tile_prob[v];
+  a.tile_first = b->tile_first[v];
+  a.ntiles = b->ntiles[v];
+  return a;
+}
+
+SweepArgs stage_args(wcns_batch *b, int s, const double *Win, double *Wout, const double *Wn) {
+  SweepArgs a;
+  memset(&a, 0, sizeof(a));
+  a.n[0] = 1;
+  a.n[1] = a.n[2] = 1;
+  a.ncell = b->total;
+  a.bc_lo = b->bc_lo;
+  a.bc_hi = b->bc_hi;
+  a.eos = b->eos;
+  a.tol.eps_ar = b->opt.eps_ar;
+  a.tol.eps_a = b->opt.eps_a;
+  a.tol.eps_rc = b->opt.eps_rc;
+  a.tol.hs_ar = b->opt.hs_ar;
+  a.tol.hs_a = b->opt.hs_a;
+  a.tol.hs_rc = b->opt.hs_rc;
+  a.eps_is = b->opt.eps_is;
+  a.scheme = b->opt.scheme;
+  a.epilogue = EPI_COMBINE;
+  a.read_L = 0;
+  const double ra[3] = {0.0, 0.75, 1.0 / 3.0};
+  const double rb[3] = {1.0, 0.25, 2.0 / 3.0};
+  a.rk_a = ra[s];
+  a.rk_b = rb[s];
+  a.stage = s;
+  a.W_in = Win;
+  a.Wn = Wn;
+  a.W_out = Wout;
+  a.ctl = b->ctl;
+  a.stats = b->stats;
+  return a;
+}
+
+// Enqueue one SSPRK3 step of every problem on stream s with tile variant v.
+int enqueue_batch_step(wcns_batch *b, double *W, double cfl, double *t_acc, int v, int grid, cudaStream_t s) {
+  batch_begin_kernel<<<(b->nprob + 255) / 256, 256, 0, s>>>(b->nprob, b->inv_dx, b->dt, b->smax, cfl, t_acc);
+  b->launches++;
+  if (cudaGetLastError() != cudaSuccess) return WCNS_E_CUDA;
+  for (int st = 0; st < 3; ++st) {
+    const double *Win = st == 0 ? W : (st == 1 ? b->W1 : b->W2);
+    double *Wout = st == 0 ? b->W1 : (st == 1 ? b->W2 : W);
+    SweepArgs a = stage_args(b, st, Win, Wout, W);
+    // only the last stage's wave-speed maxima feed the next step's dt
+    BatchArgs ba = batch_args(b, v, st == 2 ? b->smax : b->smax_scratch);
+    const Variant &var = kVariants[v];
+    cudaError_t e = (b->opt.precision == WCNS_MIXED ? var.mixed : var.fp64)(a, ba, grid, s);
+    b->launches++;
+    if (e != cudaSuccess) return WCNS_E_CUDA;
+  }
+  return WCNS_OK;
+}
+
+int launch_batch_reduce(wcns_batch *b, const double *W, cudaStream_t s) {
+  if (cudaMemsetAsync(b->smax, 0, sizeof(unsigned long long) * b->nprob, s) != cudaSuccess) return WCNS_E_CUDA;
+  BatchArgs ba = batch_args(b, 1, b->smax);
+  const int grid = b->sms * 8 < ba.ntiles ? b->sms * 8 : ba.ntiles;
+  batch_reduce_kernel<<<grid > 0 ? grid : 1, 128, 0, s>>>(W, b->total, b->eos, ba, kVariants[1].tm - 1);
+  b->launches++;
+  return cudaGetLastError() == cudaSuccess ? WCNS_OK : WCNS_E_CUDA;
+}
+
+void drop_graph(wcns_batch *b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = NULL;
+  b->graph_W = NULL;
+}
+
+// Autotuner: time one step of every (tile length, blocks per SM) candidate
+// on a copy of the state and keep the fastest.
+int autotune(wcns_batch *b, const double *W, double cfl) {
+  const size_t bytes = sizeof(double) * 5 * (size_t)b->total;
+  double *trial = b->Wtrial;  // allocated at create: tuning allocates nothing
+  DevStats saved;
+  cudaStreamSynchronize(b->stream);
+  cudaMemcpy(&saved, b->stats, sizeof(saved), cudaMemcpyDeviceToHost);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int bv = 1, bg = b->sms;
+  for (int v = 0; v < kNumVariants; ++v) {
+    const int occ = b->opt.precision == WCNS_MIXED ? kVariants[v].occm() : kVariants[v].occ64();
+    for (int bps = 1; bps <= occ && bps <= 8; bps *= 2) {
+      int grid = b->sms * bps;
+      if (grid > b->ntiles[v]) grid = b->ntiles[v];
+      cudaMemcpyAsync(trial, W, bytes, cudaMemcpyDeviceToDevice, b->cap);
+      if (launch_batch_reduce(b, trial, b->cap)) continue;
+      if (enqueue_batch_step(b, trial, cfl, NULL, v, grid, b->cap)) continue;  // warm
+      cudaEventRecord(e0, b->cap);
+      for (int r = 0; r < 2; ++r) enqueue_batch_step(b, trial, cfl, NULL, v, grid, b->cap);
+      cudaEventRecord(e1, b->cap);
+      if (cudaEventSynchronize(e1) != cudaSuccess) continue;
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        bv = v;
+        bg = grid;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(b->cap);
+  cudaMemcpy(b->stats, &saved, sizeof(saved), cudaMemcpyHostToDevice);
+  if (cudaGetLastError() != cudaSuccess) return WCNS_E_CUDA;
+  b->variant = bv;
+  b->grid = bg;
+  b->tuned = 1;
+  return WCNS_OK;
+}
+
+}  // namespace
 
 extern "C" {
-int wcns_batch_create(int, const int *, const double *, const double *, int, int, double, double, double,
-                      wcns_batch **out) {
-  if (out) *out = 0;
-  return WCNS_E_UNSUPPORTED;
+
+int wcns_batch_create(int nprob, const int *ncells, const double *lo, const double *hi, int bc_lo, int bc_hi,
+                      double gamma_g, double gamma_l, double pinf_l, wcns_batch **out) {
+  if (!out) return WCNS_E_INVALID_ARG;
+  *out = NULL;
+  if (nprob < 1 || !ncells || !lo || !hi) return WCNS_E_INVALID_ARG;
+  if (!(gamma_g > 1.0) || !(gamma_l > 1.0) || !(pinf_l >= 0.0) || !(gamma_g <= gamma_l)) return WCNS_E_INVALID_ARG;
+  if ((bc_lo != WCNS_BC_TRANSMISSIVE && bc_lo != WCNS_BC_PERIODIC) ||
+      (bc_hi != WCNS_BC_TRANSMISSIVE && bc_hi != WCNS_BC_PERIODIC) ||
+      ((bc_lo == WCNS_BC_PERIODIC) != (bc_hi == WCNS_BC_PERIODIC)))
+    return WCNS_E_INVALID_ARG;
+  std::vector<long long> offs(nprob);
+  std::vector<double> idx(nprob);
+  long long total = 0;
+  for (int k = 0; k < nprob; ++k) {
+    if (ncells[k] < 1 || !(hi[k] > lo[k])) return WCNS_E_INVALID_ARG;
+    offs[k] = total;
+    total += ncells[k];
+    idx[k] = 1.0 / ((hi[k] - lo[k]) / ncells[k]);  // same rounding as the single-grid handle
+  }
+  wcns_batch *b = (wcns_batch *)calloc(1, sizeof(wcns_batch));
+  if (!b) return WCNS_E_CUDA;
+  b->nprob = nprob;
+  b->total = total;
+  b->bc_lo = bc_lo;
+  b->bc_hi = bc_hi;
+  b->eos.r1 = 1.0 / (gamma_l - 1.0);
+  b->eos.r2 = 1.0 / (gamma_g - 1.0);
+  b->eos.q1 = gamma_l * pinf_l / (gamma_l - 1.0);
+  wcns_default_options(&b->opt);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+  if (b->sms < 1) b->sms = 1;
+  cudaError_t e = cudaSuccess;
+  const size_t sbytes = sizeof(double) * 5 * (size_t)total;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMalloc(&b->offsets, sizeof(long long) * nprob);
+  if (e == cudaSuccess) e = cudaMalloc(&b->ncell, sizeof(int) * nprob);
+  if (e == cudaSuccess) e = cudaMalloc(&b->inv_dx, sizeof(double) * nprob);
+  if (e == cudaSuccess) e = cudaMalloc(&b->dt, sizeof(double) * nprob);
+  if (e == cudaSuccess) e = cudaMalloc(&b->smax, sizeof(unsigned long long) * nprob);
+  if (e == cudaSuccess) e = cudaMalloc(&b->smax_scratch, sizeof(unsigned long long) * nprob);
+  if (e == cudaSuccess) e = cudaMalloc(&b->W1, sbytes);
+  if (e == cudaSuccess) e = cudaMalloc(&b->W2, sbytes);
+  if (e == cudaSuccess) e = cudaMalloc(&b->Wtrial, sbytes);
+  if (e == cudaSuccess) e = cudaMalloc(&b->stats, sizeof(DevStats));
+  if (e == cudaSuccess) e = cudaMalloc(&b->ctl, sizeof(StepCtl));
+  if (e == cudaSuccess) e = cudaMemset(b->stats, 0, sizeof(DevStats));
+  if (e == cudaSuccess) e = cudaMemset(b->ctl, 0, sizeof(StepCtl));
+  if (e == cudaSuccess) e = cudaMemcpy(b->offsets, offs.data(), sizeof(long long) * nprob, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->ncell, ncells, sizeof(int) * nprob, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->inv_dx, idx.data(), sizeof(double) * nprob, cudaMemcpyHostToDevice);
+  // work lists, one per tile length (tiles of TM midpoints cover TM-1 cells)
+  for (int v = 0; v < kNumVariants && e == cudaSuccess; ++v) {
+    std::vector<int> tp, tf;
+    const int per = kVariants[v].tm - 1;
+    for (int k = 0; k < nprob; ++k)
+      for (int c = 0; c < ncells[k]; c += per) {
+        tp.push_back(k);
+        tf.push_back(c);
+      }
+    b->ntiles[v] = (int)tp.size();
+    e = cudaMalloc(&b->tile_prob[v], sizeof(int) * tp.size());
+    if (e == cudaSuccess) e = cudaMalloc(&b->tile_first[v], sizeof(int) * tf.size());
+    if (e == cudaSuccess) e = cudaMemcpy(b->tile_prob[v], tp.data(), sizeof(int) * tp.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->tile_first[v], tf.data(), sizeof(int) * tf.size(), cudaMemcpyHostToDevice);
+  }
+  b->variant = 1;
+  b->grid = b->sms;
+  if (e != cudaSuccess) {
+    wcns_batch_destroy(b);
+    return WCNS_E_CUDA;
+  }
+  *out = b;
+  return WCNS_OK;
 }
-int wcns_batch_set_options(wcns_batch *, const wcns_options *) { return WCNS_E_UNSUPPORTED; }
-int wcns_batch_advance(wcns_batch *, double *, int, double, double *) { return WCNS_E_UNSUPPORTED; }
-int wcns_batch_get_stats(wcns_batch *, wcns_stats *) { return WCNS_E_UNSUPPORTED; }
-long long wcns_batch_total_cells(const wcns_batch *) { return 0; }
-long long wcns_batch_launch_count(const wcns_batch *) { return 0; }
-void wcns_batch_destroy(wcns_batch *) {}
+
+int wcns_batch_set_options(wcns_batch *b, const wcns_options *o) {
+  if (!b || !o) return WCNS_E_INVALID_ARG;
+  if (o->precision != WCNS_FP64 && o->precision != WCNS_MIXED) return WCNS_E_INVALID_ARG;
+  if (o->scheme < 0 || o->scheme > 2 || !(o->eps_is > 0.0)) return WCNS_E_INVALID_ARG;
+  if (b->opt.precision != o->precision || b->opt.scheme != o->scheme) b->tuned = 0;
+  b->opt = *o;
+  b->stream = (cudaStream_t)o->stream;
+  drop_graph(b);
+  return WCNS_OK;
 }
+
+int wcns_batch_advance(wcns_batch *b, double *W, int nsteps, double cfl, double *t_out) {
+  if (!b || !W || nsteps < 0 || !(cfl > 0.0 && cfl <= 1.0)) return WCNS_E_INVALID_ARG;
+  if (nsteps == 0) return WCNS_OK;
+  if (!b->tuned) {
+    int st = autotune(b, W, cfl);
+    if (st) return st;
+    drop_graph(b);
+  }
+  // order after the caller's pending work
+  if (cudaEventRecord(b->ev_in, b->stream) != cudaSuccess) return WCNS_E_CUDA;
+  if (cudaStreamWaitEvent(b->cap, b->ev_in, 0) != cudaSuccess) return WCNS_E_CUDA;
+  int st = launch_batch_reduce(b, W, b->cap);
+  if (st) return st;
+  if (!b->graph || b->graph_W != W || b->graph_cfl != cfl || b->graph_t != t_out) {
+    drop_graph(b);
+    cudaGraph_t g;
+    if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return WCNS_E_CUDA;
+    st = enqueue_batch_step(b, W, cfl, t_out, b->variant, b->grid, b->cap);
+    cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+    if (st || e != cudaSuccess) return WCNS_E_CUDA;
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      b->graph = NULL;
+      return WCNS_E_CUDA;
+    }
+    b->graph_W = W;
+    b->graph_cfl = cfl;
+    b->graph_t = t_out;
+  }
+  for (int k = 0; k < nsteps; ++k) {
+    if (cudaGraphLaunch(b->graph, b->cap) != cudaSuccess) return WCNS_E_CUDA;
+    b->launches += 4;
+  }
+  if (cudaEventRecord(b->ev_out, b->cap) != cudaSuccess) return WCNS_E_CUDA;
+  if (cudaStreamWaitEvent(b->stream, b->ev_out, 0) != cudaSuccess) return WCNS_E_CUDA;
+  return WCNS_OK;
+}
+
+int wcns_batch_get_stats(wcns_batch *b, wcns_stats *out) {
+  if (!b || !out) return WCNS_E_INVALID_ARG;
+  DevStats s;
+  if (cudaStreamSynchronize(b->cap) != cudaSuccess) return WCNS_E_CUDA;
+  if (cudaMemcpy(&s, b->stats, sizeof(s), cudaMemcpyDeviceToHost) != cudaSuccess) return WCNS_E_CUDA;
+  out->interp_limited = (long long)s.interp_limited;
+  out->interp_hard = (long long)s.interp_hard;
+  out->flux_limited = (long long)s.flux_limited;
+  out->flux_hard = (long long)s.flux_hard;
+  out->nonfinite = (long long)s.nonfinite;
+  out->inadmissible = (long long)s.inadmissible;
+  out->midpoints = (long long)s.midpoints;
+  return WCNS_OK;
+}
+
+long long wcns_batch_total_cells(const wcns_batch *b) { return b ? b->total : 0; }
+long long wcns_batch_launch_count(const wcns_batch *b) { return b ? b->launches : 0; }
+
+int wcns_batch_tuning(const wcns_batch *b, int *tile_cells, int *grid) {
+  if (!b) return WCNS_E_INVALID_ARG;
+  if (tile_cells) *tile_cells = kVariants[b->variant].tm - 1;
+  if (grid) *grid = b->grid;
+  return b->tuned ? WCNS_OK : WCNS_E_UNSUPPORTED;
+}
+
+void wcns_batch_destroy(wcns_batch *b) {
+  if (!b) return;
+  if (b->cap) cudaStreamSynchronize(b->cap);
+  drop_graph(b);
+  for (int v = 0; v < kNumVariants; ++v) {
+    cudaFree(b->tile_prob[v]);
+    cudaFree(b->tile_first[v]);
+  }
+  cudaFree(b->offsets);
+  cudaFree(b->ncell);
+  cudaFree(b->inv_dx);
+  cudaFree(b->dt);
+  cudaFree(b->smax);
+  cudaFree(b->smax_scratch);
+  cudaFree(b->W1);
+  cudaFree(b->W2);
+  cudaFree(b->Wtrial);
+  cudaFree(b->stats);
+  cudaFree(b->ctl);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  free(b);
+}
+
+}  // extern "C"

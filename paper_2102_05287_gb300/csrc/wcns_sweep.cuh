@@ -41,15 +41,18 @@ namespace wcns {
 // x sweep takes rows of 128 midpoints (coalesced along x); the y/z sweeps
 // take 32 consecutive x columns per block (coalesced across lines).
 // ---------------------------------------------------------------------------
-template <int NDIM, int DIR>
-struct Tile {
-  static constexpr int TL = (DIR == 0) ? (NDIM == 1 ? 1 : 2) : 32;
-  static constexpr int TM = (DIR == 0) ? 128 : 16;
-  static constexpr int THREADS = (DIR == 0) ? TL * TM : 256;
+template <int TL_, int TM_, int THREADS_>
+struct TileT {
+  static constexpr int TL = TL_;
+  static constexpr int TM = TM_;
+  static constexpr int THREADS = THREADS_;
   static constexpr int NS = TM + 5;      // nodes per line
   static constexpr int NN = TL * NS;     // nodes per block
   static constexpr int NM = TL * TM;     // midpoints per block
 };
+template <int NDIM, int DIR>
+using Tile = TileT<(DIR == 0) ? (NDIM == 1 ? 1 : 2) : 32, (DIR == 0) ? 128 : 16,
+                   (DIR == 0) ? (NDIM == 1 ? 128 : 256) : 256>;
 
 template <class R>
 struct Prec;
@@ -387,9 +390,8 @@ __device__ __forceinline__ R hcs(R gt, R gm2, R gm1, R g0, R gp1, R gp2, R gp3) 
 // ---------------------------------------------------------------------------
 // Shared-memory layout of one tile.
 // ---------------------------------------------------------------------------
-template <int NDIM, int DIR>
+template <int NDIM, int DIR, class T>
 struct Smem {
-  using T = Tile<NDIM, DIR>;
   static constexpr int NF = NDIM + 4;
   // per node: W (NF), velocity (NDIM), p, c, rho*ctilde^2, G (NF)
   static constexpr int NODE_DOUBLES = 2 * NF + NDIM + 3;
@@ -417,55 +419,75 @@ struct Smem {
   }
 };
 
-// Line geometry of one block: base cell index and stride along DIR.
-template <int NDIM, int DIR>
-struct Lines {
+// Geometry of one line of a tile: first cell index, stride along the swept
+// axis, cells on the line, and whether the line exists.
+struct Line {
   long long base;
   long long stride;
   int n;
   bool valid;
-  __device__ Lines(const SweepArgs &a, int l) {
-    using T = Tile<NDIM, DIR>;
+};
+
+// Geometry policy of the handle's grid: block (x, y, z) = (tile along DIR,
+// block of lines, third axis).  dt and lambda come from the device step
+// control (Sec. 3.3 directional split).
+template <int NDIM, int DIR, class T>
+struct GridGeo {
+  const SweepArgs &a;
+  int tile0;
+  __device__ GridGeo(const SweepArgs &a_) : a(a_), tile0(blockIdx.x * (T::TM - 1)) {}
+  __device__ Line line(int l) const {
+    Line r;
     const int nx = a.n[0], ny = a.n[1];
     if (DIR == 0) {
       int y = blockIdx.y * T::TL + l;
-      valid = y < ny;
+      r.valid = y < ny;
       y = min(y, ny - 1);
-      base = ((long long)blockIdx.z * ny + y) * nx;
-      stride = 1;
-      n = nx;
+      r.base = ((long long)blockIdx.z * ny + y) * nx;
+      r.stride = 1;
+      r.n = nx;
     } else {
       int x = blockIdx.y * T::TL + l;
-      valid = x < nx;
+      r.valid = x < nx;
       x = min(x, nx - 1);
       if (DIR == 1) {
-        base = (long long)blockIdx.z * nx * ny + x;
-        stride = nx;
-        n = ny;
+        r.base = (long long)blockIdx.z * nx * ny + x;
+        r.stride = nx;
+        r.n = ny;
       } else {
-        base = (long long)blockIdx.z * nx + x;
-        stride = (long long)nx * ny;
-        n = a.n[2];
+        r.base = (long long)blockIdx.z * nx + x;
+        r.stride = (long long)nx * ny;
+        r.n = a.n[2];
       }
     }
+    return r;
   }
+  __device__ double dt() const { return a.ctl->dt; }
+  __device__ double inv_dx() const { return a.inv_dx; }
+  // lambda_d = dt / (dx_d sigma_d), sigma_d = tau_d / sum(tau),
+  // tau = max(|u_d| + c)/dx_d of the stage input (Sec. 3.3).
+  __device__ double lam() const {
+    if (NDIM == 1) return a.ctl->dt * a.inv_dx;
+    double tsum = 0.0;
+#pragma unroll
+    for (int j = 0; j < NDIM; ++j) tsum += __longlong_as_double(a.ctl->smax[a.stage][j]) * a.inv_dx_all[j];
+    return a.ctl->dt * tsum / __longlong_as_double(a.ctl->smax[a.stage][DIR]);
+  }
+  __device__ unsigned long long *smax_slot(int j) const { return &a.ctl->smax[a.stage + 1][j]; }
 };
 
 // ---------------------------------------------------------------------------
 // The sweep kernel.
 // ---------------------------------------------------------------------------
-template <int NDIM, int DIR, class R>
-__global__ void __launch_bounds__(Tile<NDIM, DIR>::THREADS, 1) sweep_kernel(const SweepArgs a) {
-  using T = Tile<NDIM, DIR>;
-  using S = Smem<NDIM, DIR>;
+template <int NDIM, int DIR, class R, class T, class Geo>
+__device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, double *smem_raw) {
+  using S = Smem<NDIM, DIR, T>;
   constexpr int NF = NDIM + 4, E = 2 + NDIM, A = 3 + NDIM;
   // The FP32 path works in deviation form about node i (see the file header).
   constexpr bool DEV = sizeof(R) == 4;
-  extern __shared__ double smem_raw[];
-  if (!a.ctl->active) return;  // a finished advance: the step is a no-op
   S sm(smem_raw);
   const int tid = threadIdx.x;
-  const int tile0 = blockIdx.x * (T::TM - 1);  // first midpoint (= left face of cell tile0)
+  const int tile0 = geo.tile0;  // first midpoint (= left face of cell tile0)
   const long long N = a.ncell;
   const EosConst eos = a.eos;
 
@@ -473,7 +495,7 @@ __global__ void __launch_bounds__(Tile<NDIM, DIR>::THREADS, 1) sweep_kernel(cons
   for (int q = tid; q < T::NN; q += T::THREADS) {
     const int l = DIR == 0 ? q / T::NS : q % T::TL;
     const int s = DIR == 0 ? q % T::NS : q / T::TL;
-    const Lines<NDIM, DIR> ln(a, l);
+    const Line ln = geo.line(l);
     const int n = ln.n;
     int pos = tile0 - 3 + s;
     double w[NF];
@@ -545,18 +567,8 @@ __global__ void __launch_bounds__(Tile<NDIM, DIR>::THREADS, 1) sweep_kernel(cons
   }
   __syncthreads();
 
-  // Directional split (Sec. 3.3): lambda_d = dt / (dx_d sigma_d) with
-  // sigma_d = tau_d / sum(tau), tau = max(|u_d| + c)/dx_d of the stage input.
-  const double dt = a.ctl->dt;
-  double lam;
-  if (NDIM == 1) {
-    lam = dt * a.inv_dx;
-  } else {
-    double tsum = 0.0;
-#pragma unroll
-    for (int j = 0; j < NDIM; ++j) tsum += __longlong_as_double(a.ctl->smax[a.stage][j]) * a.inv_dx_all[j];
-    lam = dt * tsum / __longlong_as_double(a.ctl->smax[a.stage][DIR]);
-  }
+  const double dt = geo.dt();
+  const double lam = geo.lam();
   R epsR = (R)a.eps_is;
   if (sizeof(R) == 4) epsR = fmax(epsR, R(1e-30));
 
@@ -567,8 +579,8 @@ __global__ void __launch_bounds__(Tile<NDIM, DIR>::THREADS, 1) sweep_kernel(cons
     const int m = DIR == 0 ? q % T::TM : q / T::TL;
     const int si = m + 2;  // node i; node i+1 is m + 3
     // Tiles overlap by one midpoint: count limiter events once per midpoint.
-    const int cnt = (m < T::TM - 1 || tile0 + m == Lines<NDIM, DIR>(a, l).n) &&
-                    tile0 + m <= Lines<NDIM, DIR>(a, l).n && Lines<NDIM, DIR>(a, l).valid;
+    const Line lnm = geo.line(l);
+    const int cnt = (m < T::TM - 1 || tile0 + m == lnm.n) && tile0 + m <= lnm.n && lnm.valid;
     const int ni = S::nslot(l, si), ni1 = S::nslot(l, si + 1);
     double Wi[NF], Wi1[NF], vi[NDIM], Gi[NF];
 #pragma unroll
@@ -869,7 +881,7 @@ __global__ void __launch_bounds__(Tile<NDIM, DIR>::THREADS, 1) sweep_kernel(cons
   for (int q = tid; q < T::TL * (T::TM - 1); q += T::THREADS) {
     const int l = DIR == 0 ? q / (T::TM - 1) : q % T::TL;
     const int m = DIR == 0 ? q % (T::TM - 1) : q / T::TL;
-    const Lines<NDIM, DIR> ln(a, l);
+    const Line ln = geo.line(l);
     const int pos = tile0 + m;
     if (!ln.valid || pos >= ln.n) continue;
     ++midpoints_done;
@@ -877,8 +889,8 @@ __global__ void __launch_bounds__(Tile<NDIM, DIR>::THREADS, 1) sweep_kernel(cons
     const int ml = S::mslot(l, m), mr = S::mslot(l, m + 1);
     double upd[NF];
 #pragma unroll
-    for (int f = 0; f < NF - 1; ++f) upd[f] = (sm.F[f * T::NM + ml] - sm.F[f * T::NM + mr]) * a.inv_dx;
-    upd[A] = (sm.ap[ml] - sm.am[mr]) * a.inv_dx;
+    for (int f = 0; f < NF - 1; ++f) upd[f] = (sm.F[f * T::NM + ml] - sm.F[f * T::NM + mr]) * geo.inv_dx();
+    upd[A] = (sm.ap[ml] - sm.am[mr]) * geo.inv_dx();
     if (a.epilogue == EPI_WRITE) {
 #pragma unroll
       for (int f = 0; f < NF; ++f) a.L[(long long)f * N + idx] = upd[f];
@@ -917,7 +929,7 @@ __global__ void __launch_bounds__(Tile<NDIM, DIR>::THREADS, 1) sweep_kernel(cons
       }
     }
   }
-  if (a.epilogue == EPI_COMBINE && a.ctl) {
+  if (a.epilogue == EPI_COMBINE) {
 #pragma unroll
     for (int j = 0; j < NDIM; ++j) {
       unsigned long long b = __double_as_longlong(smax_local[j]);
@@ -926,7 +938,7 @@ __global__ void __launch_bounds__(Tile<NDIM, DIR>::THREADS, 1) sweep_kernel(cons
         const unsigned long long ob = __shfl_xor_sync(0xffffffffu, b, o);
         b = ob > b ? ob : b;
       }
-      if ((tid & 31) == 0 && b) atomicMax(&a.ctl->smax[a.stage + 1][j], b);
+      if ((tid & 31) == 0 && b) atomicMax(geo.smax_slot(j), b);
     }
   }
   // midpoint count (one per cell updated)
@@ -934,11 +946,19 @@ __global__ void __launch_bounds__(Tile<NDIM, DIR>::THREADS, 1) sweep_kernel(cons
   if ((tid & 31) == 0 && midpoints_done) atomicAdd(&a.stats->midpoints, (unsigned long long)midpoints_done);
 }
 
+template <int NDIM, int DIR, class R>
+__global__ void __launch_bounds__(Tile<NDIM, DIR>::THREADS, 1) sweep_kernel(const SweepArgs a) {
+  extern __shared__ double smem_raw[];
+  if (!a.ctl->active) return;  // a finished advance: the step is a no-op
+  using T = Tile<NDIM, DIR>;
+  sweep_body<NDIM, DIR, R, T>(a, GridGeo<NDIM, DIR, T>(a), smem_raw);
+}
+
 // Launch one sweep: grid = (tiles along DIR, line blocks, third axis).
 template <int NDIM, int DIR, class R>
 cudaError_t launch_sweep_t(const SweepArgs &a, cudaStream_t st) {
   using T = Tile<NDIM, DIR>;
-  const size_t bytes = Smem<NDIM, DIR>::BYTES;
+  const size_t bytes = Smem<NDIM, DIR, T>::BYTES;
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(sweep_kernel<NDIM, DIR, R>,

@@ -25,10 +25,10 @@ _PREC = {"fp64": 0, "mixed": 1}
 # Every entry point declared in include/wcns.h.
 EXPORTS = [
     "wcns_create", "wcns_default_options", "wcns_set_options", "wcns_get_options", "wcns_rhs",
-    "wcns_max_wavespeed", "wcns_rk3_step", "wcns_advance_steps", "wcns_advance_to",
+    "wcns_max_wavespeed", "wcns_rk3_step", "wcns_set_stage_trace", "wcns_advance_steps", "wcns_advance_to",
     "wcns_advance_steps_host", "wcns_get_stats", "wcns_reset_stats", "wcns_nfields", "wcns_ncells",
     "wcns_launch_count", "wcns_rk3_step_noalloc", "wcns_profile_enable", "wcns_profile_read", "wcns_strerror", "wcns_destroy", "wcns_batch_create", "wcns_batch_set_options",
-    "wcns_batch_advance", "wcns_batch_get_stats", "wcns_batch_total_cells", "wcns_batch_launch_count",
+    "wcns_batch_advance", "wcns_batch_tuning", "wcns_batch_get_stats", "wcns_batch_total_cells", "wcns_batch_launch_count",
     "wcns_batch_destroy",
 ]
 
@@ -87,6 +87,7 @@ def load(path=LIB_PATH):
         "wcns_rhs": ([vp, vp, vp, d], i),
         "wcns_max_wavespeed": ([vp, vp, P(d)], i),
         "wcns_rk3_step": ([vp, vp, d], i),
+        "wcns_set_stage_trace": ([vp, vp, vp], i),
         "wcns_advance_steps": ([vp, vp, i, d, d, P(d)], i),
         "wcns_advance_to": ([vp, vp, d, d, d, P(d), P(C.c_long)], i),
         "wcns_advance_steps_host": ([vp, vp, i, d, d, P(d)], i),
@@ -103,6 +104,7 @@ def load(path=LIB_PATH):
         "wcns_batch_create": ([i, P(i), P(d), P(d), i, i, d, d, d, P(vp)], i),
         "wcns_batch_set_options": ([vp, P(wcns_options)], i),
         "wcns_batch_advance": ([vp, vp, i, d, vp], i),
+        "wcns_batch_tuning": ([vp, P(i), P(i)], i),
         "wcns_batch_get_stats": ([vp, P(wcns_stats)], i),
         "wcns_batch_total_cells": ([vp], ll),
         "wcns_batch_launch_count": ([vp], ll),
@@ -227,6 +229,13 @@ class Solver:
         _check(self.lib.wcns_rk3_step(self.h, self._w(W), float(dt)), "wcns_rk3_step")
         return W
 
+    def set_stage_trace(self, W1=None, W2=None):
+        """Copy the two intermediate SSPRK3 stage states of every step into
+        W1, W2 (CUDA tensors shaped like the state); None, None stops."""
+        self._trace = (W1, W2)  # keep the buffers alive while traced
+        _check(self.lib.wcns_set_stage_trace(self.h, self._w(W1) if W1 is not None else None,
+                                             self._w(W2) if W2 is not None else None), "wcns_set_stage_trace")
+
     def advance_steps(self, W, nsteps, cfl=0.5, dt_fixed=0.0, t=0.0):
         tt = C.c_double(t)
         _check(self.lib.wcns_advance_steps(self.h, self._w(W), int(nsteps), float(cfl), float(dt_fixed),
@@ -312,6 +321,11 @@ class Batch:
 
     def launches(self):
         return int(self.lib.wcns_batch_launch_count(self.h))
+
+    def tuning(self):
+        tc, g = C.c_int(0), C.c_int(0)
+        st = self.lib.wcns_batch_tuning(self.h, C.byref(tc), C.byref(g))
+        return {"tile_cells": tc.value, "grid": g.value} if st == WCNS_OK else None
 
     def close(self):
         if getattr(self, "h", None):
