@@ -20,7 +20,7 @@ LIB = os.path.join(BUILD, "libwcns.so")
 PEAKS = os.path.join(BUILD, "peaks")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["wcns_fp64.cu", "wcns_mixed.cu", "wcns_api.cu", "wcns_batch.cu"]
-DEPS = ["wcns_sweep.cuh", "wcns_internal.h", "wcns_batch.cuh"]
+DEPS = ["wcns_sweep.cuh", "wcns_internal.h", "wcns_mixed_body.cuh"]
 
 
 def nvcc():

@@ -12,7 +12,7 @@
 #include <vector>
 
 #include "../../include/wcns.h"
-#include "wcns_sweep.cuh"
+#include "wcns_mixed_body.cuh"
 
 using namespace wcns;
 
@@ -55,13 +55,22 @@ struct BatchGeo {
   __device__ unsigned long long *smax_slot(int) const { return &b.smax[prob]; }
 };
 
-template <class R, class T>
+// MIXED selects the mixed-precision body (wcns_mixed_body.cuh).
+template <bool MIXED, class T>
 __global__ void __launch_bounds__(T::THREADS) batch_sweep_kernel(const SweepArgs a, const BatchArgs b) {
   extern __shared__ double smem_raw[];
   for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
-    sweep_body<1, 0, R, T>(a, BatchGeo<T>(b, t), smem_raw);
+    if constexpr (MIXED)
+      sweep_body_mixed<1, 0, T>(a, BatchGeo<T>(b, t), smem_raw);
+    else
+      sweep_body<1, 0, double, T>(a, BatchGeo<T>(b, t), smem_raw);
     __syncthreads();
   }
+}
+
+template <bool MIXED, class T>
+constexpr size_t batch_smem() {
+  return MIXED ? SmemMixed<1, T>::BYTES : Smem<1, 0, T>::BYTES;
 }
 
 // max(|u| + c) per problem (FP64 EOS, Sec. 2), one block per tile.
@@ -111,29 +120,29 @@ __global__ void batch_begin_kernel(int nprob, const double *inv_dx, double *dt, 
 
 typedef cudaError_t (*BatchLauncher)(const SweepArgs &, const BatchArgs &, int grid, cudaStream_t);
 
-template <class R, int TM>
+template <bool MIXED, int TM>
 cudaError_t launch_batch(const SweepArgs &a, const BatchArgs &b, int grid, cudaStream_t s) {
   using T = TileT<1, TM, TM>;
-  const size_t bytes = Smem<1, 0, T>::BYTES;
+  const size_t bytes = batch_smem<MIXED, T>();
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(batch_sweep_kernel<R, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(batch_sweep_kernel<MIXED, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)bytes);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  batch_sweep_kernel<R, T><<<grid, T::THREADS, bytes, s>>>(a, b);
+  batch_sweep_kernel<MIXED, T><<<grid, T::THREADS, bytes, s>>>(a, b);
   return cudaGetLastError();
 }
 
-template <class R, int TM>
+template <bool MIXED, int TM>
 int max_blocks_per_sm() {
   using T = TileT<1, TM, TM>;
   int nb = 0;
-  cudaFuncSetAttribute(batch_sweep_kernel<R, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)Smem<1, 0, T>::BYTES);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_sweep_kernel<R, T>, T::THREADS,
-                                                    Smem<1, 0, T>::BYTES) != cudaSuccess)
+  const size_t bytes = batch_smem<MIXED, T>();
+  cudaFuncSetAttribute(batch_sweep_kernel<MIXED, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_sweep_kernel<MIXED, T>, T::THREADS, bytes) !=
+      cudaSuccess)
     return 1;
   return nb > 0 ? nb : 1;
 }
@@ -144,12 +153,12 @@ struct Variant {
   int (*occ64)(), (*occm)();
 };
 const Variant kVariants[] = {
-    {64, launch_batch<double, 64>, launch_batch<float, 64>, max_blocks_per_sm<double, 64>,
-     max_blocks_per_sm<float, 64>},
-    {128, launch_batch<double, 128>, launch_batch<float, 128>, max_blocks_per_sm<double, 128>,
-     max_blocks_per_sm<float, 128>},
-    {256, launch_batch<double, 256>, launch_batch<float, 256>, max_blocks_per_sm<double, 256>,
-     max_blocks_per_sm<float, 256>},
+    {64, launch_batch<false, 64>, launch_batch<true, 64>, max_blocks_per_sm<false, 64>,
+     max_blocks_per_sm<true, 64>},
+    {128, launch_batch<false, 128>, launch_batch<true, 128>, max_blocks_per_sm<false, 128>,
+     max_blocks_per_sm<true, 128>},
+    {256, launch_batch<false, 256>, launch_batch<true, 256>, max_blocks_per_sm<false, 256>,
+     max_blocks_per_sm<true, 256>},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 

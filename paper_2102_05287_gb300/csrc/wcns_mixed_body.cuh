@@ -1,0 +1,652 @@
+// Mixed-precision sweep body: the same RHS as sweep_body (wcns_sweep.cuh)
+// arranged for GB300's 61:1 FP32:FP64 throughput.
+//
+// FP64 is kept where the method needs it: the node pressure (p + p_inf
+// cancellation), the stored midpoint fluxes and the cell update (so the
+// conserved components still telescope to FP64 round-off), the SSPRK3
+// combine, and the limiters' theta solves.  Everything else runs in FP32 in
+// deviation form about node i:
+//   * node prep splits every primitive value and flux into an FP32 pair
+//     (hi, lo) with hi + lo = value (hi truncated to 24 bits, lo the exact
+//     remainder rounded), using integer bit operations, so a deviation
+//     (hi_j - hi_i) + (lo_j - lo_i) is accurate to FP32 relative precision
+//     of the deviation itself;
+//   * projection, WCNS-IS, back-projection, both HLLC fluxes and the HCS
+//     reconstruction work on deviations (hllc_dev, hcs);
+//   * the limiters first try to certify in FP32, with a rigorous margin,
+//     that every quantity the paper tests (partial densities, volume
+//     fractions, rho ctilde^2) of every interpolated state and half state is
+//     at least its tolerance; then every theta is 1 exactly as in FP64 and
+//     nothing else is needed.  Otherwise the FP64 limiter code runs on FP64
+//     states rebuilt from the same deviations.
+#pragma once
+#include "wcns_sweep.cuh"
+
+namespace wcns {
+
+template <int NDIM, int DIR>
+using TileMixed = TileT<(DIR == 0) ? (NDIM == 1 ? 1 : 2) : 16, (DIR == 0) ? 128 : 16,
+                        (DIR == 0) ? (NDIM == 1 ? 128 : 256) : 256>;
+
+// value = hi + lo: hi keeps the leading 24 bits of the double (truncated),
+// lo is the exact remainder rounded to FP32.  Integer operations only, so
+// the FP64 pipe is not involved.  Values outside FP32's normal range (never
+// met by admissible states, apart from exact zeros) fall back to a
+// conversion with lo = 0.
+__device__ __forceinline__ void split_hilo(double v, float &hi, float &lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned int sign = (unsigned int)(b >> 63) << 31;
+  const int e = (int)((b >> 52) & 0x7FFull);
+  const int e32 = e - 1023 + 127;
+  if (e32 <= 0 || e32 >= 255) {
+    hi = e == 0 ? 0.0f : __double2float_rn(v);
+    lo = 0.0f;
+    return;
+  }
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  hi = __uint_as_float(sign | ((unsigned int)e32 << 23) | (unsigned int)(m >> 29));
+  const unsigned int low = (unsigned int)(m & 0x1FFFFFFFull);
+  const int es = e - 1075 + 127;  // exponent of the last mantissa bit, biased for FP32
+  const float scale = es > 0 ? __uint_as_float((unsigned int)es << 23) : 0.0f;
+  lo = __uint_as_float(__float_as_uint((float)low * scale) | sign);
+}
+
+// Shared-memory layout of a mixed tile.
+template <int NDIM, class T>
+struct SmemMixed {
+  static constexpr int NF = NDIM + 4;
+  // FP64: W, G per node; FP32: V hi/lo, G hi/lo per node, c, node flags
+  static constexpr size_t NODE_BYTES = 8 * 2 * NF + 4 * 4 * NF + 4 + 4;
+  static constexpr size_t MID_BYTES = 8 * (NF + 1);
+  static constexpr size_t BYTES = NODE_BYTES * T::NN + MID_BYTES * T::NM;
+  double *W, *G, *F, *am, *ap;
+  float *Vh, *Vl, *Gh, *Gl, *c;
+  unsigned int *ok;
+  __device__ SmemMixed(double *base) {
+    W = base;
+    G = W + NF * T::NN;
+    F = G + NF * T::NN;
+    am = F + (NF - 1) * T::NM;
+    ap = am + T::NM;
+    Vh = (float *)(ap + T::NM);
+    Vl = Vh + NF * T::NN;
+    Gh = Vl + NF * T::NN;
+    Gl = Gh + NF * T::NN;
+    c = Gl + NF * T::NN;
+    ok = (unsigned int *)(c + T::NN);
+  }
+};
+
+// Certification margin: FP32 evaluation of a short expression over terms of
+// total magnitude `mag` is within 2^-20 * mag of the exact value (a handful
+// of roundings at 2^-24 each).
+__device__ __forceinline__ float margin(float mag) { return 9.5367431640625e-07f * mag; }
+
+// FP32 check that rho*ctilde^2 = rho e - pbar of a conservative state given
+// by (a1r1, a2r2, m[], E, alpha) is >= eps.  Returns true only if certain.
+template <int NDIM>
+__device__ __forceinline__ bool rct2_certified(const EosConst &e, float a1r1, float a2r2, const float *m, float E,
+                                               float alpha, float magE, double eps) {
+  const float rho = a1r1 + a2r2;
+  if (!(rho > 0.0f)) return false;
+  float m2 = 0.0f;
+#pragma unroll
+  for (int j = 0; j < NDIM; ++j) m2 += m[j] * m[j];
+  const float ke = 0.5f * __fdividef(m2, rho);
+  const float Gam = (float)e.r2 + (float)(e.r1 - e.r2) * alpha;
+  const float pb = __fdividef((float)e.q1 * alpha, Gam + 1.0f);
+  const float v = E - ke - pb;
+  return v - margin(magE + ke + pb) * 4.0f >= (float)eps;
+}
+
+template <int NDIM, int DIR, class T, class Geo>
+__device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &geo, double *smem_raw) {
+  using R = float;
+  using S = SmemMixed<NDIM, T>;
+  constexpr int NF = NDIM + 4, E = 2 + NDIM, A = 3 + NDIM;
+  auto nslot = [](int l, int s) { return DIR == 0 ? l * T::NS + s : s * T::TL + l; };
+  auto mslot = [](int l, int m) { return DIR == 0 ? l * T::TM + m : m * T::TL + l; };
+  S sm(smem_raw);
+  const int tid = threadIdx.x;
+  const int tile0 = geo.tile0;
+  const long long N = a.ncell;
+  const EosConst eos = a.eos;
+  const LimTol tol = a.tol;
+  // Tolerances rounded up into FP32, so "x >= epsf" implies "x >= eps".
+  const float epsf_ar = (float)(tol.eps_ar * (1.0 + 1e-6));
+  const float epsf_a = (float)(tol.eps_a * (1.0 + 1e-6));
+  const float epsf_rc = (float)(tol.eps_rc * (1.0 + 1e-6));
+
+  // ---- 1+2: stage nodes, FP64 node work, hi/lo split -----------------------
+  for (int q = tid; q < T::NN; q += T::THREADS) {
+    const int l = DIR == 0 ? q / T::NS : q % T::TL;
+    const int s = DIR == 0 ? q % T::NS : q / T::TL;
+    const Line ln = geo.line(l);
+    const int n = ln.n;
+    const int pos = tile0 - 3 + s;
+    double w[NF];
+    bool dirichlet = false, flip = false;
+    int src = pos;
+    if (pos < -3 || pos > n + 2) {
+      src = min(max(pos, 0), n - 1);
+    } else if (pos < 0 || pos >= n) {
+      const int kind = pos < 0 ? a.bc_lo : a.bc_hi;
+      if (kind == BC_TRANS) {
+        src = pos < 0 ? 0 : n - 1;
+      } else if (kind == BC_PERIODIC) {
+        src = ((pos % n) + n) % n;
+      } else if (kind == BC_SYMMETRY) {
+        src = pos < 0 ? -1 - pos : 2 * n - 1 - pos;
+        flip = true;
+      } else {
+        dirichlet = true;
+      }
+    }
+    if (dirichlet) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) w[f] = pos < 0 ? a.dir_lo[f] : a.dir_hi[f];
+    } else {
+      const long long idx = ln.base + (long long)src * ln.stride;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) w[f] = __ldg(a.W_in + (long long)f * N + idx);
+      if (flip) w[2 + DIR] = -w[2 + DIR];
+    }
+    // Sec. 2 in FP64: p from rho e (the p + p_inf cancellation).
+    const double rho = w[0] + w[1];
+    const double ir = 1.0 / rho;
+    double v[NDIM], m2 = 0.0;
+#pragma unroll
+    for (int j = 0; j < NDIM; ++j) {
+      v[j] = w[2 + j] * ir;
+      m2 = fma(w[2 + j], v[j], m2);
+    }
+    const double rhoe = w[E] - 0.5 * m2;
+    const double Gam = mixGamma(eos, w[A]);
+    const double Pi = mixPi(eos, w[A]);
+    const double p = (rhoe - Pi) / Gam;
+    const double un = v[DIR];
+    double g[NF];
+    g[0] = w[0] * un;
+    g[1] = w[1] * un;
+#pragma unroll
+    for (int j = 0; j < NDIM; ++j) g[2 + j] = w[2 + j] * un + (j == DIR ? p : 0.0);
+    g[E] = (w[E] + p) * un;
+    g[A] = w[A] * un;
+    const int slot = nslot(l, s);
+    float vh[NF], vl[NF];
+    split_hilo(w[0], vh[0], vl[0]);
+    split_hilo(w[1], vh[1], vl[1]);
+#pragma unroll
+    for (int j = 0; j < NDIM; ++j) split_hilo(v[j], vh[2 + j], vl[2 + j]);
+    split_hilo(p, vh[E], vl[E]);
+    split_hilo(w[A], vh[A], vl[A]);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      sm.W[f * T::NN + slot] = w[f];
+      sm.G[f * T::NN + slot] = g[f];
+      sm.Vh[f * T::NN + slot] = vh[f];
+      sm.Vl[f * T::NN + slot] = vl[f];
+      float gh, gl;
+      split_hilo(g[f], gh, gl);
+      sm.Gh[f * T::NN + slot] = gh;
+      sm.Gl[f * T::NN + slot] = gl;
+    }
+    // FP32 sound speed: rho c^2 = gbar (p + pbar) (Sec. 2)
+    const float a1 = vh[A] + vl[A];
+    const float Gam32 = (float)eos.r2 + (float)(eos.r1 - eos.r2) * a1;
+    const float pb32 = __fdividef((float)eos.q1 * a1, Gam32 + 1.0f);
+    const float rho32 = vh[0] + vh[1];
+    const float pp = vh[E] + vl[E] + pb32;
+    sm.c[slot] = sqrtf(__fdividef((1.0f + __fdividef(1.0f, Gam32)) * pp, rho32));
+    // Node quantities certified above the limiter tolerances (the first
+    // test of Algorithms 1-3); bit set = certified.  hi is the value
+    // truncated toward zero, so hi >= eps > 0 implies value >= eps.
+    unsigned int okb = 0;
+    if (vh[0] >= epsf_ar) okb |= 1u;
+    if (vh[1] >= epsf_ar) okb |= 2u;
+    if (vh[A] >= epsf_a) okb |= 4u;
+    if (((1.0f - vh[A]) - vl[A]) * (1.0f - 2.4e-7f) >= epsf_a) okb |= 8u;
+    if (Gam32 * pp - margin(Gam32 * (fabsf(vh[E]) + pb32)) * 4.0f >= epsf_rc) okb |= 16u;
+    sm.ok[slot] = okb;
+    if (DIR == 0 && ln.valid && s >= 3 && s < 3 + T::TM - 1 && pos < n) {
+      const double rct = rhoe - Pi / (Gam + 1.0);
+      const bool adm = w[0] >= 0.0 && w[1] >= 0.0 && w[A] >= 0.0 && w[A] <= 1.0 && rct > 0.0 && isfinite(rhoe) &&
+                       isfinite(p);
+      if (!adm) atomicAdd(&a.stats->inadmissible, 1ull);
+    }
+  }
+  __syncthreads();
+
+  const double dt = geo.dt();
+  const double lam = geo.lam();
+  const float l2 = (float)(2.0 * lam);
+  const R epsR = fmaxf((float)a.eps_is, 1e-30f);
+  const unsigned int ALL = 31u;
+
+  // ---- 3: midpoint fluxes ---------------------------------------------------
+  int nlim_i = 0, nhard_i = 0, nlim_f = 0, nhard_f = 0;
+  for (int q = tid; q < T::NM; q += T::THREADS) {
+    const int l = DIR == 0 ? q / T::TM : q % T::TL;
+    const int m = DIR == 0 ? q % T::TM : q / T::TL;
+    const int si = m + 2;
+    const Line lnm = geo.line(l);
+    const int cnt = (m < T::TM - 1 || tile0 + m == lnm.n) && tile0 + m <= lnm.n && lnm.valid;
+    const int ni = nslot(l, si), ni1 = nslot(l, si + 1);
+    // reference node i in FP32 (hi parts) and deviations of the stencil nodes
+    float hi_i[NF], lo_i[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      hi_i[f] = sm.Vh[f * T::NN + ni];
+      lo_i[f] = sm.Vl[f * T::NN + ni];
+    }
+    auto dev = [&](int s, float *d) {
+      const int sl = nslot(l, s);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) d[f] = (sm.Vh[f * T::NN + sl] - hi_i[f]) + (sm.Vl[f * T::NN + sl] - lo_i[f]);
+    };
+    auto gdev = [&](int s, int f) {
+      const int sl = nslot(l, s);
+      return (sm.Gh[f * T::NN + sl] - sm.Gh[f * T::NN + ni]) + (sm.Gl[f * T::NN + sl] - sm.Gl[f * T::NN + ni]);
+    };
+    RefNode<NDIM, R> ref;
+    ref.r1 = hi_i[0];
+    ref.r2 = hi_i[1];
+    ref.rho = hi_i[0] + hi_i[1];
+#pragma unroll
+    for (int j = 0; j < NDIM; ++j) ref.u[j] = hi_i[2 + j];
+    ref.p = hi_i[E];
+    ref.a1 = hi_i[A];
+    // FP32 conservative states of nodes i, i+1 from the primitive hi parts
+    // (relative precision; used for (E + p)_ref and the half-state checks).
+    float Wf[2][NF];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int nk = k ? ni1 : ni;
+      float r1 = sm.Vh[0 * T::NN + nk], r2 = sm.Vh[1 * T::NN + nk], al = sm.Vh[A * T::NN + nk];
+      float pk = sm.Vh[E * T::NN + nk];
+      const float rho = r1 + r2;
+      float ke = 0.0f;
+      Wf[k][0] = r1;
+      Wf[k][1] = r2;
+#pragma unroll
+      for (int j = 0; j < NDIM; ++j) {
+        const float u = sm.Vh[(2 + j) * T::NN + nk];
+        Wf[k][2 + j] = rho * u;
+        ke += u * u;
+      }
+      Wf[k][E] = pk * ((float)eos.r2 + (float)(eos.r1 - eos.r2) * al) + (float)eos.q1 * al + 0.5f * rho * ke;
+      Wf[k][A] = al;
+    }
+    ref.Ep = Wf[0][E] + hi_i[E];
+    const float ci = sm.c[ni], ci1 = sm.c[ni1];
+    const unsigned int ok_i = sm.ok[ni], ok_i1 = sm.ok[ni1];
+
+    float d1[NF];  // node i+1
+    dev(si + 1, d1);
+    // First-order HLLC in deviation form (Sec. 3.2).
+    float dGH[NF], sH;
+    {
+      float d0[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) d0[f] = 0.0f;
+      hllc_dev<NDIM, DIR, R>(ref, eos, d0, ci, d1, ci1, dGH, sH);
+    }
+    // Delta of alpha between the nodes and node-flux deviation of node i+1
+    const float dal = d1[A];
+    float dG1[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) dG1[f] = gdev(si + 1, f);
+
+    float dGh[NF], duh;  // high-order G^ - G_i and u^ - u_i
+    bool slow_flux = false;
+    if (a.scheme == SCHEME_HLLC1) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) dGh[f] = dGH[f];
+      duh = sH - ref.u[DIR];
+    } else {
+      // Steps 1-2: projection with means of nodes i, i+1 (App. A).
+      const float ar1 = 0.5f * (hi_i[0] + sm.Vh[0 * T::NN + ni1]);
+      const float ar2 = 0.5f * (hi_i[1] + sm.Vh[1 * T::NN + ni1]);
+      const float rb = ar1 + ar2;
+      const float cb = 0.5f * (ci + ci1);
+      const float irc = __fdividef(1.0f, rb * cb);
+      const float k1 = ar1 * irc / cb, k2 = ar2 * irc / cb;
+      float U[6][NF];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        float dv[NF];
+        if (j == 2) {
+#pragma unroll
+          for (int f = 0; f < NF; ++f) dv[f] = 0.0f;
+        } else if (j == 3) {
+#pragma unroll
+          for (int f = 0; f < NF; ++f) dv[f] = d1[f];
+        } else {
+          dev(m + j, dv);
+        }
+        U[j][0] = dv[2 + DIR] - irc * dv[E];
+        U[j][1] = dv[0] - k1 * dv[E];
+        U[j][2] = dv[1] - k2 * dv[E];
+        int row = 3;
+#pragma unroll
+        for (int k = 0; k < NDIM; ++k)
+          if (k != DIR) U[j][row++] = dv[2 + k];
+        U[j][NF - 2] = dv[A];
+        U[j][NF - 1] = dv[2 + DIR] + irc * dv[E];
+      }
+      // Step 3: WCNS-IS (Sec. 4.3) on deviations.
+      float UL[NF], UR[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        UL[f] = wenois<R>(U[0][f], U[1][f], 0.0f, U[3][f], U[4][f], epsR);
+        UR[f] = wenois<R>(U[5][f], U[4][f], U[3][f], 0.0f, U[1][f], epsR);
+      }
+      // Step 4: back-projection to primitive deviations.
+      float dV[2][NF];
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const float *Us = side ? UR : UL;
+        float *d = dV[side];
+        const float dac = Us[NF - 1] - Us[0];
+        d[0] = Us[1] + __fdividef(ar1, 2.0f * cb) * dac;
+        d[1] = Us[2] + __fdividef(ar2, 2.0f * cb) * dac;
+        int row = 3;
+#pragma unroll
+        for (int k = 0; k < NDIM; ++k) {
+          if (k == DIR) {
+            d[2 + k] = 0.5f * (Us[0] + Us[NF - 1]);
+          } else {
+            d[2 + k] = Us[row];
+            ++row;
+          }
+        }
+        d[E] = 0.5f * rb * cb * dac;
+        d[A] = Us[NF - 2];
+      }
+      // Sound speeds of the interpolated states (Sec. 2), FP32.
+      float cs[2];
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const float *d = dV[side];
+        const float a1 = ref.a1 + (lo_i[A] + d[A]);
+        const float Gam = (float)eos.r2 + (float)(eos.r1 - eos.r2) * a1;
+        const float pb = __fdividef((float)eos.q1 * a1, Gam + 1.0f);
+        const float rho = ref.rho + (lo_i[0] + lo_i[1] + d[0] + d[1]);
+        cs[side] = sqrtf(__fdividef((1.0f + __fdividef(1.0f, Gam)) * (ref.p + (lo_i[E] + d[E]) + pb), rho));
+      }
+      // Interpolation limiter (Sec. 5.1): FP32 certification, else FP64.
+      if (a.scheme == SCHEME_PP) {
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+          float *d = dV[side];
+          const unsigned int okn = side ? ok_i1 : ok_i;
+          bool cert = okn == ALL;
+          if (cert) {
+            const float r1 = hi_i[0] + (lo_i[0] + d[0]);
+            const float r2 = hi_i[1] + (lo_i[1] + d[1]);
+            const float al = hi_i[A] + (lo_i[A] + d[A]);
+            const float om = ((1.0f - hi_i[A]) - lo_i[A]) - d[A];
+            const float pt = hi_i[E] + (lo_i[E] + d[E]);
+            const float Gam = (float)eos.r2 + (float)(eos.r1 - eos.r2) * al;
+            const float pb = __fdividef((float)eos.q1 * al, Gam + 1.0f);
+            cert = r1 - margin(fabsf(hi_i[0]) + fabsf(d[0])) >= epsf_ar &&
+                   r2 - margin(fabsf(hi_i[1]) + fabsf(d[1])) >= epsf_ar &&
+                   al - margin(fabsf(hi_i[A]) + fabsf(d[A])) >= epsf_a &&
+                   om - margin(fabsf(om) + fabsf(d[A])) >= epsf_a &&
+                   Gam * (pt + pb) - margin(Gam * (fabsf(hi_i[E]) + fabsf(d[E]) + pb)) * 4.0f >= epsf_rc;
+          }
+          if (cert) continue;
+          // FP64 path: node i plus deviation, V -> W, Algorithms 1-3.
+          const int nk = side ? ni1 : ni;
+          double Wn[NF], Wt[NF], V[NF];
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            Wn[f] = sm.W[f * T::NN + nk];
+            V[f] = ((double)hi_i[f] + (double)lo_i[f]) + (double)d[f];
+          }
+          const double rho = V[0] + V[1];
+          double k2s = 0.0;
+#pragma unroll
+          for (int k = 0; k < NDIM; ++k) {
+            Wt[2 + k] = rho * V[2 + k];
+            k2s = fma(V[2 + k], V[2 + k], k2s);
+          }
+          Wt[0] = V[0];
+          Wt[1] = V[1];
+          Wt[E] = fma(V[E], mixGamma(eos, V[A]), mixPi(eos, V[A])) + 0.5 * rho * k2s;
+          Wt[A] = V[A];
+          const double rct_n = rho_ct2<NDIM>(eos, Wn);
+          const int fl = interp_limit<NDIM>(eos, tol, Wn, rct_n, Wt);
+          nlim_i += cnt * (fl & 1);
+          nhard_i += cnt * (fl >> 1);
+          if (fl) {
+            const double r = Wt[0] + Wt[1];
+            const double ir = 1.0 / r;
+            double mm = 0.0, vv[NDIM];
+#pragma unroll
+            for (int k = 0; k < NDIM; ++k) {
+              vv[k] = Wt[2 + k] * ir;
+              mm = fma(Wt[2 + k], vv[k], mm);
+            }
+            const double pn = (Wt[E] - 0.5 * mm - mixPi(eos, Wt[A])) / mixGamma(eos, Wt[A]);
+            const double ref64[5] = {(double)hi_i[0] + (double)lo_i[0], (double)hi_i[1] + (double)lo_i[1],
+                                     (double)hi_i[E] + (double)lo_i[E], (double)hi_i[A] + (double)lo_i[A], 0.0};
+            d[0] = (float)(Wt[0] - ref64[0]);
+            d[1] = (float)(Wt[1] - ref64[1]);
+#pragma unroll
+            for (int k = 0; k < NDIM; ++k) d[2 + k] = (float)(vv[k] - ((double)hi_i[2 + k] + (double)lo_i[2 + k]));
+            d[E] = (float)(pn - ref64[2]);
+            d[A] = (float)(Wt[A] - ref64[3]);
+            // sound speed of the limited state
+            const double Gm_ = mixGamma(eos, Wt[A]);
+            const double pb = mixPi(eos, Wt[A]) / (Gm_ + 1.0);
+            cs[side] = (float)sqrt((1.0 + 1.0 / Gm_) * (pn + pb) * ir);
+          }
+        }
+      }
+      // Steps 6-8: midpoint HLLC and HCS reconstruction, deviation form.
+      float dGt[NF], ut;
+      hllc_dev<NDIM, DIR, R>(ref, eos, dV[0], cs[0], dV[1], cs[1], dGt, ut);
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+        dGh[f] = hcs<R>(dGt[f], gdev(m, f), gdev(m + 1, f), 0.0f, dG1[f], gdev(m + 4, f), gdev(m + 5, f));
+      {
+        auto udev = [&](int s) {
+          const int sl = nslot(l, s);
+          return (sm.Vh[(2 + DIR) * T::NN + sl] - hi_i[2 + DIR]) + (sm.Vl[(2 + DIR) * T::NN + sl] - lo_i[2 + DIR]);
+        };
+        duh = hcs<R>(ut - ref.u[DIR] - lo_i[2 + DIR], udev(m), udev(m + 1), 0.0f, d1[2 + DIR], udev(m + 4),
+                     udev(m + 5));
+      }
+      // Flux limiter (Sec. 5.2): FP32 certification of the four half states.
+      if (a.scheme == SCHEME_PP) {
+        bool cert = ok_i == ALL && ok_i1 == ALL;
+        const float ai = hi_i[A], ai1 = hi_i[A] + dal;
+        const float ui = ref.u[DIR];
+#pragma unroll
+        for (int st = 0; st < 4 && cert; ++st) {
+          // st: 0 = W_i^{HLLC,+}, 1 = W_{i+1}^{HLLC,-}, 2 = W_i^{+}, 3 = W_{i+1}^{-}
+          const bool hl = st < 2;
+          const bool right = st & 1;
+          const float *dg = hl ? dGH : dGh;
+          const float du = hl ? sH - ui - lo_i[2 + DIR] : duh;
+          float D[NF];  // flux minus the node's physical flux, FP32
+#pragma unroll
+          for (int f = 0; f < NF - 1; ++f) D[f] = right ? dg[f] - dG1[f] : dg[f];
+          D[A] = right ? -dal * ui + dg[A] - ai1 * du : dg[A] - ai * du;
+          const float sgn = right ? 1.0f : -1.0f;  // W_i - 2 lam (.), W_{i+1} + 2 lam (.)
+          const float *wn = Wf[right ? 1 : 0];
+          float x[NF], mag[NF];
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            x[f] = wn[f] + sgn * l2 * D[f];
+            mag[f] = fabsf(wn[f]) + fabsf(l2 * D[f]);
+          }
+          // 1 - alpha of the node from its hi/lo parts (exact), then the step
+          const float omn = right ? ((1.0f - hi_i[A]) - lo_i[A]) - dal : (1.0f - hi_i[A]) - lo_i[A];
+          const float om = omn - sgn * l2 * D[A];
+          cert = x[0] - margin(mag[0]) >= epsf_ar && x[1] - margin(mag[1]) >= epsf_ar &&
+                 x[A] - margin(mag[A]) >= epsf_a && om - margin(fabsf(omn) + fabsf(l2 * D[A])) >= epsf_a &&
+                 rct2_certified<NDIM>(eos, x[0], x[1], x + 2, x[E], x[A], mag[E], tol.eps_rc * (1.0 + 1e-6));
+        }
+        slow_flux = !cert;
+      }
+    }
+    // Assemble the FP64 split fluxes G^-_{i+1/2}, G^+_{i+1/2} (Sec. 3.2).
+    double Gm[NF], Gp[NF];
+    const double ai64 = sm.W[A * T::NN + ni], ai164 = sm.W[A * T::NN + ni1];
+#pragma unroll
+    for (int f = 0; f < NF - 1; ++f) Gm[f] = Gp[f] = sm.G[f * T::NN + ni] + (double)dGh[f];
+    {
+      const float ai = hi_i[A], ai1 = hi_i[A] + dal, ui = ref.u[DIR];
+      Gm[A] = (double)(dGh[A] - ai * duh);
+      Gp[A] = (double)((ai - ai1) * ui + dGh[A] - ai1 * duh);
+    }
+    if (slow_flux) {
+      double GHm[NF], GHp[NF], Fi[NF], Fi1[NF], Wi[NF], Wi1[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        Wi[f] = sm.W[f * T::NN + ni];
+        Wi1[f] = sm.W[f * T::NN + ni1];
+        Fi[f] = sm.G[f * T::NN + ni];
+        Fi1[f] = sm.G[f * T::NN + ni1];
+      }
+      Fi[A] = Fi1[A] = 0.0;
+      const double ui64 = (double)hi_i[2 + DIR] + (double)lo_i[2 + DIR];
+      const double uH = (double)sH;
+      const double uh64 = ui64 + (double)duh;
+#pragma unroll
+      for (int f = 0; f < NF - 1; ++f) GHm[f] = GHp[f] = Fi[f] + (double)dGH[f];
+      GHm[A] = sm.G[A * T::NN + ni] + (double)dGH[A] - ai64 * uH;
+      GHp[A] = sm.G[A * T::NN + ni] + (double)dGH[A] - ai164 * uH;
+      Gm[A] = sm.G[A * T::NN + ni] + (double)dGh[A] - ai64 * uh64;
+      Gp[A] = sm.G[A * T::NN + ni] + (double)dGh[A] - ai164 * uh64;
+      const int fl = flux_limit<NDIM>(eos, tol, Wi, Wi1, Fi, Fi1, GHm, GHp, lam, Gm, Gp);
+      nlim_f += cnt * (fl & 1);
+      nhard_f += cnt * (fl >> 1);
+    }
+    const int ms = mslot(l, m);
+#pragma unroll
+    for (int f = 0; f < NF - 1; ++f) sm.F[f * T::NM + ms] = Gm[f];
+    sm.am[ms] = Gm[A];
+    sm.ap[ms] = Gp[A];
+  }
+  if (nlim_i) atomicAdd(&a.stats->interp_limited, (unsigned long long)nlim_i);
+  if (nhard_i) atomicAdd(&a.stats->interp_hard, (unsigned long long)nhard_i);
+  if (nlim_f) atomicAdd(&a.stats->flux_limited, (unsigned long long)nlim_f);
+  if (nhard_f) atomicAdd(&a.stats->flux_hard, (unsigned long long)nhard_f);
+  __syncthreads();
+
+  // ---- 4: cell update (FP64) -------------------------------------------------
+  float smax_local[NDIM];
+#pragma unroll
+  for (int j = 0; j < NDIM; ++j) smax_local[j] = 0.0f;
+  int done = 0;
+  const double idx_ = geo.inv_dx();
+  for (int q = tid; q < T::TL * (T::TM - 1); q += T::THREADS) {
+    const int l = DIR == 0 ? q / (T::TM - 1) : q % T::TL;
+    const int m = DIR == 0 ? q % (T::TM - 1) : q / T::TL;
+    const Line ln = geo.line(l);
+    const int pos = tile0 + m;
+    if (!ln.valid || pos >= ln.n) continue;
+    ++done;
+    const long long idx = ln.base + (long long)pos * ln.stride;
+    const int ml = mslot(l, m), mr = mslot(l, m + 1);
+    double upd[NF];
+#pragma unroll
+    for (int f = 0; f < NF - 1; ++f) upd[f] = (sm.F[f * T::NM + ml] - sm.F[f * T::NM + mr]) * idx_;
+    upd[A] = (sm.ap[ml] - sm.am[mr]) * idx_;
+    if (a.epilogue == EPI_WRITE) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) a.L[(long long)f * N + idx] = upd[f];
+    } else if (a.epilogue == EPI_ACCUM) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) a.L[(long long)f * N + idx] += upd[f];
+    } else {
+      const int ns = nslot(l, m + 3);
+      double w[NF];
+      bool finite = true;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const double tot = a.read_L ? a.L[(long long)f * N + idx] + upd[f] : upd[f];
+        const double wn = a.rk_a != 0.0 ? a.Wn[(long long)f * N + idx] : 0.0;
+        w[f] = a.rk_a * wn + a.rk_b * (sm.W[f * T::NN + ns] + dt * tot);
+        finite = finite && isfinite(w[f]);
+        a.W_out[(long long)f * N + idx] = w[f];
+      }
+      if (!finite) atomicAdd(&a.stats->nonfinite, 1ull);
+      // max(|u_d| + c) of the new state for the next stage (FP32 suffices
+      // for the directional split, Sec. 3.3)
+      float hi, lo;
+      float wf[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        split_hilo(w[f], hi, lo);
+        wf[f] = hi + lo;
+      }
+      const float rho = wf[0] + wf[1];
+      float m2 = 0.0f;
+#pragma unroll
+      for (int j = 0; j < NDIM; ++j) m2 += wf[2 + j] * wf[2 + j];
+      const float Gam = (float)eos.r2 + (float)(eos.r1 - eos.r2) * wf[A];
+      const float pb = __fdividef((float)eos.q1 * wf[A], Gam + 1.0f);
+      const float rct = wf[E] - 0.5f * __fdividef(m2, rho) - pb;
+      const float iG = __fdividef(1.0f, Gam);
+      const float c = sqrtf(fmaxf((1.0f + iG) * iG * rct, 0.0f) / rho);
+#pragma unroll
+      for (int j = 0; j < NDIM; ++j) {
+        const float sj = fabsf(__fdividef(wf[2 + j], rho)) + c;
+        smax_local[j] = (sj > smax_local[j] || sj != sj) ? sj : smax_local[j];
+      }
+    }
+  }
+  if (a.epilogue == EPI_COMBINE) {
+#pragma unroll
+    for (int j = 0; j < NDIM; ++j) {
+      // 1 + 2^-20 headroom: the FP32 maximum never undercuts the FP64 one
+      unsigned long long b = __double_as_longlong((double)smax_local[j] * (1.0 + 9.5367431640625e-07));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ob = __shfl_xor_sync(0xffffffffu, b, o);
+        b = ob > b ? ob : b;
+      }
+      if ((tid & 31) == 0 && b) atomicMax(geo.smax_slot(j), b);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) done += __shfl_xor_sync(0xffffffffu, done, o);
+  if ((tid & 31) == 0 && done) atomicAdd(&a.stats->midpoints, (unsigned long long)done);
+}
+
+template <int NDIM, int DIR>
+__global__ void __launch_bounds__(TileMixed<NDIM, DIR>::THREADS, 1) sweep_kernel_mixed(const SweepArgs a) {
+  extern __shared__ double smem_raw[];
+  if (!a.ctl->active) return;
+  using T = TileMixed<NDIM, DIR>;
+  sweep_body_mixed<NDIM, DIR, T>(a, GridGeo<NDIM, DIR, T>(a), smem_raw);
+}
+
+template <int NDIM, int DIR>
+cudaError_t launch_sweep_mixed_t(const SweepArgs &a, cudaStream_t st) {
+  using T = TileMixed<NDIM, DIR>;
+  const size_t bytes = SmemMixed<NDIM, T>::BYTES;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel_mixed<NDIM, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const int nd = a.n[DIR];
+  dim3 grid((nd + T::TM - 2) / (T::TM - 1), 1, 1);
+  if (DIR == 0) {
+    grid.y = (a.n[1] + T::TL - 1) / T::TL;
+    grid.z = a.n[2];
+  } else {
+    grid.y = (a.n[0] + T::TL - 1) / T::TL;
+    grid.z = DIR == 1 ? a.n[2] : a.n[1];
+  }
+  sweep_kernel_mixed<NDIM, DIR><<<grid, T::THREADS, bytes, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace wcns
