@@ -24,6 +24,10 @@
 
 namespace wcns {
 
+#ifndef MIXED_MIN_BLOCKS
+#define MIXED_MIN_BLOCKS 2
+#endif
+
 template <int NDIM, int DIR>
 using TileMixed = TileT<(DIR == 0) ? (NDIM == 1 ? 1 : 2) : 16, (DIR == 0) ? 128 : 16,
                         (DIR == 0) ? (NDIM == 1 ? 128 : 256) : 256>;
@@ -415,8 +419,7 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
           Wt[1] = V[1];
           Wt[E] = fma(V[E], mixGamma(eos, V[A]), mixPi(eos, V[A])) + 0.5 * rho * k2s;
           Wt[A] = V[A];
-          const double rct_n = rho_ct2<NDIM>(eos, Wn);
-          const int fl = interp_limit<NDIM>(eos, tol, Wn, rct_n, Wt);
+          const int fl = interp_limit<NDIM>(eos, tol, Wn, Wt);
           nlim_i += cnt * (fl & 1);
           nhard_i += cnt * (fl >> 1);
           if (fl) {
@@ -618,7 +621,7 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
 }
 
 template <int NDIM, int DIR>
-__global__ void __launch_bounds__(TileMixed<NDIM, DIR>::THREADS, 1) sweep_kernel_mixed(const SweepArgs a) {
+__global__ void __launch_bounds__(TileMixed<NDIM, DIR>::THREADS, MIXED_MIN_BLOCKS) sweep_kernel_mixed(const SweepArgs a) {
   extern __shared__ double smem_raw[];
   if (!a.ctl->active) return;
   using T = TileMixed<NDIM, DIR>;
@@ -633,6 +636,8 @@ cudaError_t launch_sweep_mixed_t(const SweepArgs &a, cudaStream_t st) {
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(sweep_kernel_mixed<NDIM, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(sweep_kernel_mixed<NDIM, DIR>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     configured = true;
   }

@@ -51,7 +51,7 @@ struct TileT {
   static constexpr int NM = TL * TM;     // midpoints per block
 };
 template <int NDIM, int DIR>
-using Tile = TileT<(DIR == 0) ? (NDIM == 1 ? 1 : 2) : 32, (DIR == 0) ? 128 : 16,
+using Tile = TileT<(DIR == 0) ? (NDIM == 1 ? 1 : 2) : 16, (DIR == 0) ? 128 : 32,
                    (DIR == 0) ? (NDIM == 1 ? 128 : 256) : 256>;
 
 template <class R>
@@ -103,6 +103,47 @@ __device__ __forceinline__ R wenois(R um2, R um1, R u0, R up1, R up2, R eps) {
   const R w2 = R(5.0 / 16.0) * (R(1) + r2);
   const R w3 = R(1.0 / 16.0) * (R(1) + r3);
   return Prec<R>::div(w0 * s0 + w1 * s1 + w2 * s2 + w3 * s3, (w0 + w1) + (w2 + w3));
+}
+
+// FP64 specialisation with one division instead of six: multiplying every
+// eta_k by D = b0 b1 b01 b2 b3 (b = beta + eps) leaves the weights
+// omega_k = eta_k / sum(eta) unchanged and clears the five ratio divisions:
+//   eta0 D = d0 (b0 b01 + tau^2) b1 b2 b3,  eta1 D = d1 (b1 b01 + tau^2) b0 b2 b3,
+//   eta2 D = d2 (b2 + tau) b0 b1 b01 b3,    eta3 D = d3 (b3 + tau) b0 b1 b01 b2.
+// If the scaled sum leaves the comfortable FP64 range the direct form runs.
+template <>
+__device__ __forceinline__ double wenois<double>(double um2, double um1, double u0, double up1, double up2,
+                                                 double eps) {
+  const double s0 = 0.5 * (u0 + up1);
+  const double s1 = 0.5 * (3.0 * u0 - um1);
+  const double s2 = 0.125 * (3.0 * u0 + 6.0 * up1 - up2);
+  const double s3 = 0.125 * (3.0 * um2 - 10.0 * um1 + 15.0 * u0);
+  const double e0 = u0 - up1, e1 = um1 - u0;
+  const double a01 = um1 - 2.0 * u0 + up1, c01 = um1 - up1;
+  const double a2 = u0 - 2.0 * up1 + up2, c2 = 3.0 * u0 - 4.0 * up1 + up2;
+  const double a3 = um2 - 2.0 * um1 + u0, c3 = um2 - 4.0 * um1 + 3.0 * u0;
+  const double t5a = up2 - 4.0 * up1 + 6.0 * u0 - 4.0 * um1 + um2;
+  const double t5b = up2 - 2.0 * up1 + 2.0 * um1 - um2;
+  const double tau = (13.0 / 12.0) * t5a * t5a + 0.25 * t5b * t5b;
+  const double b0 = e0 * e0 + eps;
+  const double b1 = e1 * e1 + eps;
+  const double b01 = (13.0 / 12.0) * a01 * a01 + 0.25 * c01 * c01 + eps;
+  const double b2 = (13.0 / 12.0) * a2 * a2 + 0.25 * c2 * c2 + eps;
+  const double b3 = (13.0 / 12.0) * a3 * a3 + 0.25 * c3 * c3 + eps;
+  const double t2 = tau * tau;
+  const double p23 = b2 * b3, p01b = (b0 * b1) * b01;
+  const double w0 = (15.0 / 32.0) * (b0 * b01 + t2) * (b1 * p23);
+  const double w1 = (5.0 / 32.0) * (b1 * b01 + t2) * (b0 * p23);
+  const double w2 = (5.0 / 16.0) * (b2 + tau) * (p01b * b3);
+  const double w3 = (1.0 / 16.0) * (b3 + tau) * (p01b * b2);
+  const double sum = (w0 + w1) + (w2 + w3);
+  if (sum > 1e-280 && sum < 1e280) return (w0 * s0 + w1 * s1 + w2 * s2 + w3 * s3) / sum;
+  const double r01 = tau / b01;
+  const double v0 = (15.0 / 32.0) * (1.0 + (tau / b0) * r01);
+  const double v1 = (5.0 / 32.0) * (1.0 + (tau / b1) * r01);
+  const double v2 = (5.0 / 16.0) * (1.0 + tau / b2);
+  const double v3 = (1.0 / 16.0) * (1.0 + tau / b3);
+  return (v0 * s0 + v1 * s1 + v2 * s2 + v3 * s3) / ((v0 + v1) + (v2 + v3));
 }
 
 // ---------------------------------------------------------------------------
@@ -277,6 +318,21 @@ __device__ __forceinline__ double rho_ct2(const EosConst &e, const double *W) {
   return W[E] - 0.5 * m2 / rho - mixPinf(e, W[A]);
 }
 
+// "rho ctilde^2 < eps" decided without divisions: for rho > 0 and
+// Gamma + 1 > 0, multiply E - m^2/(2 rho) - Pi/(Gamma+1) < eps through by
+// rho (Gamma + 1).  Any other state uses the quotient form.
+template <int NDIM>
+__device__ __forceinline__ bool rct2_below(const EosConst &e, const double *W, double eps) {
+  constexpr int E = 2 + NDIM, A = 3 + NDIM;
+  const double rho = W[0] + W[1];
+  const double G1 = mixGamma(e, W[A]) + 1.0;
+  if (!(rho > 0.0) || !(G1 > 0.0)) return rho_ct2<NDIM>(e, W) < eps;
+  double m2 = 0.0;
+#pragma unroll
+  for (int j = 0; j < NDIM; ++j) m2 = fma(W[2 + j], W[2 + j], m2);
+  return ((W[E] - eps) * rho - 0.5 * m2) * G1 - mixPi(e, W[A]) * rho < 0.0;
+}
+
 // theta solving (1-theta) fA + theta fB = eps with the paper's three cases.
 __device__ __forceinline__ double lim_theta(double fA, double fB, double eps) {
   if (fA < eps) return 0.0;
@@ -284,39 +340,58 @@ __device__ __forceinline__ double lim_theta(double fA, double fB, double eps) {
   return 1.0;
 }
 
+// The same three cases for rho ctilde^2, with the quotient evaluated only
+// when a blend is needed.
 template <int NDIM>
-__device__ __forceinline__ double lim_quantity(const EosConst &e, const double *W, int which) {
+__device__ __forceinline__ double lim_theta_rct(const EosConst &e, const double *A, const double *B, double eps) {
+  if (rct2_below<NDIM>(e, A, eps)) return 0.0;
+  if (!rct2_below<NDIM>(e, B, eps)) return 1.0;
+  const double fA = rho_ct2<NDIM>(e, A);
+  return (fA - eps) / (fA - rho_ct2<NDIM>(e, B));
+}
+
+template <int NDIM>
+__device__ __forceinline__ double lim_quantity(const double *W, int which) {
   constexpr int A = 3 + NDIM;
   switch (which) {
     case 0: return W[0];
     case 1: return W[1];
     case 2: return W[A];
-    case 3: return 1.0 - W[A];
-    default: return rho_ct2<NDIM>(e, W);
+    default: return 1.0 - W[A];
   }
+}
+
+// Hard-switch test of Secs. 5.1-5.2: a tested quantity below its
+// hard-switch tolerance.
+template <int NDIM>
+__device__ __forceinline__ bool hard_fail(const EosConst &e, const LimTol &t, const double *X) {
+  constexpr int A = 3 + NDIM;
+  return X[0] < t.hs_ar || X[1] < t.hs_ar || X[A] < t.hs_a || 1.0 - X[A] < t.hs_a ||
+         rct2_below<NDIM>(e, X, t.hs_rc);
 }
 
 // Sec. 5.1, Algorithms 1-3 + hard switch: limit Wt toward the node state Wn.
 // Returns bit 0 = some theta < 1, bit 1 = hard switch.
 template <int NDIM>
-__device__ int interp_limit(const EosConst &e, const LimTol &t, const double *Wn, double rctn,
-                            double *Wt) {
+__device__ int interp_limit(const EosConst &e, const LimTol &t, const double *Wn, double *Wt) {
   constexpr int NF = NDIM + 4;
   int flags = 0;
 #pragma unroll 1
   for (int which = 0; which < 5; ++which) {
-    const double eps = which < 2 ? t.eps_ar : (which < 4 ? t.eps_a : t.eps_rc);
-    const double fA = which == 4 ? rctn : lim_quantity<NDIM>(e, Wn, which);
-    const double th = lim_theta(fA, lim_quantity<NDIM>(e, Wt, which), eps);
+    double th;
+    if (which < 4) {
+      const double eps = which < 2 ? t.eps_ar : t.eps_a;
+      th = lim_theta(lim_quantity<NDIM>(Wn, which), lim_quantity<NDIM>(Wt, which), eps);
+    } else {
+      th = lim_theta_rct<NDIM>(e, Wn, Wt, t.eps_rc);
+    }
     if (th < 1.0) {
       flags |= 1;
 #pragma unroll
       for (int q = 0; q < NF; ++q) Wt[q] = (1.0 - th) * Wn[q] + th * Wt[q];
     }
   }
-  constexpr int A = 3 + NDIM;
-  if (Wt[0] < t.hs_ar || Wt[1] < t.hs_ar || Wt[A] < t.hs_a || 1.0 - Wt[A] < t.hs_a ||
-      rho_ct2<NDIM>(e, Wt) < t.hs_rc) {
+  if (hard_fail<NDIM>(e, t, Wt)) {
     flags |= 2;
 #pragma unroll
     for (int q = 0; q < NF; ++q) Wt[q] = Wn[q];
@@ -331,7 +406,7 @@ template <int NDIM>
 __device__ int flux_limit(const EosConst &e, const LimTol &t, const double *Wi, const double *Wi1,
                           const double *Fi, const double *Fi1, const double *GHm, const double *GHp,
                           double lam, double *Gm, double *Gp) {
-  constexpr int NF = NDIM + 4, A = 3 + NDIM;
+  constexpr int NF = NDIM + 4;
   const double l2 = 2.0 * lam;
   double Ap[NF], Am[NF], Bp[NF], Bm[NF];
 #pragma unroll
@@ -344,9 +419,15 @@ __device__ int flux_limit(const EosConst &e, const LimTol &t, const double *Wi, 
   int flags = 0;
 #pragma unroll 1
   for (int which = 0; which < 5; ++which) {
-    const double eps = which < 2 ? t.eps_ar : (which < 4 ? t.eps_a : t.eps_rc);
-    const double thp = lim_theta(lim_quantity<NDIM>(e, Ap, which), lim_quantity<NDIM>(e, Bp, which), eps);
-    const double thm = lim_theta(lim_quantity<NDIM>(e, Am, which), lim_quantity<NDIM>(e, Bm, which), eps);
+    double thp, thm;
+    if (which < 4) {
+      const double eps = which < 2 ? t.eps_ar : t.eps_a;
+      thp = lim_theta(lim_quantity<NDIM>(Ap, which), lim_quantity<NDIM>(Bp, which), eps);
+      thm = lim_theta(lim_quantity<NDIM>(Am, which), lim_quantity<NDIM>(Bm, which), eps);
+    } else {
+      thp = lim_theta_rct<NDIM>(e, Ap, Bp, t.eps_rc);
+      thm = lim_theta_rct<NDIM>(e, Am, Bm, t.eps_rc);
+    }
     const double th = fmin(thp, thm);
     if (th < 1.0) {
       flags |= 1;
@@ -359,15 +440,7 @@ __device__ int flux_limit(const EosConst &e, const LimTol &t, const double *Wi, 
       }
     }
   }
-  bool hard = false;
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    const double *X = s ? Bm : Bp;
-    if (X[0] < t.hs_ar || X[1] < t.hs_ar || X[A] < t.hs_a || 1.0 - X[A] < t.hs_a ||
-        rho_ct2<NDIM>(e, X) < t.hs_rc)
-      hard = true;
-  }
-  if (hard) {
+  if (hard_fail<NDIM>(e, t, Bp) || hard_fail<NDIM>(e, t, Bm)) {
     flags |= 2;
 #pragma unroll
     for (int q = 0; q < NF; ++q) {
@@ -477,14 +550,13 @@ struct GridGeo {
 };
 
 // ---------------------------------------------------------------------------
-// The sweep kernel.
+// The FP64 sweep body (the mixed-precision body is wcns_mixed_body.cuh).
 // ---------------------------------------------------------------------------
 template <int NDIM, int DIR, class R, class T, class Geo>
 __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, double *smem_raw) {
+  static_assert(sizeof(R) == 8, "sweep_body is the FP64 body");
   using S = Smem<NDIM, DIR, T>;
   constexpr int NF = NDIM + 4, E = 2 + NDIM, A = 3 + NDIM;
-  // The FP32 path works in deviation form about node i (see the file header).
-  constexpr bool DEV = sizeof(R) == 4;
   S sm(smem_raw);
   const int tid = threadIdx.x;
   const int tile0 = geo.tile0;  // first midpoint (= left face of cell tile0)
@@ -497,7 +569,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
     const int s = DIR == 0 ? q % T::NS : q / T::TL;
     const Line ln = geo.line(l);
     const int n = ln.n;
-    int pos = tile0 - 3 + s;
+    const int pos = tile0 - 3 + s;
     double w[NF];
     bool dirichlet = false, flip = false;
     int src = pos;
@@ -525,7 +597,10 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
       for (int f = 0; f < NF; ++f) w[f] = __ldg(a.W_in + (long long)f * N + idx);
       if (flip) w[2 + DIR] = -w[2 + DIR];
     }
-    // Sec. 2: p from rho e, rho c^2 = gbar (p + pbar), rho ctilde^2 = rho e - pbar.
+    // Sec. 2, with Gamma = 1/(gbar-1) and Pi = gbar pbar/(gbar-1):
+    //   p = (rho e - Pi)/Gamma,  pbar = Pi/(Gamma+1),
+    //   rho c^2 = gbar (p + pbar) = ((Gamma+1) rho e - Pi)/Gamma^2,
+    // with one division for 1/rho and one for 1/(Gamma (Gamma+1)).
     const double rho = w[0] + w[1];
     const double ir = 1.0 / rho;
     double v[NDIM], m2 = 0.0;
@@ -537,12 +612,11 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
     const double rhoe = w[E] - 0.5 * m2;
     const double Gam = mixGamma(eos, w[A]);
     const double Pi = mixPi(eos, w[A]);
-    const double iG = 1.0 / Gam;
+    const double x = 1.0 / (Gam * (Gam + 1.0));
+    const double iG = (Gam + 1.0) * x;
     const double p = (rhoe - Pi) * iG;
-    const double pbar = Pi / (Gam + 1.0);
-    const double rc2 = (1.0 + iG) * (p + pbar);
-    const double c = sqrt(rc2 * ir);
-    const double rct = rhoe - pbar;
+    const double c = sqrt(((Gam + 1.0) * rhoe - Pi) * (iG * iG) * ir);
+    const double rct = rhoe - Pi * (Gam * x);
     const int slot = S::nslot(l, s);
 #pragma unroll
     for (int f = 0; f < NF; ++f) sm.W[f * T::NN + slot] = w[f];
@@ -569,8 +643,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
 
   const double dt = geo.dt();
   const double lam = geo.lam();
-  R epsR = (R)a.eps_is;
-  if (sizeof(R) == 4) epsR = fmax(epsR, R(1e-30));
+  const double epsR = a.eps_is;
 
   // ---- 3: midpoint fluxes ---------------------------------------------------
   int nlim_i = 0, nhard_i = 0, nlim_f = 0, nhard_f = 0;
@@ -582,69 +655,24 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
     const Line lnm = geo.line(l);
     const int cnt = (m < T::TM - 1 || tile0 + m == lnm.n) && tile0 + m <= lnm.n && lnm.valid;
     const int ni = S::nslot(l, si), ni1 = S::nslot(l, si + 1);
-    double Wi[NF], Wi1[NF], vi[NDIM], Gi[NF];
+    double Wi[NF], Wi1[NF], vi[NDIM];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       Wi[f] = sm.W[f * T::NN + ni];
       Wi1[f] = sm.W[f * T::NN + ni1];
-      Gi[f] = sm.G[f * T::NN + ni];
     }
 #pragma unroll
     for (int j = 0; j < NDIM; ++j) vi[j] = sm.vel[j * T::NN + ni];
     const double pi_ = sm.p[ni];
-    const double ui = vi[DIR];
 
-    // Deviation of node (l, s) from node i in primitive variables
-    // (a1r1, a2r2, u_1..u_ndim, p, alpha1), rounded to R.
-    auto node_dev = [&](int s, R *dv) {
-      const int sl = S::nslot(l, s);
-      dv[0] = (R)(sm.W[0 * T::NN + sl] - Wi[0]);
-      dv[1] = (R)(sm.W[1 * T::NN + sl] - Wi[1]);
-#pragma unroll
-      for (int k = 0; k < NDIM; ++k) dv[2 + k] = (R)(sm.vel[k * T::NN + sl] - vi[k]);
-      dv[E] = (R)(sm.p[sl] - pi_);
-      dv[A] = (R)(sm.W[A * T::NN + sl] - Wi[A]);
-    };
-    RefNode<NDIM, R> ref;
-    if (DEV) {
-      ref.r1 = (R)Wi[0];
-      ref.r2 = (R)Wi[1];
-      ref.rho = (R)(Wi[0] + Wi[1]);
-#pragma unroll
-      for (int j = 0; j < NDIM; ++j) ref.u[j] = (R)vi[j];
-      ref.p = (R)pi_;
-      ref.Ep = (R)(Wi[E] + pi_);
-      ref.a1 = (R)Wi[A];
-    }
-
-    // First-order HLLC flux from the nodes (Sec. 3.2), in R.
+    // First-order HLLC flux from the nodes (Sec. 3.2).
     double GH[NF], uH;
-    if (DEV) {
-      R d0[NF], d1[NF], dG[NF], ss;
+    {
+      double vr[NDIM];
 #pragma unroll
-      for (int f = 0; f < NF; ++f) d0[f] = R(0);
-      node_dev(si + 1, d1);
-      hllc_dev<NDIM, DIR, R>(ref, eos, d0, (R)sm.c[ni], d1, (R)sm.c[ni1], dG, ss);
-#pragma unroll
-      for (int f = 0; f < NF; ++f) GH[f] = Gi[f] + (double)dG[f];
-      uH = (double)ss;
-    } else {
-      R wl[NF], wr[NF], vl[NDIM], vr[NDIM], G[NF], ss;
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        wl[f] = (R)Wi[f];
-        wr[f] = (R)Wi1[f];
-      }
-#pragma unroll
-      for (int j = 0; j < NDIM; ++j) {
-        vl[j] = (R)vi[j];
-        vr[j] = (R)sm.vel[j * T::NN + ni1];
-      }
-      hllc<NDIM, DIR, R>(wl, vl, (R)pi_, wl[0] + wl[1], (R)sm.c[ni], wr, vr, (R)sm.p[ni1], wr[0] + wr[1],
-                         (R)sm.c[ni1], G, ss);
-#pragma unroll
-      for (int f = 0; f < NF; ++f) GH[f] = (double)G[f];
-      uH = (double)ss;
+      for (int j = 0; j < NDIM; ++j) vr[j] = sm.vel[j * T::NN + ni1];
+      hllc<NDIM, DIR, double>(Wi, vi, pi_, Wi[0] + Wi[1], sm.c[ni], Wi1, vr, sm.p[ni1], Wi1[0] + Wi1[1],
+                              sm.c[ni1], GH, uH);
     }
     double GHm[NF], GHp[NF];
 #pragma unroll
@@ -662,21 +690,27 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
     } else {
       // Steps 1-2: primitive deviations from node i, projected with
       // Rinv_{i+1/2} (App. A; means of a1r1, a2r2, rho and c of nodes i, i+1).
-      const R ar1 = R(0.5) * (R)(Wi[0] + Wi1[0]);
-      const R ar2 = R(0.5) * (R)(Wi[1] + Wi1[1]);
-      const R rb = ar1 + ar2;
-      const R cb = R(0.5) * (R)(sm.c[ni] + sm.c[ni1]);
-      const R irc = Prec<R>::div(R(1), rb * cb);
-      const R k1 = ar1 * irc / cb, k2 = ar2 * irc / cb;
-      R U[6][NF];
+      const double ar1 = 0.5 * (Wi[0] + Wi1[0]);
+      const double ar2 = 0.5 * (Wi[1] + Wi1[1]);
+      const double rb = ar1 + ar2;
+      const double cb = 0.5 * (sm.c[ni] + sm.c[ni1]);
+      const double irc = 1.0 / (rb * cb);
+      const double k1 = ar1 * irc / cb, k2 = ar2 * irc / cb;
+      double U[6][NF];
 #pragma unroll
       for (int j = 0; j < 6; ++j) {
-        R dv[NF];
+        double dv[NF];
         if (j == 2) {
 #pragma unroll
-          for (int f = 0; f < NF; ++f) dv[f] = R(0);
+          for (int f = 0; f < NF; ++f) dv[f] = 0.0;
         } else {
-          node_dev(m + j, dv);
+          const int sl = S::nslot(l, m + j);
+          dv[0] = sm.W[0 * T::NN + sl] - Wi[0];
+          dv[1] = sm.W[1 * T::NN + sl] - Wi[1];
+#pragma unroll
+          for (int k = 0; k < NDIM; ++k) dv[2 + k] = sm.vel[k * T::NN + sl] - vi[k];
+          dv[E] = sm.p[sl] - pi_;
+          dv[A] = sm.W[A * T::NN + sl] - Wi[A];
         }
         U[j][0] = dv[2 + DIR] - irc * dv[E];
         U[j][1] = dv[0] - k1 * dv[E];
@@ -689,47 +723,37 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
         U[j][NF - 1] = dv[2 + DIR] + irc * dv[E];
       }
       // Step 3: left/right WCNS-IS per characteristic field.
-      R UL[NF], UR[NF];
+      double UL[NF], UR[NF];
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
-        UL[f] = wenois<R>(U[0][f], U[1][f], R(0), U[3][f], U[4][f], epsR);
-        UR[f] = wenois<R>(U[5][f], U[4][f], U[3][f], R(0), U[1][f], epsR);
+        UL[f] = wenois<double>(U[0][f], U[1][f], 0.0, U[3][f], U[4][f], epsR);
+        UR[f] = wenois<double>(U[5][f], U[4][f], U[3][f], 0.0, U[1][f], epsR);
       }
-      // Step 4: back-project to primitive deviations.
-      R dV[2][NF];
+      // Steps 4-5: back-project, add node i, V -> W.
+      double WL[NF], WR[NF], VL[NF], VR[NF];  // V: (a1r1, a2r2, vel.., p, a1)
+      const double h1 = ar1 / (2.0 * cb), h2 = ar2 / (2.0 * cb);
 #pragma unroll
       for (int side = 0; side < 2; ++side) {
-        const R *Us = side ? UR : UL;
-        R *d = dV[side];
-        const R dac = Us[NF - 1] - Us[0];
-        d[0] = Us[1] + Prec<R>::div(ar1, R(2) * cb) * dac;
-        d[1] = Us[2] + Prec<R>::div(ar2, R(2) * cb) * dac;
+        const double *Us = side ? UR : UL;
+        double *V = side ? VR : VL;
+        double *W = side ? WR : WL;
+        const double dac = Us[NF - 1] - Us[0];
+        V[0] = Wi[0] + (Us[1] + h1 * dac);
+        V[1] = Wi[1] + (Us[2] + h2 * dac);
         int row = 3;
 #pragma unroll
         for (int k = 0; k < NDIM; ++k) {
+          double dvk;
           if (k == DIR) {
-            d[2 + k] = R(0.5) * (Us[0] + Us[NF - 1]);
+            dvk = 0.5 * (Us[0] + Us[NF - 1]);
           } else {
-            d[2 + k] = Us[row];
+            dvk = Us[row];
             ++row;
           }
+          V[2 + k] = vi[k] + dvk;
         }
-        d[E] = R(0.5) * rb * cb * dac;
-        d[A] = Us[NF - 2];
-      }
-      // Step 5: V -> W in FP64 (node i plus deviation).
-      double WL[NF], WR[NF], VL[NF], VR[NF];  // V: (a1r1, a2r2, vel.., p, a1)
-#pragma unroll
-      for (int side = 0; side < 2; ++side) {
-        const R *d = dV[side];
-        double *V = side ? VR : VL;
-        double *W = side ? WR : WL;
-        V[0] = Wi[0] + (double)d[0];
-        V[1] = Wi[1] + (double)d[1];
-#pragma unroll
-        for (int k = 0; k < NDIM; ++k) V[2 + k] = vi[k] + (double)d[2 + k];
-        V[E] = pi_ + (double)d[E];
-        V[A] = Wi[A] + (double)d[A];
+        V[E] = pi_ + 0.5 * rb * cb * dac;
+        V[A] = Wi[A] + Us[NF - 2];
         const double rho = V[0] + V[1];
         double k2s = 0.0;
 #pragma unroll
@@ -743,104 +767,50 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
         W[A] = V[A];
       }
       // Interpolation limiter (Sec. 5.1): left toward W_i, right toward W_{i+1}.
-      bool changed[2] = {false, false};
       if (a.scheme == SCHEME_PP) {
-        const int fl = interp_limit<NDIM>(eos, a.tol, Wi, sm.rct[ni], WL);
-        const int fr = interp_limit<NDIM>(eos, a.tol, Wi1, sm.rct[ni1], WR);
-        nlim_i += cnt * ((fl & 1) + (fr & 1));
-        nhard_i += cnt * ((fl >> 1) + (fr >> 1));
-        changed[0] = fl != 0;
-        changed[1] = fr != 0;
-      }
-      // A limited state: primitive values again from its conservative vector.
 #pragma unroll
-      for (int side = 0; side < 2; ++side) {
-        if (!changed[side]) continue;
-        const double *W = side ? WR : WL;
-        double *V = side ? VR : VL;
-        const double rho = W[0] + W[1];
-        const double ir = 1.0 / rho;
-        double m2 = 0.0;
+        for (int side = 0; side < 2; ++side) {
+          double *W = side ? WR : WL;
+          double *V = side ? VR : VL;
+          const int fl = interp_limit<NDIM>(eos, a.tol, side ? Wi1 : Wi, W);
+          nlim_i += cnt * (fl & 1);
+          nhard_i += cnt * (fl >> 1);
+          if (fl) {  // a limited state: primitives again from W
+            const double r = W[0] + W[1];
+            const double ir = 1.0 / r;
+            double mm = 0.0;
 #pragma unroll
-        for (int k = 0; k < NDIM; ++k) {
-          V[2 + k] = W[2 + k] * ir;
-          m2 = fma(W[2 + k], V[2 + k], m2);
-        }
-        V[0] = W[0];
-        V[1] = W[1];
-        V[E] = (W[E] - 0.5 * m2 - mixPi(eos, W[A])) / mixGamma(eos, W[A]);
-        V[A] = W[A];
-        if (DEV) {
-          R *d = dV[side];
-          d[0] = (R)(V[0] - Wi[0]);
-          d[1] = (R)(V[1] - Wi[1]);
-#pragma unroll
-          for (int k = 0; k < NDIM; ++k) d[2 + k] = (R)(V[2 + k] - vi[k]);
-          d[E] = (R)(V[E] - pi_);
-          d[A] = (R)(V[A] - Wi[A]);
+            for (int k = 0; k < NDIM; ++k) {
+              V[2 + k] = W[2 + k] * ir;
+              mm = fma(W[2 + k], V[2 + k], mm);
+            }
+            V[0] = W[0];
+            V[1] = W[1];
+            V[E] = (W[E] - 0.5 * mm - mixPi(eos, W[A])) / mixGamma(eos, W[A]);
+            V[A] = W[A];
+          }
         }
       }
-      // Step 6: midpoint HLLC (sound speeds from the mixture EOS, Sec. 2).
-      R cs[2];
+      // Step 6: midpoint HLLC; rho c^2 = ((Gamma+1) p + Pi)/Gamma (Sec. 2).
+      double Gt[NF], ut, cs[2];
 #pragma unroll
       for (int side = 0; side < 2; ++side) {
         const double *V = side ? VR : VL;
-        if (DEV) {
-          const R *d = dV[side];
-          const R a1 = ref.a1 + d[A];
-          const R Gam = (R)eos.r2 + (R)(eos.r1 - eos.r2) * a1;
-          const R pb = Prec<R>::div((R)eos.q1 * a1, Gam + R(1));
-          const R rho = ref.rho + d[0] + d[1];
-          cs[side] = Prec<R>::sqrt_(Prec<R>::div((R(1) + Prec<R>::div(R(1), Gam)) * (ref.p + d[E] + pb), rho));
-        } else {
-          const double Gam = mixGamma(eos, V[A]);
-          const double pb = mixPi(eos, V[A]) / (Gam + 1.0);
-          cs[side] = (R)sqrt((1.0 + 1.0 / Gam) * (V[E] + pb) / (V[0] + V[1]));
-        }
+        const double Gam = mixGamma(eos, V[A]);
+        cs[side] = sqrt(((Gam + 1.0) * V[E] + mixPi(eos, V[A])) / (Gam * (V[0] + V[1])));
       }
-      // Steps 7-8: HCS reconstruction of G-hat, u-hat (node fluxes, velocities).
-      double Gh[NF], uh;
-      if (DEV) {
-        R dGt[NF], ut;
-        hllc_dev<NDIM, DIR, R>(ref, eos, dV[0], cs[0], dV[1], cs[1], dGt, ut);
-        // G^ - G_i = psi (G~ - G_i) + sum_k c_k (G_k - G_i)  (weights sum to 1)
-        const int sm2 = S::nslot(l, m), sm1 = S::nslot(l, m + 1), sp2 = S::nslot(l, m + 4),
-                  sp3 = S::nslot(l, m + 5);
+      hllc<NDIM, DIR, double>(WL, VL + 2, VL[E], VL[0] + VL[1], cs[0], WR, VR + 2, VR[E], VR[0] + VR[1], cs[1],
+                              Gt, ut);
+      // Steps 7-8: HCS reconstruction from node fluxes and velocities.
+      double Gh[NF];
+      const int s0 = S::nslot(l, m), s1 = S::nslot(l, m + 1), s4 = S::nslot(l, m + 4), s5 = S::nslot(l, m + 5);
 #pragma unroll
-        for (int f = 0; f < NF; ++f) {
-          const double *g = sm.G + f * T::NN;
-          const R dh = hcs<R>(dGt[f], (R)(g[sm2] - Gi[f]), (R)(g[sm1] - Gi[f]), R(0), (R)(g[ni1] - Gi[f]),
-                              (R)(g[sp2] - Gi[f]), (R)(g[sp3] - Gi[f]));
-          Gh[f] = Gi[f] + (double)dh;
-        }
-        const double *un = sm.vel + DIR * T::NN;
-        const R duh = hcs<R>(ut - ref.u[DIR], (R)(un[sm2] - ui), (R)(un[sm1] - ui), R(0), (R)(un[ni1] - ui),
-                             (R)(un[sp2] - ui), (R)(un[sp3] - ui));
-        uh = ui + (double)duh;
-      } else {
-        R wl[NF], wr[NF], vl[NDIM], vr[NDIM], Gt[NF], ut;
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-          wl[f] = (R)WL[f];
-          wr[f] = (R)WR[f];
-        }
-#pragma unroll
-        for (int k = 0; k < NDIM; ++k) {
-          vl[k] = (R)VL[2 + k];
-          vr[k] = (R)VR[2 + k];
-        }
-        hllc<NDIM, DIR, R>(wl, vl, (R)VL[E], wl[0] + wl[1], cs[0], wr, vr, (R)VR[E], wr[0] + wr[1], cs[1], Gt,
-                           ut);
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-          const double *g = sm.G + f * T::NN;
-          Gh[f] = (double)hcs<R>(Gt[f], (R)g[S::nslot(l, m)], (R)g[S::nslot(l, m + 1)], (R)g[ni], (R)g[ni1],
-                                 (R)g[S::nslot(l, m + 4)], (R)g[S::nslot(l, m + 5)]);
-        }
-        const double *un = sm.vel + DIR * T::NN;
-        uh = (double)hcs<R>(ut, (R)un[S::nslot(l, m)], (R)un[S::nslot(l, m + 1)], (R)un[ni], (R)un[ni1],
-                            (R)un[S::nslot(l, m + 4)], (R)un[S::nslot(l, m + 5)]);
+      for (int f = 0; f < NF; ++f) {
+        const double *g = sm.G + f * T::NN;
+        Gh[f] = hcs<double>(Gt[f], g[s0], g[s1], g[ni], g[ni1], g[s4], g[s5]);
       }
+      const double *un = sm.vel + DIR * T::NN;
+      const double uh = hcs<double>(ut, un[s0], un[s1], un[ni], un[ni1], un[s4], un[s5]);
       // Step 9: G^-_{i+1/2} and G^+_{i+1/2}.
 #pragma unroll
       for (int f = 0; f < NF; ++f) Gm[f] = Gp[f] = Gh[f];
@@ -851,7 +821,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
         double Fi[NF], Fi1[NF];
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
-          Fi[f] = Gi[f];
+          Fi[f] = sm.G[f * T::NN + ni];
           Fi1[f] = sm.G[f * T::NN + ni1];
         }
         Fi[A] = 0.0;
@@ -878,6 +848,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
 #pragma unroll
   for (int j = 0; j < NDIM; ++j) smax_local[j] = 0.0;
   int midpoints_done = 0;
+  const double idx_ = geo.inv_dx();
   for (int q = tid; q < T::TL * (T::TM - 1); q += T::THREADS) {
     const int l = DIR == 0 ? q / (T::TM - 1) : q % T::TL;
     const int m = DIR == 0 ? q % (T::TM - 1) : q / T::TL;
@@ -889,8 +860,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
     const int ml = S::mslot(l, m), mr = S::mslot(l, m + 1);
     double upd[NF];
 #pragma unroll
-    for (int f = 0; f < NF - 1; ++f) upd[f] = (sm.F[f * T::NM + ml] - sm.F[f * T::NM + mr]) * geo.inv_dx();
-    upd[A] = (sm.ap[ml] - sm.am[mr]) * geo.inv_dx();
+    for (int f = 0; f < NF - 1; ++f) upd[f] = (sm.F[f * T::NM + ml] - sm.F[f * T::NM + mr]) * idx_;
+    upd[A] = (sm.ap[ml] - sm.am[mr]) * idx_;
     if (a.epilogue == EPI_WRITE) {
 #pragma unroll
       for (int f = 0; f < NF; ++f) a.L[(long long)f * N + idx] = upd[f];
@@ -910,7 +881,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
         a.W_out[(long long)f * N + idx] = w[f];
       }
       if (!finite) atomicAdd(&a.stats->nonfinite, 1ull);
-      // max(|u_d| + c) of the new state (Sec. 3.3) for the next stage
+      // max(|u_d| + c) of the new state (Sec. 3.3) for the next stage:
+      // c^2 = ((Gamma+1) rho e - Pi)/(Gamma^2 rho)
       const double rho = w[0] + w[1];
       const double ir = 1.0 / rho;
       double m2 = 0.0;
@@ -918,10 +890,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
       for (int j = 0; j < NDIM; ++j) m2 = fma(w[2 + j], w[2 + j], m2);
       const double rhoe = w[E] - 0.5 * m2 * ir;
       const double Gam = mixGamma(eos, w[A]);
-      const double iG = 1.0 / Gam;
-      const double pb = mixPi(eos, w[A]) / (Gam + 1.0);
-      // rho c^2 = gbar (gbar - 1)(rho e - pbar), gbar - 1 = 1/Gamma
-      const double c = sqrt((1.0 + iG) * iG * (rhoe - pb) * ir);
+      const double c = sqrt(((Gam + 1.0) * rhoe - mixPi(eos, w[A])) / (Gam * Gam * rho));
 #pragma unroll
       for (int j = 0; j < NDIM; ++j) {
         const double sj = fabs(w[2 + j] * ir) + c;
