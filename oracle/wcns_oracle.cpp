@@ -365,8 +365,8 @@ static IsOut wcnsis_left(const real *u, double eps) {
   real s[4];
   s[0] = 0.5 * (u0 + up1);
   s[1] = 0.5 * (-um1 + 3.0 * u0);
-  s[2] = (3.0 * u0 + 6.0 * up1 - up2) / 8.0;
-  s[3] = (3.0 * um2 - 10.0 * um1 + 15.0 * u0) / 8.0;
+  s[2] = 0.125 * (3.0 * u0 + 6.0 * up1 - up2);  // x/8 == x*0.125 exactly
+  s[3] = 0.125 * (3.0 * um2 - 10.0 * um1 + 15.0 * u0);
   // Smoothness indicators.
   real b0 = (u0 - up1) * (u0 - up1);
   real b1 = (um1 - u0) * (um1 - u0);
