@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--ny", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--workload", default="shock_bubble",
+                    choices=["shock_bubble", "precision_2048", "convergence", "riemann_batch", "bubble_3d"],
+                    help="shock_bubble (default): the headline line; the others measure the remaining "
+                         "workloads and print their own JSON line")
     return ap.parse_args()
 
 
@@ -405,8 +409,198 @@ def run_gb300(args, world, rank, local):
     s64.close()
 
 
+# ---------------------------------------------------------------------------
+# further workloads (one JSON line each)
+# ---------------------------------------------------------------------------
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _pressure(W, eos, ndim):
+    """Mixture pressure of a conservative state (Sec. 2), for error reports."""
+    a1 = W[3 + ndim]
+    rho = W[0] + W[1]
+    ke = sum(W[2 + j] * W[2 + j] for j in range(ndim)) / rho
+    G = a1 / (eos["gamma_l"] - 1) + (1 - a1) / (eos["gamma_g"] - 1)
+    Pi = a1 * eos["gamma_l"] * eos["pinf_l"] / (eos["gamma_l"] - 1)
+    return (W[2 + ndim] - 0.5 * ke - Pi) / G
+
+
+def _errors(a, b, eos, ndim):
+    """L1 / Linf errors of a against b, relative, in rho, p, alpha1."""
+    out = {}
+    for name, fa, fb in (("rho", a[0] + a[1], b[0] + b[1]), ("p", _pressure(a, eos, ndim), _pressure(b, eos, ndim)),
+                         ("alpha1", a[3 + ndim], b[3 + ndim])):
+        d = (fa - fb).abs()
+        out[name] = {"l1": float(d.sum() / fb.abs().sum()), "linf": float(d.max() / fb.abs().max())}
+    return out
+
+
+def workload_precision(args):
+    """2048x1024 shock/bubble: FP64 vs mixed on the GPU, and both against one
+    step of the FP64 oracle."""
+    import numpy as np
+    import torch
+    from oracle import Oracle
+    from paper_2102_05287_gb300 import problems as P
+    from paper_2102_05287_gb300.wcns import Solver
+    pr = P.shock_bubble_2d(2048, 1024, seed=2)
+    res = {}
+    states = {}
+    one = {}
+    for prec in ("fp64", "mixed"):
+        s = Solver(pr.n, pr.lo, pr.hi, pr.bcs, precision=prec, **pr.eos)
+        W = torch.from_numpy(pr.W).cuda()
+        W1 = W.clone()
+        s.advance_steps(W1, 1, cfl=0.5)
+        one[prec] = W1
+        s.advance_steps(W, args.warmup, cfl=0.5)
+        torch.cuda.synchronize()
+        e0, e1 = _events(torch)
+        e0.record()
+        s.advance_steps(W, args.steps, cfl=0.5)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        res[prec] = {"ms_per_step": ms, "cell_stage_updates_per_s": 3 * pr.ncells / (ms * 1e-3), "stats": s.stats()}
+        states[prec] = W
+        s.close()
+    o = Oracle(pr.n, pr.lo, pr.hi, pr.bcs, **pr.eos)
+    sm = o.max_wavespeed(pr.W)
+    t0 = time.perf_counter()
+    ref = o.rk3_step(pr.W, 0.5 / (sm[0] * pr.n[0] / 2.0 + sm[1] * pr.n[1]))
+    t_or = time.perf_counter() - t0
+    ref = torch.from_numpy(ref)
+    line = {"workload": "precision_2048x1024", "metric": METRIC, "unit": UNIT,
+            "steps": args.steps, "warmup": args.warmup, "results": res,
+            "mixed_speedup_vs_fp64": res["fp64"]["ms_per_step"] / res["mixed"]["ms_per_step"],
+            "mixed_vs_fp64_after_steps": _errors(states["mixed"].cpu(), states["fp64"].cpu(), pr.eos, 2),
+            "one_step_vs_oracle": {"fp64": _errors(one["fp64"].cpu(), ref, pr.eos, 2),
+                                   "mixed": _errors(one["mixed"].cpu(), ref, pr.eos, 2)},
+            "oracle_one_step_s": t_or}
+    print(json.dumps(line), flush=True)
+
+
+def workload_convergence(args):
+    """Smooth 1D interface advection (periodic, alpha1 = 0.5 + 0.25 sin 2 pi x,
+    rho1 = 1000, rho2 = 1, u = 1, p = 1e5, dt = 4e-5 dx, t_end = 1e-3) for
+    N = 64..4096: L1 error of alpha1 against the exact solution and the
+    observed order between successive N, FP64 and mixed.  Each precision's
+    round-off floor is taken as its error at the finest grid (where the
+    scheme's truncation error is below 1e-14); the order is fitted only over
+    the N whose error exceeds 100x that floor (null if fewer than two)."""
+    import numpy as np
+    import torch
+    from paper_2102_05287_gb300 import problems as P
+    from paper_2102_05287_gb300.wcns import Solver
+    rows = []
+    for N in (64, 128, 256, 512, 1024, 2048, 4096):
+        pr = P.advection_1d_smooth(N)
+        steps = int(round(pr.t_end / pr.dt_fixed))
+        row = {"N": N, "steps": steps}
+        for prec in ("fp64", "mixed"):
+            s = Solver(pr.n, pr.lo, pr.hi, pr.bcs, precision=prec, **pr.eos)
+            W = torch.from_numpy(pr.W).cuda()
+            e0, e1 = _events(torch)
+            e0.record()
+            t = s.advance_steps(W, steps, dt_fixed=pr.dt_fixed)
+            e1.record()
+            torch.cuda.synchronize()
+            a = W[-1].cpu().numpy()
+            err = np.abs(a - pr.extra["exact"](t))
+            row[prec] = {"l1_alpha1": float(err.mean()), "linf_alpha1": float(err.max()),
+                         "ms": e0.elapsed_time(e1)}
+            s.close()
+        rows.append(row)
+    fit = {}
+    for prec in ("fp64", "mixed"):
+        for a, b in zip(rows[:-1], rows[1:]):
+            b[prec]["order"] = float(np.log2(a[prec]["l1_alpha1"] / b[prec]["l1_alpha1"]))
+        floor = rows[-1][prec]["l1_alpha1"]
+        use = [r for r in rows if r[prec]["l1_alpha1"] > 100.0 * floor]
+        fit[prec] = {"floor": floor, "N": [r["N"] for r in use], "order": None}
+        if len(use) >= 2:
+            fit[prec]["order"] = float(-np.polyfit(np.log([r["N"] for r in use]),
+                                                   np.log([r[prec]["l1_alpha1"] for r in use]), 1)[0])
+    print(json.dumps({"workload": "convergence_1d_smooth", "t_end": 1e-3, "rows": rows, "fitted_order": fit}),
+          flush=True)
+
+
+def workload_batch(args):
+    """4096 independent 1D two-phase Riemann problems (log-uniform sizes
+    128..8192, seed 3): one persistent launch per stage, CUDA-graph step,
+    autotuned tiles; FP64 and mixed."""
+    import torch
+    from paper_2102_05287_gb300 import problems as P
+    from paper_2102_05287_gb300.wcns import Batch
+    rb = P.riemann_batch()
+    total = int(rb.offsets[-1])
+    res, states = {}, {}
+    for prec in ("fp64", "mixed"):
+        b = Batch(rb.sizes, [0.0] * len(rb.sizes), [1.0] * len(rb.sizes), "transmissive", "transmissive",
+                  precision=prec, **rb.eos)
+        W = torch.from_numpy(rb.W).cuda()
+        b.advance(W, args.warmup, cfl=0.5)  # includes the autotuning run
+        torch.cuda.synchronize()
+        e0, e1 = _events(torch)
+        l0 = b.launches()
+        e0.record()
+        b.advance(W, args.steps, cfl=0.5)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        res[prec] = {"ms_per_step": ms, "cell_stage_updates_per_s": 3 * total / (ms * 1e-3),
+                     "tuning": b.tuning(), "launches_per_step": (b.launches() - l0) / args.steps,
+                     "stats": b.stats()}
+        states[prec] = W
+        b.close()
+    a, bb = states["mixed"], states["fp64"]
+    err = {"l1_rel_rho": float(((a[0] + a[1]) - (bb[0] + bb[1])).abs().sum() / (bb[0] + bb[1]).abs().sum()),
+           "l1_rel_alpha1": float((a[4] - bb[4]).abs().sum() / bb[4].abs().sum())}
+    print(json.dumps({"workload": "riemann_batch_4096", "problems": len(rb.sizes), "cells": total,
+                      "steps": args.steps, "warmup": args.warmup, "results": res,
+                      "mixed_speedup_vs_fp64": res["fp64"]["ms_per_step"] / res["mixed"]["ms_per_step"],
+                      "mixed_vs_fp64_after_steps": err}), flush=True)
+
+
+def workload_3d(args):
+    """3D air-bubble collapse in water, 384^3, 7 fields SoA: mixed (the
+    workload's precision) and FP64, a few SSPRK3 steps each."""
+    import torch
+    from paper_2102_05287_gb300 import problems as P
+    from paper_2102_05287_gb300.wcns import Solver
+    pr = P.bubble_collapse_3d(384)
+    res, states = {}, {}
+    for prec in ("mixed", "fp64"):
+        s = Solver(pr.n, pr.lo, pr.hi, pr.bcs, precision=prec, **pr.eos)
+        W = torch.from_numpy(pr.W).cuda()
+        s.advance_steps(W, 1, cfl=0.5)
+        torch.cuda.synchronize()
+        e0, e1 = _events(torch)
+        k = max(1, min(args.steps, 3))
+        e0.record()
+        s.advance_steps(W, k, cfl=0.5)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / k
+        res[prec] = {"ms_per_step": ms, "steps": k, "cell_stage_updates_per_s": 3 * pr.ncells / (ms * 1e-3),
+                     "stats": s.stats()}
+        states[prec] = W.cpu()
+        del W
+        s.close()
+        torch.cuda.empty_cache()
+    print(json.dumps({"workload": "bubble_collapse_3d_384", "cells": pr.ncells, "results": res,
+                      "mixed_speedup_vs_fp64": res["fp64"]["ms_per_step"] / res["mixed"]["ms_per_step"],
+                      "mixed_vs_fp64_after_steps": _errors(states["mixed"], states["fp64"], pr.eos, 3)}),
+          flush=True)
+
+
 def main():
     args = parse()
+    if args.workload != "shock_bubble":
+        {"precision_2048": workload_precision, "convergence": workload_convergence,
+         "riemann_batch": workload_batch, "bubble_3d": workload_3d}[args.workload](args)
+        return
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)

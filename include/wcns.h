@@ -34,6 +34,8 @@
 extern "C" {
 #endif
 
+/* A handle (wcns_handle or wcns_batch) is not thread-safe: calls on one
+ * handle must not run concurrently. */
 typedef struct wcns_handle wcns_handle;
 
 /* Status codes. */
@@ -149,7 +151,10 @@ int wcns_set_stage_trace(wcns_handle *h, double *W1_out, double *W2_out);
  * uses dt_fixed; otherwise dt = cfl / sum_d tau_d from the state at the
  * start of each step (Sec. 3.3), computed and kept on the device.
  * *t_io (host) holds the start time on entry and the final time on exit.
- * Synchronises once at the end. */
+ * One step (dt kernel and all sweeps) is captured once into a CUDA graph
+ * per (W, dt_fixed, cfl) and replayed on the handle's private stream,
+ * ordered after the caller's pending work; per-kernel timing disables the
+ * graph.  Synchronises once at the end. */
 int wcns_advance_steps(wcns_handle *h, double *W, int nsteps, double cfl, double dt_fixed,
                        double *t_io);
 

@@ -26,6 +26,14 @@ struct wcns_handle {
   StepCtl *ctl;
   DevStats *stats;
   long long launches;
+  // CUDA-graph replay of whole SSPRK3 steps on a private stream
+  cudaStream_t launch_stream;  // stream the launchers use (the caller's, or cap)
+  cudaStream_t cap;
+  cudaEvent_t ev_in, ev_out;
+  cudaGraphExec_t graph;
+  double *graph_W, *graph_t1, *graph_t2;
+  double graph_dt, graph_cfl;
+  int use_graphs;
   // per-kernel timing
   int prof_cap, prof_n;
   long long prof_dropped;
@@ -137,19 +145,19 @@ int launch_reduce(wcns_handle *h, const double *W, int slot) {
   long long blocks = (h->N + threads - 1) / threads;
   if (blocks > 152 * 8) blocks = 152 * 8;
   if (blocks < 1) blocks = 1;
-  reduce_wavespeed_kernel<<<(int)blocks, threads, 0, h->stream>>>(W, h->N, h->ndim, h->eos, h->ctl, slot);
+  reduce_wavespeed_kernel<<<(int)blocks, threads, 0, h->launch_stream>>>(W, h->N, h->ndim, h->eos, h->ctl, slot);
   h->launches++;
   return cuda_status(cudaGetLastError());
 }
 
 int launch_init(wcns_handle *h, double t, double t_end) {
-  init_ctl_kernel<<<1, 1, 0, h->stream>>>(h->ctl, t, t_end);
+  init_ctl_kernel<<<1, 1, 0, h->launch_stream>>>(h->ctl, t, t_end);
   h->launches++;
   return cuda_status(cudaGetLastError());
 }
 
 int launch_begin(wcns_handle *h, double dt_fixed, double cfl, int advance_time) {
-  step_begin_kernel<<<1, 1, 0, h->stream>>>(h->ctl, h->ndim, h->inv_dx[0], h->inv_dx[1], h->inv_dx[2],
+  step_begin_kernel<<<1, 1, 0, h->launch_stream>>>(h->ctl, h->ndim, h->inv_dx[0], h->inv_dx[1], h->inv_dx[2],
                                             dt_fixed, cfl, advance_time);
   h->launches++;
   return cuda_status(cudaGetLastError());
@@ -195,8 +203,8 @@ int launch_sweep(wcns_handle *h, int d, const SweepArgs &a) {
       h->prof_dropped++;
     }
   }
-  cudaError_t e = h->opt.precision == WCNS_MIXED ? launch_sweep_mixed(h->ndim, d, a, h->stream)
-                                                 : launch_sweep_fp64(h->ndim, d, a, h->stream);
+  cudaError_t e = h->opt.precision == WCNS_MIXED ? launch_sweep_mixed(h->ndim, d, a, h->launch_stream)
+                                                 : launch_sweep_fp64(h->ndim, d, a, h->launch_stream);
   if (slot >= 0) cudaEventRecord(h->prof_ev[2 * slot + 1], h->stream);
   h->launches++;
   return cuda_status(e);
@@ -259,9 +267,66 @@ int enqueue_step(wcns_handle *h, double *W, double dt_fixed, double cfl) {
     }
     double *trace = s == 0 ? h->trace_W1 : (s == 1 ? h->trace_W2 : NULL);
     if (trace && cudaMemcpyAsync(trace, Wout, sizeof(double) * (size_t)h->nf * (size_t)h->N,
-                                 cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+                                 cudaMemcpyDeviceToDevice, h->launch_stream) != cudaSuccess)
       return WCNS_E_CUDA;
   }
+  return WCNS_OK;
+}
+
+void drop_graph(wcns_handle *h) {
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  h->graph = NULL;
+  h->graph_W = NULL;
+}
+
+// nsteps SSPRK3 steps.  With graphs enabled (and no per-kernel timing) one
+// step is captured once on the private stream and replayed there, ordered
+// after the caller's pending work by events; otherwise the kernels are
+// launched directly on the caller's stream.
+int run_steps(wcns_handle *h, double *W, int nsteps, double dt_fixed, double cfl) {
+  if (nsteps <= 0) return WCNS_OK;
+  if (!h->use_graphs || h->prof_cap > 0 || !h->cap) {
+    for (int k = 0; k < nsteps; ++k) {
+      int st = enqueue_step(h, W, dt_fixed, cfl);
+      if (st) return st;
+    }
+    return WCNS_OK;
+  }
+  if (cudaEventRecord(h->ev_in, h->stream) != cudaSuccess) return WCNS_E_CUDA;
+  if (cudaStreamWaitEvent(h->cap, h->ev_in, 0) != cudaSuccess) return WCNS_E_CUDA;
+  if (!h->graph || h->graph_W != W || h->graph_dt != dt_fixed || h->graph_cfl != cfl ||
+      h->graph_t1 != h->trace_W1 || h->graph_t2 != h->trace_W2) {
+    drop_graph(h);
+    cudaGraph_t g;
+    h->launch_stream = h->cap;
+    if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      h->launch_stream = h->stream;
+      return WCNS_E_CUDA;
+    }
+    const long long before = h->launches;
+    int st = enqueue_step(h, W, dt_fixed, cfl);
+    h->launches = before;  // counted when replayed
+    cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+    h->launch_stream = h->stream;
+    if (st || e != cudaSuccess) return WCNS_E_CUDA;
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      h->graph = NULL;
+      return WCNS_E_CUDA;
+    }
+    h->graph_W = W;
+    h->graph_dt = dt_fixed;
+    h->graph_cfl = cfl;
+    h->graph_t1 = h->trace_W1;
+    h->graph_t2 = h->trace_W2;
+  }
+  for (int k = 0; k < nsteps; ++k) {
+    if (cudaGraphLaunch(h->graph, h->cap) != cudaSuccess) return WCNS_E_CUDA;
+    h->launches += 1 + 3 * h->ndim;
+  }
+  if (cudaEventRecord(h->ev_out, h->cap) != cudaSuccess) return WCNS_E_CUDA;
+  if (cudaStreamWaitEvent(h->stream, h->ev_out, 0) != cudaSuccess) return WCNS_E_CUDA;
   return WCNS_OK;
 }
 
@@ -341,6 +406,11 @@ int wcns_create(const wcns_grid *g, const wcns_bcs *bcs, double gamma_g, double 
   if (e == cudaSuccess) e = cudaMalloc(&h->stats, sizeof(DevStats));
   if (e == cudaSuccess) e = cudaMemset(h->stats, 0, sizeof(DevStats));
   if (e == cudaSuccess) e = cudaMemset(h->ctl, 0, sizeof(StepCtl));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
+  h->launch_stream = h->stream;
+  h->use_graphs = 1;
   if (e != cudaSuccess) {
     wcns_destroy(h);
     return WCNS_E_CUDA;
@@ -357,6 +427,8 @@ int wcns_set_options(wcns_handle *h, const wcns_options *o) {
     return WCNS_E_INVALID_ARG;
   h->opt = *o;
   h->stream = (cudaStream_t)o->stream;
+  h->launch_stream = h->stream;
+  drop_graph(h);
   return WCNS_OK;
 }
 
@@ -406,7 +478,7 @@ int wcns_rk3_step(wcns_handle *h, double *W, double dt) {
   if (!h || !W || !(dt > 0.0) || !isfinite(dt)) return WCNS_E_INVALID_ARG;
   int st = launch_init(h, 0.0, INFINITY);
   if (!st && h->ndim > 1) st = launch_reduce(h, W, 3);
-  if (!st) st = enqueue_step(h, W, dt, 0.0);
+  if (!st) st = enqueue_step(h, W, dt, 0.0);  // dt varies per call: direct launches
   return st;
 }
 
@@ -416,7 +488,7 @@ int wcns_advance_steps(wcns_handle *h, double *W, int nsteps, double cfl, double
   const double t0 = t_io ? *t_io : 0.0;
   int st = launch_init(h, t0, INFINITY);
   if (!st && (h->ndim > 1 || dt_fixed == 0.0)) st = launch_reduce(h, W, 3);
-  for (int k = 0; k < nsteps && !st; ++k) st = enqueue_step(h, W, dt_fixed, cfl);
+  if (!st) st = run_steps(h, W, nsteps, dt_fixed, cfl);
   if (st) return st;
   if (t_io) {
     StepCtl c;
@@ -436,7 +508,7 @@ int wcns_advance_to(wcns_handle *h, double *W, double t0, double t_end, double c
   StepCtl c;
   int batch = 8;
   for (;;) {
-    for (int k = 0; k < batch && !st; ++k) st = enqueue_step(h, W, 0.0, cfl);
+    st = run_steps(h, W, batch, 0.0, cfl);
     if (st) return st;
     CK(cudaMemcpyAsync(&c, h->ctl, sizeof(StepCtl), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -487,7 +559,9 @@ int wcns_reset_stats(wcns_handle *h) {
 
 int wcns_profile_enable(wcns_handle *h, int capacity) {
   if (!h || capacity < 0) return WCNS_E_INVALID_ARG;
-  if (h->stream) cudaStreamSynchronize(h->stream);
+  // the timing events are re-created: let every launch that records one finish
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->cap) CK(cudaStreamSynchronize(h->cap));
   profile_free(h);
   if (capacity == 0) return WCNS_OK;
   h->prof_ev = (cudaEvent_t *)calloc(2 * (size_t)capacity, sizeof(cudaEvent_t));
@@ -548,7 +622,14 @@ const char *wcns_strerror(int s) {
 
 void wcns_destroy(wcns_handle *h) {
   if (!h) return;
-  if (h->stream) cudaStreamSynchronize(h->stream);
+  cudaStreamSynchronize(h->stream);
+  if (h->cap) cudaStreamSynchronize(h->cap);
+  drop_graph(h);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  h->ev_in = h->ev_out = NULL;
+  h->cap = NULL;
   profile_free(h);
   cudaFree(h->W1);
   cudaFree(h->W2);
@@ -656,6 +737,7 @@ extern "C" int wcns_rk3_step_noalloc(const wcns_grid *g, const wcns_bcs *bcs, do
   h.eos.q1 = gamma_l * pinf_l / (gamma_l - 1.0);
   h.opt = o;
   h.stream = (cudaStream_t)o.stream;
+  h.launch_stream = h.stream;
   const size_t M = (size_t)nf * (size_t)N;
   h.W1 = states;
   h.W2 = states + M;

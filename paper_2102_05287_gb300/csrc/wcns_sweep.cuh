@@ -695,7 +695,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
       const double rb = ar1 + ar2;
       const double cb = 0.5 * (sm.c[ni] + sm.c[ni1]);
       const double irc = 1.0 / (rb * cb);
-      const double k1 = ar1 * irc / cb, k2 = ar2 * irc / cb;
+      const double ic = irc * rb;  // 1/c without another division
+      const double k1 = ar1 * irc * ic, k2 = ar2 * irc * ic;
       double U[6][NF];
 #pragma unroll
       for (int j = 0; j < 6; ++j) {
@@ -731,7 +732,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
       }
       // Steps 4-5: back-project, add node i, V -> W.
       double WL[NF], WR[NF], VL[NF], VR[NF];  // V: (a1r1, a2r2, vel.., p, a1)
-      const double h1 = ar1 / (2.0 * cb), h2 = ar2 / (2.0 * cb);
+      const double h1 = 0.5 * ar1 * ic, h2 = 0.5 * ar2 * ic;
 #pragma unroll
       for (int side = 0; side < 2; ++side) {
         const double *Us = side ? UR : UL;
