@@ -48,6 +48,7 @@ class _Config(C.Structure):
         ("hs_ar", C.c_double),
         ("hs_a", C.c_double),
         ("hs_rc", C.c_double),
+        ("dir_face", (C.c_void_p * 2) * 3),
     ]
 
 
@@ -137,7 +138,7 @@ class Oracle:
 
     def __init__(self, n, lo, hi, bcs, gamma_g, gamma_l, pinf_l, scheme="pp-wcns-is",
                  eps_is=1e-40, tols=(1e-10, 1e-10, 1e-8), hs_tols=(1e-11, 1e-11, 1e-9),
-                 dirichlet=None, counting=False):
+                 dirichlet=None, dirichlet_face=None, counting=False):
         n = list(n)
         ndim = len(n)
         c = _Config()
@@ -152,6 +153,14 @@ class Oracle:
                 if dirichlet is not None and d < ndim and dirichlet[d][s] is not None:
                     for q, v in enumerate(dirichlet[d][s]):
                         c.dirichlet[d][s][q] = float(v)
+        # per-face Dirichlet states: {(axis, side): array (nf, face cells)}
+        self._faces = {}
+        for (d, s), arr in (dirichlet_face or {}).items():
+            a = np.ascontiguousarray(arr, dtype=np.float64)
+            nface = int(np.prod([n[k] for k in range(ndim) if k != d]))
+            assert a.size == (ndim + 4) * nface, (a.shape, nface)
+            self._faces[(d, s)] = a
+            c.dir_face[d][s] = a.ctypes.data
         c.gamma_g, c.gamma_l, c.pinf_l = float(gamma_g), float(gamma_l), float(pinf_l)
         c.scheme = _SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
         c.eps_is = eps_is

@@ -75,6 +75,10 @@ typedef struct {
   double eps_is;                 // epsilon of the IS nonlinear weights
   double eps_ar, eps_a, eps_rc;  // limiter tolerances (Section 5.1)
   double hs_ar, hs_a, hs_rc;     // hard-switch tolerances (Section 5.1)
+  // Optional per-face Dirichlet states: dir_face[d][side] = NULL (use
+  // dirichlet[d][side] everywhere) or [nf][face cells], the face cells
+  // ordered by the other axes in increasing order, the lower one fastest.
+  const double *dir_face[3][2];
 } oc_config;
 
 typedef struct {
@@ -706,7 +710,20 @@ static void gather_line(const oc_config &c, const double *W, int d, int *ijk,
       src = i < 0 ? -1 - i : 2 * n - 1 - i;
       flip = true;
     } else if (kind == OC_BC_DIRICHLET) {
-      for (int q = 0; q < nf; ++q) dst[q] = c.dirichlet[d][side][q];
+      const double *face = c.dir_face[d][side];
+      if (face) {
+        // position of this line on the face: the other axes, lower fastest
+        long fidx = 0, mult = 1;
+        for (int dd = 0; dd < c.ndim; ++dd) {
+          if (dd == d) continue;
+          fidx += mult * ijk[dd];
+          mult *= c.n[dd];
+        }
+        const long nface = mult;
+        for (int q = 0; q < nf; ++q) dst[q] = face[(size_t)q * nface + fidx];
+      } else {
+        for (int q = 0; q < nf; ++q) dst[q] = c.dirichlet[d][side][q];
+      }
       continue;
     }
     int save = ijk[d];
@@ -725,12 +742,29 @@ static void max_wavespeed_impl(const oc_config &c, const double *W, double *out)
   Eos e = make_eos(c);
   for (int d = 0; d < 3; ++d) out[d] = 0.0;
   real w[7] = {};
-  for (long idx = 0; idx < N; ++idx) {
-    for (int q = 0; q < nf; ++q) w[q] = W[(size_t)q * N + idx];
-    Thermo t = thermo(e, c.ndim, w);
+  auto take = [&](const real *ws) {
+    Thermo t = thermo(e, c.ndim, ws);
     for (int d = 0; d < c.ndim; ++d) {
       double s = o_val(o_abs(t.vel[d]) + t.c);
       if (!(s <= out[d])) out[d] = s;  // a NaN wins and stays
+    }
+  };
+  for (long idx = 0; idx < N; ++idx) {
+    for (int q = 0; q < nf; ++q) w[q] = W[(size_t)q * N + idx];
+    take(w);
+  }
+  // Dirichlet ghost states enter the boundary midpoints' fluxes like cells,
+  // so their wave speeds bound dt as well (the other kinds of ghost copy
+  // interior cells and add nothing).
+  for (int dd = 0; dd < c.ndim; ++dd) {
+    for (int side = 0; side < 2; ++side) {
+      if (c.bc[dd][side] != OC_BC_DIRICHLET) continue;
+      const double *face = c.dir_face[dd][side];
+      const long nface = face ? N / c.n[dd] : 1;
+      for (long k = 0; k < nface; ++k) {
+        for (int q = 0; q < nf; ++q) w[q] = face ? face[(size_t)q * nface + k] : c.dirichlet[dd][side][q];
+        take(w);
+      }
     }
   }
 }

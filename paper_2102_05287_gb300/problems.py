@@ -161,6 +161,52 @@ def sedov_multimaterial(N=401, eos=PAPER_EOS):
                    (("transmissive", "transmissive"),), dict(eos), t_end=1e-3, dt_fixed=2.5e-7)
 
 
+def mach10_water_cylinder(nx=1152, ny=768, eos=PAPER_EOS, x_shock=8e-3):
+    """Section 6 Mach 10 shock / water cylinder: [0, 30L] x [-10L, 10L],
+    L = 1 mm, constant extrapolation on every face; water cylinder of
+    diameter 8L at (13L, 0) in air, cells whose centre lies inside it are
+    water (sharp interface); the incident shock stands at x = x_shock
+    (8L, one L upstream of the cylinder: the paper gives the position only
+    in a schematic).  States from the paper's initial-condition table."""
+    L = 1e-3
+    x = _centers(nx, 0.0, 30 * L)
+    y = _centers(ny, -10 * L, 10 * L)
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    water = np.hypot(X - 13 * L, Y) < 4 * L
+    post = X < x_shock
+    eps = 1e-8
+    a1 = np.where(water, 1 - eps, eps)
+    a1r1 = np.where(water, 1000.0, 1e-8)
+    a2r2 = np.where(water, 1e-8, np.where(post, 6.8571, 1.2))
+    u = np.where(post & ~water, 2.8179e3, 0.0)
+    p = np.where(post & ~water, 1.165e7, 1e5)
+    W = conservative(eos, a1r1, a2r2, [u, np.zeros_like(u)], p, a1)
+    tr = ("transmissive", "transmissive")
+    return Problem("mach10_water_cylinder", W, (nx, ny), (0.0, -10 * L), (30 * L, 10 * L), (tr, tr), dict(eos),
+                   cfl=0.5)
+
+
+def mach100_water_jet(nx=1024, ny=512, eos=PAPER_EOS):
+    """Section 6 Mach 100 water jet: [0, 1] x [-0.25, 0.25] filled with
+    ambient air (p 1e5); the left face is a Dirichlet face whose state is a
+    water jet (rho 1000, u 1.5e5, p 1e5) for |y| <= 0.05 and the ambient air
+    elsewhere; constant extrapolation on the other faces.  The face states
+    are in extra["dirichlet_face"][(0, 0)] as a (6, ny) array."""
+    x = _centers(nx, 0.0, 1.0)
+    y = _centers(ny, -0.25, 0.25)
+    eps = 1e-8
+    ones = np.ones((ny, nx))
+    W = conservative(eos, 1e-8 * ones, ones, [0.0 * ones, 0.0 * ones], 1e5 * ones, eps * ones)
+    jet = np.abs(y) <= 0.05
+    face = conservative(eos, np.where(jet, 1000.0, 1e-8), np.where(jet, 1e-8, 1.0),
+                        [np.where(jet, 1.5e5, 0.0), np.zeros(ny)], np.full(ny, 1e5),
+                        np.where(jet, 1 - eps, eps))
+    ambient = conservative(eos, 1e-8, 1.0, [0.0, 0.0], 1e5, eps)
+    bcs = (("dirichlet", "transmissive"), ("transmissive", "transmissive"))
+    return Problem("mach100_water_jet", W, (nx, ny), (0.0, -0.25), (1.0, 0.25), bcs, dict(eos), cfl=0.5,
+                   extra=dict(dirichlet=((ambient, None), (None, None)), dirichlet_face={(0, 0): face}))
+
+
 # ---------------------------------------------------------------------------
 # Benchmark workloads
 # ---------------------------------------------------------------------------

@@ -475,6 +475,99 @@ def test_strong_1d_problems_stay_admissible(name):
         assert _admissible(o, W)
 
 
+def rho_ct2(eos, W, ndim):
+    """rho ctilde^2 = rho e - pbar_inf of every cell (Section 2 mixture rules),
+    written out here independently of the oracle."""
+    g1, p1, g2 = eos["gamma_l"], eos["pinf_l"], eos["gamma_g"]
+    a1 = W[3 + ndim]
+    rho = W[0] + W[1]
+    rhoe = W[2 + ndim] - 0.5 * sum(W[2 + j] ** 2 for j in range(ndim)) / rho
+    G = a1 / (g1 - 1) + (1 - a1) / (g2 - 1)
+    Pi = a1 * g1 * p1 / (g1 - 1)
+    return rhoe - Pi / (G + 1)
+
+
+def in_G(eos, W, ndim):
+    """Every cell finite and in the admissible set G of Section 2."""
+    if not np.all(np.isfinite(W)):
+        return False
+    a1 = W[3 + ndim]
+    return bool(W[0].min() >= 0 and W[1].min() >= 0 and a1.min() >= 0 and a1.max() <= 1
+                and rho_ct2(eos, W, ndim).min() > 0)
+
+
+@pytest.mark.parametrize("name", ["sedov_multimaterial", "sod_gas_liquid", "interface_advection_1d"])
+def test_limiters_are_necessary_1d(name):
+    """Sections 6.2-6.4: WCNS-IS without the two limiters leaves G in its
+    first step on the interface-advection, gas/liquid Sod and multi-material
+    Sedov problems, while PP-WCNS-IS stays in G."""
+    pr = getattr(P, name)()
+    unl = Oracle(pr.n, pr.lo, pr.hi, pr.bcs, scheme="wcns-is", **pr.eos)
+    assert not in_G(pr.eos, unl.rk3_step(pr.W, pr.dt_fixed), 1)
+    pp = Oracle(pr.n, pr.lo, pr.hi, pr.bcs, **pr.eos)
+    W = pr.W
+    for _ in range(50):
+        W = pp.rk3_step(W, pr.dt_fixed)
+        assert in_G(pr.eos, W, 1)
+    assert pp.stats.as_dict()["flux_limited"] > 0
+
+
+def _cfl_dt(o, pr, W, cfl=0.5):
+    sm = o.max_wavespeed(W)
+    return cfl / sum(sm[d] * pr.n[d] / (pr.hi[d] - pr.lo[d]) for d in range(len(pr.n)))
+
+
+def test_limiters_are_necessary_mach10_cylinder():
+    """Section 6, Mach 10 shock / water cylinder: the unlimited scheme fails
+    at once (the squared sound speed turns negative at the incident shock);
+    PP-WCNS-IS keeps every stage state in G."""
+    pr = P.mach10_water_cylinder(96, 64)
+    unl = Oracle(pr.n, pr.lo, pr.hi, pr.bcs, scheme="wcns-is", **pr.eos)
+    assert not in_G(pr.eos, unl.rk3_step(pr.W, _cfl_dt(unl, pr, pr.W)), 2)
+    pp = Oracle(pr.n, pr.lo, pr.hi, pr.bcs, **pr.eos)
+    W = pr.W
+    for _ in range(15):
+        W = pp.rk3_step(W, _cfl_dt(pp, pr, W))
+        assert in_G(pr.eos, W, 2)
+
+
+def test_mach100_jet_inflow_bounds_dt_and_stays_admissible():
+    """Section 6, Mach 100 water jet: the Dirichlet inflow (u = 1.5e5 m/s)
+    enters the max wave speed although no cell holds it yet, and PP-WCNS-IS
+    stays in G as the jet enters."""
+    pr = P.mach100_water_jet(64, 32)
+    o = Oracle(pr.n, pr.lo, pr.hi, pr.bcs, dirichlet=pr.extra["dirichlet"],
+               dirichlet_face=pr.extra["dirichlet_face"], **pr.eos)
+    sm = o.max_wavespeed(pr.W)
+    assert sm[0] > 1.5e5
+    W = pr.W
+    for _ in range(20):
+        W = o.rk3_step(W, _cfl_dt(o, pr, W))
+        assert in_G(pr.eos, W, 2)
+    assert W[0].max() > 100.0  # water has entered the domain
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_dirichlet_face_of_boundary_cells_equals_extrapolation(ndim):
+    """A per-face Dirichlet state equal, line by line, to the boundary cell
+    is exactly constant extrapolation (Section 6 boundary treatment)."""
+    n = (14, 11) if ndim == 2 else (9, 8, 7)
+    W = P.random_admissible(n, seed=21)
+    tr = tuple(("transmissive", "transmissive") for _ in range(ndim))
+    ref_o = make(n, bcs=tr)
+    dt = 0.3 / ref_o.max_wavespeed(W)[:ndim].sum() / max(n)
+    ref = ref_o.rhs(W, dt)
+    for axis in range(ndim):
+        for side in range(2):
+            bcs = tuple(tuple("dirichlet" if (d == axis and s == side) else "transmissive" for s in range(2))
+                        for d in range(ndim))
+            sl = [slice(None)] * (ndim + 1)
+            sl[ndim - axis] = 0 if side == 0 else -1
+            face = np.ascontiguousarray(W[tuple(sl)]).reshape(ndim + 4, -1)
+            o = make(n, bcs=bcs, dirichlet_face={(axis, side): face})
+            np.testing.assert_array_equal(o.rhs(W, dt), ref)
+
+
 def test_water_air_shock_tube_converges_to_exact_solution():
     """1D water-air shock tube against the exact two-stiffened-gas Riemann
     solution: the L1 density error falls with the grid."""
