@@ -122,17 +122,32 @@ void wcns_default_options(wcns_options *opt);
 int wcns_set_options(wcns_handle *h, const wcns_options *opt);
 int wcns_get_options(const wcns_handle *h, wcns_options *opt);
 
+/* A Dirichlet state that varies along a face (Sec. 6, Mach 100 water jet:
+ * the inflow state depends on the position along the left boundary).
+ * W_face is a HOST array of nf * (ncells / n[axis]) doubles, conservative
+ * states laid out [nf][face cells], the face cells ordered by the remaining
+ * axes in increasing order with the lower axis fastest; the three ghost
+ * layers of each line normal to the face take that line's state.  The face
+ * must have kind WCNS_BC_DIRICHLET (else WCNS_E_INVALID_ARG).  The first
+ * call allocates a device copy owned by the handle (later calls overwrite
+ * it in place); W_face = NULL frees it and the face returns to the uniform
+ * state of wcns_bcs.dirichlet.  Synchronises the handle's stream. */
+int wcns_set_dirichlet_face(wcns_handle *h, int axis, int side, const double *W_face);
+
 /* Semi-discrete right-hand side L(W) = dW/dt of Sec. 4 (eq. for dW/dt with
  * G^{x,-}_{i+1/2} - G^{x,+}_{i-1/2}, including the alpha1 div(u) term),
  * summed over the ndim directions.  dt is the Euler step the flux limiter
  * protects (Sec. 5.2): lambda_d = dt / (dx_d sigma_d), sigma_d = tau_d /
- * sum(tau) with tau_d = max(|u_d| + c)/dx_d of W (Sec. 3.3).
+ * sum(tau) with tau_d = max(|u_d| + c)/dx_d of W and the Dirichlet ghost
+ * states (Sec. 3.3).
  * W and dWdt are device arrays of nf * ncells doubles; they must not
  * overlap.  Asynchronous on the handle's stream. */
 int wcns_rhs(wcns_handle *h, const double *W, double *dWdt, double dt);
 
 /* max over cells of (|u_d| + c) for each direction d < ndim (Sec. 3.3);
- * out[d] = 0 for d >= ndim.  out is a HOST array of 3 doubles; synchronises. */
+ * out[d] = 0 for d >= ndim.  Dirichlet ghost states (uniform or per face)
+ * count as cells: they enter the boundary midpoints' fluxes, so their wave
+ * speeds bound dt as well.  out is a HOST array of 3 doubles; synchronises. */
 int wcns_max_wavespeed(wcns_handle *h, const double *W, double out[3]);
 
 /* One SSPRK3 (Shu-Osher) step of size dt, in place on the device array W

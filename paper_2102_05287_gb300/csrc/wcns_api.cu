@@ -18,6 +18,8 @@ struct wcns_handle {
   double dx[3], inv_dx[3];
   int bc[3][2];
   double dirichlet[3][2][7];
+  double *dir_face[3][2];  // optional per-face Dirichlet states (device, [nf][face cells])
+  double *bc_states;       // device copies of the uniform Dirichlet states [3][2][7]
   EosConst eos;
   wcns_options opt;
   cudaStream_t stream;
@@ -87,7 +89,7 @@ __global__ void reduce_wavespeed_kernel(const double *__restrict__ W, long long 
 
 __global__ void init_ctl_kernel(StepCtl *ctl, double t, double t_end) {
   for (int k = 0; k < 4; ++k)
-    for (int d = 0; d < 3; ++d) ctl->smax[k][d] = 0ull;
+    for (int d = 0; d < 3; ++d) ctl->smax[k][d] = ctl->smax_bc[d];
   ctl->dt = 0.0;
   ctl->t = t;
   ctl->t_end = t_end;
@@ -107,7 +109,7 @@ __global__ void step_begin_kernel(StepCtl *ctl, int ndim, double ix0, double ix1
     if (d < ndim) tsum += __longlong_as_double(ctl->smax[0][d]) * ix[d];
   }
   for (int k = 1; k < 4; ++k)
-    for (int d = 0; d < 3; ++d) ctl->smax[k][d] = 0ull;
+    for (int d = 0; d < 3; ++d) ctl->smax[k][d] = ctl->smax_bc[d];
   double dt = dt_fixed > 0.0 ? dt_fixed : cfl / tsum;
   if (!advance_time) {
     ctl->dt = dt;
@@ -177,6 +179,9 @@ SweepArgs base_args(wcns_handle *h, int d) {
     a.dir_lo[q] = h->dirichlet[d][0][q];
     a.dir_hi[q] = h->dirichlet[d][1][q];
   }
+  a.dir_face_lo = h->dir_face[d][0];
+  a.dir_face_hi = h->dir_face[d][1];
+  a.face_n = h->N / h->n[d];
   a.inv_dx = h->inv_dx[d];
   a.eos = h->eos;
   a.tol.eps_ar = h->opt.eps_ar;
@@ -277,6 +282,37 @@ void drop_graph(wcns_handle *h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
   h->graph = NULL;
   h->graph_W = NULL;
+}
+
+// Dirichlet ghost states enter the boundary midpoints' fluxes like cells, so
+// their max(|u_d| + c) bounds dt too (Sec. 3.3).  They are reduced by the
+// same kernel as the cells, into slot 0 of the (reset) step control, and the
+// result is kept as the floor every wave-speed slot starts from.  Called when
+// the boundary data change; every entry point re-initialises the step
+// control afterwards.  Stream-ordered, no allocation.
+int update_bc_wavespeed(wcns_handle *h) {
+  cudaStream_t st = h->stream;
+  cudaError_t e = cudaMemsetAsync(h->ctl, 0, sizeof(StepCtl), st);
+  for (int d = 0; d < h->ndim && e == cudaSuccess; ++d) {
+    for (int s = 0; s < 2 && e == cudaSuccess; ++s) {
+      if (h->bc[d][s] != WCNS_BC_DIRICHLET) continue;
+      const double *src = h->dir_face[d][s];
+      long long n = h->N / h->n[d];
+      if (!src) {
+        double *dst = h->bc_states + (size_t)(2 * d + s) * 7;
+        e = cudaMemcpyAsync(dst, h->dirichlet[d][s], sizeof(double) * h->nf, cudaMemcpyHostToDevice, st);
+        src = dst;
+        n = 1;
+      }
+      if (e != cudaSuccess) break;
+      const long long blocks = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
+      reduce_wavespeed_kernel<<<(int)blocks, 256, 0, st>>>(src, n, h->ndim, h->eos, h->ctl, 0);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->ctl->smax_bc, h->ctl->smax[0], sizeof(h->ctl->smax_bc), cudaMemcpyDeviceToDevice, st);
+  return cuda_status(e);
 }
 
 // nsteps SSPRK3 steps.  With graphs enabled (and no per-kernel timing) one
@@ -406,11 +442,14 @@ int wcns_create(const wcns_grid *g, const wcns_bcs *bcs, double gamma_g, double 
   if (e == cudaSuccess) e = cudaMalloc(&h->stats, sizeof(DevStats));
   if (e == cudaSuccess) e = cudaMemset(h->stats, 0, sizeof(DevStats));
   if (e == cudaSuccess) e = cudaMemset(h->ctl, 0, sizeof(StepCtl));
+  if (e == cudaSuccess) e = cudaMalloc(&h->bc_states, sizeof(double) * 3 * 2 * 7);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
   h->launch_stream = h->stream;
   h->use_graphs = 1;
+  if (e == cudaSuccess && (update_bc_wavespeed(h) != WCNS_OK || cudaStreamSynchronize(h->stream) != cudaSuccess))
+    e = cudaErrorUnknown;
   if (e != cudaSuccess) {
     wcns_destroy(h);
     return WCNS_E_CUDA;
@@ -436,6 +475,28 @@ int wcns_get_options(const wcns_handle *h, wcns_options *o) {
   if (!h || !o) return WCNS_E_INVALID_ARG;
   *o = h->opt;
   return WCNS_OK;
+}
+
+int wcns_set_dirichlet_face(wcns_handle *h, int axis, int side, const double *W_face) {
+  if (!h || axis < 0 || axis >= h->ndim || side < 0 || side > 1) return WCNS_E_INVALID_ARG;
+  if (h->bc[axis][side] != WCNS_BC_DIRICHLET) return WCNS_E_INVALID_ARG;
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->cap) CK(cudaStreamSynchronize(h->cap));
+  const size_t bytes = sizeof(double) * (size_t)h->nf * (size_t)(h->N / h->n[axis]);
+  if (!W_face) {
+    if (h->dir_face[axis][side]) {
+      drop_graph(h);  // the captured launches carry the buffer's address
+      CK(cudaFree(h->dir_face[axis][side]));
+      h->dir_face[axis][side] = NULL;
+    }
+    return update_bc_wavespeed(h);
+  }
+  if (!h->dir_face[axis][side]) {
+    drop_graph(h);
+    CK(cudaMalloc(&h->dir_face[axis][side], bytes));
+  }
+  CK(cudaMemcpy(h->dir_face[axis][side], W_face, bytes, cudaMemcpyHostToDevice));
+  return update_bc_wavespeed(h);
 }
 
 int wcns_set_stage_trace(wcns_handle *h, double *W1_out, double *W2_out) {
@@ -630,6 +691,8 @@ void wcns_destroy(wcns_handle *h) {
   if (h->cap) cudaStreamDestroy(h->cap);
   h->ev_in = h->ev_out = NULL;
   h->cap = NULL;
+  for (int d = 0; d < 3; ++d)
+    for (int s2 = 0; s2 < 2; ++s2) cudaFree(h->dir_face[d][s2]);
   profile_free(h);
   cudaFree(h->W1);
   cudaFree(h->W2);
@@ -637,6 +700,7 @@ void wcns_destroy(wcns_handle *h) {
   cudaFree(h->Wh);
   cudaFree(h->ctl);
   cudaFree(h->stats);
+  cudaFree(h->bc_states);
   free(h);
 }
 
@@ -653,7 +717,7 @@ void wcns_destroy(wcns_handle *h) {
 
 namespace {
 static __device__ __align__(256) double g_noalloc_states[WCNS_NOALLOC_MAX_DOUBLES];
-static __device__ __align__(256) unsigned char g_noalloc_ctl[512];
+static __device__ __align__(256) unsigned char g_noalloc_ctl[1024];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
@@ -742,11 +806,17 @@ extern "C" int wcns_rk3_step_noalloc(const wcns_grid *g, const wcns_bcs *bcs, do
   h.W1 = states;
   h.W2 = states + M;
   h.L = states + 2 * M;
+  // small region: StepCtl | DevStats | uniform Dirichlet states [3][2][7]
+  constexpr size_t kStatsOff = ((sizeof(StepCtl) + 15) / 16) * 16;
+  constexpr size_t kBcOff = ((kStatsOff + sizeof(DevStats) + 15) / 16) * 16;
+  static_assert(kBcOff + sizeof(double) * 42 <= sizeof(g_noalloc_ctl), "no-alloc control region too small");
   h.ctl = (StepCtl *)ctlmem;
-  h.stats = (DevStats *)(ctlmem + ((sizeof(StepCtl) + 15) / 16) * 16);
+  h.stats = (DevStats *)(ctlmem + kStatsOff);
+  h.bc_states = (double *)(ctlmem + kBcOff);
   // The counters keep the previous call's values: clear them.
   if (cudaMemsetAsync(h.stats, 0, sizeof(DevStats), h.stream) != cudaSuccess) return WCNS_E_CUDA;
-  st = launch_init(&h, 0.0, INFINITY);
+  st = update_bc_wavespeed(&h);
+  if (!st) st = launch_init(&h, 0.0, INFINITY);
   if (!st && h.ndim > 1) st = launch_reduce(&h, W, 3);
   if (!st) st = enqueue_step(&h, W, dt, 0.0);
   return st;

@@ -44,6 +44,7 @@ struct BatchGeo {
   __device__ Line line(int) const {
     Line r;
     r.base = base;
+    r.face = 0;
     r.stride = 1;
     r.n = n;
     r.valid = true;

@@ -37,6 +37,8 @@ struct DevStats {
 //   order like their bit patterns, so atomicMax on the bits is exact.
 struct StepCtl {
   unsigned long long smax[4][3];
+  unsigned long long smax_bc[3];  // max(|u_d| + c) of the Dirichlet ghost states: the
+                                  // floor every wave-speed slot starts from
   double dt;        // step size of the current step
   double t;         // time after the current step
   double t_end;     // advance-to target (or +inf)
@@ -58,6 +60,9 @@ struct SweepArgs {
   long long ncell;          // product of n
   int bc_lo, bc_hi;         // boundary kinds of the swept axis
   double dir_lo[7], dir_hi[7];  // Dirichlet ghost states of the swept axis
+  const double *dir_face_lo;    // optional per-face Dirichlet states [nf][face_n]
+  const double *dir_face_hi;    //   (NULL: dir_lo / dir_hi on the whole face)
+  long long face_n;             // cells on a face normal to the swept axis
   double inv_dx;            // 1/dx of the swept axis
   double inv_dx_all[3];     // 1/dx of every axis
   EosConst eos;

@@ -86,21 +86,57 @@ struct SmemMixed {
 // of roundings at 2^-24 each).
 __device__ __forceinline__ float margin(float mag) { return 9.5367431640625e-07f * mag; }
 
-// FP32 check that rho*ctilde^2 = rho e - pbar of a conservative state given
-// by (a1r1, a2r2, m[], E, alpha) is >= eps.  Returns true only if certain.
+// FP32 check that rho ctilde^2 = E - |m|^2/(2 rho) - pbar(alpha1) (Sec. 2)
+// of a conservative state is >= eps, given an FP32 state x whose every
+// component lies within margin(mag[f]) of the exact one.  Each error is
+// propagated: rho, the kinetic energy (through m and rho), pbar (through
+// alpha1, with |d pbar / d alpha1| = q1 (r2 + 1)/(Gamma + 1)^2 <= q1 (r2 + 1)),
+// and the FP32 evaluation itself.  Returns true only if certain.
 template <int NDIM>
-__device__ __forceinline__ bool rct2_certified(const EosConst &e, float a1r1, float a2r2, const float *m, float E,
-                                               float alpha, float magE, double eps) {
-  const float rho = a1r1 + a2r2;
-  if (!(rho > 0.0f)) return false;
-  float m2 = 0.0f;
+__device__ __forceinline__ bool rct2_certified(const EosConst &e, const float *x, const float *mag, double eps) {
+  constexpr int E = 2 + NDIM, A = 3 + NDIM;
+  const float rho = x[0] + x[1];
+  const float drho = margin(mag[0] + mag[1] + fabsf(rho));
+  const float rlo = rho - drho;
+  if (!(rlo > 0.0f)) return false;
+  float m2 = 0.0f, dm2 = 0.0f;
 #pragma unroll
-  for (int j = 0; j < NDIM; ++j) m2 += m[j] * m[j];
+  for (int j = 0; j < NDIM; ++j) {
+    const float mj = x[2 + j], dm = margin(mag[2 + j]);
+    m2 += mj * mj;
+    dm2 += (2.0f * fabsf(mj) + dm) * dm;
+  }
   const float ke = 0.5f * __fdividef(m2, rho);
-  const float Gam = (float)e.r2 + (float)(e.r1 - e.r2) * alpha;
-  const float pb = __fdividef((float)e.q1 * alpha, Gam + 1.0f);
-  const float v = E - ke - pb;
-  return v - margin(magE + ke + pb) * 4.0f >= (float)eps;
+  const float dke = 0.5f * __fdividef(dm2, rlo) + __fdividef(ke * drho, rlo) + margin(ke);
+  const float al = x[A];
+  const float Gam = (float)e.r2 + (float)(e.r1 - e.r2) * al;
+  const float pb = __fdividef((float)e.q1 * al, Gam + 1.0f);
+  const float dpb = (float)e.q1 * ((float)e.r2 + 1.0f) * margin(mag[A]) + margin(pb);
+  const float v = x[E] - ke - pb;
+  return v - (margin(mag[E]) + dke + dpb + margin(fabsf(x[E]) + ke + pb)) >= (float)eps;
+}
+
+// FP64 velocity, pressure and sound speed of a node from its conservative
+// state (Sec. 2), with the FP64 sweep's formulas.
+template <int NDIM>
+__device__ __forceinline__ void node_thermo64(const EosConst &eos, const double *w, double *v, double &p,
+                                              double &c) {
+  constexpr int E = 2 + NDIM, A = 3 + NDIM;
+  const double rho = w[0] + w[1];
+  const double ir = 1.0 / rho;
+  double m2 = 0.0;
+#pragma unroll
+  for (int j = 0; j < NDIM; ++j) {
+    v[j] = w[2 + j] * ir;
+    m2 = fma(w[2 + j], v[j], m2);
+  }
+  const double rhoe = w[E] - 0.5 * m2;
+  const double Gam = mixGamma(eos, w[A]);
+  const double Pi = mixPi(eos, w[A]);
+  const double x = 1.0 / (Gam * (Gam + 1.0));
+  const double iG = (Gam + 1.0) * x;
+  p = (rhoe - Pi) * iG;
+  c = sqrt(((Gam + 1.0) * rhoe - Pi) * (iG * iG) * ir);
 }
 
 template <int NDIM, int DIR, class T, class Geo>
@@ -147,8 +183,14 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
       }
     }
     if (dirichlet) {
+      const double *face = pos < 0 ? a.dir_face_lo : a.dir_face_hi;
+      if (face) {
 #pragma unroll
-      for (int f = 0; f < NF; ++f) w[f] = pos < 0 ? a.dir_lo[f] : a.dir_hi[f];
+        for (int f = 0; f < NF; ++f) w[f] = __ldg(face + (long long)f * a.face_n + ln.face);
+      } else {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) w[f] = pos < 0 ? a.dir_lo[f] : a.dir_hi[f];
+      }
     } else {
       const long long idx = ln.base + (long long)src * ln.stride;
 #pragma unroll
@@ -461,52 +503,66 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
         duh = hcs<R>(ut - ref.u[DIR] - lo_i[2 + DIR], udev(m), udev(m + 1), 0.0f, d1[2 + DIR], udev(m + 4),
                      udev(m + 5));
       }
-      // Flux limiter (Sec. 5.2): FP32 certification of the four half states.
-      if (a.scheme == SCHEME_PP) {
-        bool cert = ok_i == ALL && ok_i1 == ALL;
-        const float ai = hi_i[A], ai1 = hi_i[A] + dal;
-        const float ui = ref.u[DIR];
+    }
+    // alpha1 components of the split high-order flux (Sec. 3.2), evaluated
+    // once: the certification below tests the very values the update applies.
+    const float ai = hi_i[A], ai1 = hi_i[A] + dal, ui = ref.u[DIR];
+    const float gmA = dGh[A] - ai * duh;
+    const float gpA = (ai - ai1) * ui + dGh[A] - ai1 * duh;
+    // Flux limiter (Sec. 5.2): FP32 certification that every quantity of the
+    // four half states is at least its tolerance (then every theta is 1).
+    // margin() is taken over the operands' magnitudes, so cancellation in a
+    // difference is covered; |G_i| 2^-26 covers the rounding of the FP32
+    // node-flux deviations and of G_i + dG in FP64.
+    if (a.scheme == SCHEME_PP) {
+      bool cert = ok_i == ALL && ok_i1 == ALL;
+#pragma unroll 1
+      for (int st = 0; st < 4 && cert; ++st) {
+        // st: 0 = W_i^{HLLC,+}, 1 = W_{i+1}^{HLLC,-}, 2 = W_i^{+}, 3 = W_{i+1}^{-}
+        const bool hl = st < 2;
+        const bool right = st & 1;
+        const float *dg = hl ? dGH : dGh;
+        const float sgn = right ? 1.0f : -1.0f;  // W_i - 2 lam (.), W_{i+1} + 2 lam (.)
+        const float *wn = Wf[right ? 1 : 0];
+        float x[NF], mag[NF];
 #pragma unroll
-        for (int st = 0; st < 4 && cert; ++st) {
-          // st: 0 = W_i^{HLLC,+}, 1 = W_{i+1}^{HLLC,-}, 2 = W_i^{+}, 3 = W_{i+1}^{-}
-          const bool hl = st < 2;
-          const bool right = st & 1;
-          const float *dg = hl ? dGH : dGh;
-          const float du = hl ? sH - ui - lo_i[2 + DIR] : duh;
-          float D[NF];  // flux minus the node's physical flux, FP32
-#pragma unroll
-          for (int f = 0; f < NF - 1; ++f) D[f] = right ? dg[f] - dG1[f] : dg[f];
-          D[A] = right ? -dal * ui + dg[A] - ai1 * du : dg[A] - ai * du;
-          const float sgn = right ? 1.0f : -1.0f;  // W_i - 2 lam (.), W_{i+1} + 2 lam (.)
-          const float *wn = Wf[right ? 1 : 0];
-          float x[NF], mag[NF];
-#pragma unroll
-          for (int f = 0; f < NF; ++f) {
-            x[f] = wn[f] + sgn * l2 * D[f];
-            mag[f] = fabsf(wn[f]) + fabsf(l2 * D[f]);
-          }
-          // 1 - alpha of the node from its hi/lo parts (exact), then the step
-          const float omn = right ? ((1.0f - hi_i[A]) - lo_i[A]) - dal : (1.0f - hi_i[A]) - lo_i[A];
-          const float om = omn - sgn * l2 * D[A];
-          cert = x[0] - margin(mag[0]) >= epsf_ar && x[1] - margin(mag[1]) >= epsf_ar &&
-                 x[A] - margin(mag[A]) >= epsf_a && om - margin(fabsf(omn) + fabsf(l2 * D[A])) >= epsf_a &&
-                 rct2_certified<NDIM>(eos, x[0], x[1], x + 2, x[E], x[A], mag[E], tol.eps_rc * (1.0 + 1e-6));
+        for (int f = 0; f < NF - 1; ++f) {
+          const float D = right ? dg[f] - dG1[f] : dg[f];
+          const float ops = fabsf(dg[f]) + (right ? fabsf(dG1[f]) : 0.0f) + 1.5e-8f * fabsf(sm.Gh[f * T::NN + ni]);
+          x[f] = wn[f] + sgn * l2 * D;
+          mag[f] = fabsf(wn[f]) + l2 * ops;
         }
-        slow_flux = !cert;
+        float DA, opsA;
+        if (hl) {
+          const float du = sH - ui - lo_i[2 + DIR];
+          DA = right ? -dal * ui + dg[A] - ai1 * du : dg[A] - ai * du;
+          opsA = fabsf(dg[A]) + fabsf((right ? ai1 : ai) * du) + (right ? fabsf(dal * ui) : 0.0f);
+        } else {
+          DA = right ? gpA : gmA;
+          opsA = fabsf(DA);
+        }
+        x[A] = wn[A] + sgn * l2 * DA;
+        mag[A] = fabsf(wn[A]) + l2 * opsA;
+        // 1 - alpha of the node from its hi/lo parts, then the step
+        const float omn = right ? ((1.0f - hi_i[A]) - lo_i[A]) - dal : (1.0f - hi_i[A]) - lo_i[A];
+        const float om = omn - sgn * l2 * DA;
+        cert = x[0] - margin(mag[0]) >= epsf_ar && x[1] - margin(mag[1]) >= epsf_ar &&
+               x[A] - margin(mag[A]) >= epsf_a && om - margin(fabsf(omn) + fabsf(dal) + l2 * opsA) >= epsf_a &&
+               rct2_certified<NDIM>(eos, x, mag, tol.eps_rc * (1.0 + 1e-6));
       }
+      slow_flux = !cert;
     }
     // Assemble the FP64 split fluxes G^-_{i+1/2}, G^+_{i+1/2} (Sec. 3.2).
     double Gm[NF], Gp[NF];
-    const double ai64 = sm.W[A * T::NN + ni], ai164 = sm.W[A * T::NN + ni1];
 #pragma unroll
     for (int f = 0; f < NF - 1; ++f) Gm[f] = Gp[f] = sm.G[f * T::NN + ni] + (double)dGh[f];
-    {
-      const float ai = hi_i[A], ai1 = hi_i[A] + dal, ui = ref.u[DIR];
-      Gm[A] = (double)(dGh[A] - ai * duh);
-      Gp[A] = (double)((ai - ai1) * ui + dGh[A] - ai1 * duh);
-    }
+    Gm[A] = (double)gmA;
+    Gp[A] = (double)gpA;
     if (slow_flux) {
-      double GHm[NF], GHp[NF], Fi[NF], Fi1[NF], Wi[NF], Wi1[NF];
+      // The FP64 limiter of the FP64 path, on FP64 node states and the
+      // FP64 first-order HLLC flux (its positivity is what the limiter
+      // falls back on, so it is not taken from the FP32 deviations).
+      double Wi[NF], Wi1[NF], Fi[NF], Fi1[NF], GH[NF], uH;
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         Wi[f] = sm.W[f * T::NN + ni];
@@ -515,18 +571,37 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
         Fi1[f] = sm.G[f * T::NN + ni1];
       }
       Fi[A] = Fi1[A] = 0.0;
-      const double ui64 = (double)hi_i[2 + DIR] + (double)lo_i[2 + DIR];
-      const double uH = (double)sH;
-      const double uh64 = ui64 + (double)duh;
+      {
+        double vi[NDIM], vi1[NDIM], pi_, pi1, ci_, ci1_;
+        node_thermo64<NDIM>(eos, Wi, vi, pi_, ci_);
+        node_thermo64<NDIM>(eos, Wi1, vi1, pi1, ci1_);
+        hllc<NDIM, DIR, double>(Wi, vi, pi_, Wi[0] + Wi[1], ci_, Wi1, vi1, pi1, Wi1[0] + Wi1[1], ci1_, GH, uH);
+      }
+      double GHm[NF], GHp[NF];
 #pragma unroll
-      for (int f = 0; f < NF - 1; ++f) GHm[f] = GHp[f] = Fi[f] + (double)dGH[f];
-      GHm[A] = sm.G[A * T::NN + ni] + (double)dGH[A] - ai64 * uH;
-      GHp[A] = sm.G[A * T::NN + ni] + (double)dGH[A] - ai164 * uH;
-      Gm[A] = sm.G[A * T::NN + ni] + (double)dGh[A] - ai64 * uh64;
-      Gp[A] = sm.G[A * T::NN + ni] + (double)dGh[A] - ai164 * uh64;
-      const int fl = flux_limit<NDIM>(eos, tol, Wi, Wi1, Fi, Fi1, GHm, GHp, lam, Gm, Gp);
-      nlim_f += cnt * (fl & 1);
-      nhard_f += cnt * (fl >> 1);
+      for (int f = 0; f < NF; ++f) GHm[f] = GHp[f] = GH[f];
+      GHm[A] = GH[A] - Wi[A] * uH;
+      GHp[A] = GH[A] - Wi1[A] * uH;
+      const double ui64 = (double)hi_i[2 + DIR] + (double)lo_i[2 + DIR];
+      const double uh64 = ui64 + (double)duh;
+      Gm[A] = sm.G[A * T::NN + ni] + (double)dGh[A] - Wi[A] * uh64;
+      Gp[A] = sm.G[A * T::NN + ni] + (double)dGh[A] - Wi1[A] * uh64;
+      bool finite = true;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) finite = finite && isfinite(Gm[f]) && isfinite(Gp[f]);
+      if (finite) {
+        const int fl = flux_limit<NDIM>(eos, tol, Wi, Wi1, Fi, Fi1, GHm, GHp, lam, Gm, Gp);
+        nlim_f += cnt * (fl & 1);
+        nhard_f += cnt * (fl >> 1);
+      } else {
+        // a non-finite high-order flux: the hard switch of Sec. 5.2
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          Gm[f] = GHm[f];
+          Gp[f] = GHp[f];
+        }
+        nhard_f += cnt;
+      }
     }
     const int ms = mslot(l, m);
 #pragma unroll

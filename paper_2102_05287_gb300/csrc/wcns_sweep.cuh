@@ -497,6 +497,7 @@ struct Smem {
 struct Line {
   long long base;
   long long stride;
+  long long face;  // position of the line on a face normal to it (lower axis fastest)
   int n;
   bool valid;
 };
@@ -516,13 +517,15 @@ struct GridGeo {
       int y = blockIdx.y * T::TL + l;
       r.valid = y < ny;
       y = min(y, ny - 1);
-      r.base = ((long long)blockIdx.z * ny + y) * nx;
+      r.face = (long long)blockIdx.z * ny + y;
+      r.base = r.face * nx;
       r.stride = 1;
       r.n = nx;
     } else {
       int x = blockIdx.y * T::TL + l;
       r.valid = x < nx;
       x = min(x, nx - 1);
+      r.face = (long long)blockIdx.z * nx + x;
       if (DIR == 1) {
         r.base = (long long)blockIdx.z * nx * ny + x;
         r.stride = nx;
@@ -589,8 +592,14 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
       }
     }
     if (dirichlet) {
+      const double *face = pos < 0 ? a.dir_face_lo : a.dir_face_hi;
+      if (face) {
 #pragma unroll
-      for (int f = 0; f < NF; ++f) w[f] = pos < 0 ? a.dir_lo[f] : a.dir_hi[f];
+        for (int f = 0; f < NF; ++f) w[f] = __ldg(face + (long long)f * a.face_n + ln.face);
+      } else {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) w[f] = pos < 0 ? a.dir_lo[f] : a.dir_hi[f];
+      }
     } else {
       const long long idx = ln.base + (long long)src * ln.stride;
 #pragma unroll

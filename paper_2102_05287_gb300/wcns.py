@@ -24,7 +24,7 @@ _PREC = {"fp64": 0, "mixed": 1}
 
 # Every entry point declared in include/wcns.h.
 EXPORTS = [
-    "wcns_create", "wcns_default_options", "wcns_set_options", "wcns_get_options", "wcns_rhs",
+    "wcns_create", "wcns_default_options", "wcns_set_options", "wcns_get_options", "wcns_set_dirichlet_face", "wcns_rhs",
     "wcns_max_wavespeed", "wcns_rk3_step", "wcns_set_stage_trace", "wcns_advance_steps", "wcns_advance_to",
     "wcns_advance_steps_host", "wcns_get_stats", "wcns_reset_stats", "wcns_nfields", "wcns_ncells",
     "wcns_launch_count", "wcns_rk3_step_noalloc", "wcns_profile_enable", "wcns_profile_read", "wcns_strerror", "wcns_destroy", "wcns_batch_create", "wcns_batch_set_options",
@@ -84,6 +84,7 @@ def load(path=LIB_PATH):
         "wcns_default_options": ([P(wcns_options)], None),
         "wcns_set_options": ([vp, P(wcns_options)], i),
         "wcns_get_options": ([vp, P(wcns_options)], i),
+        "wcns_set_dirichlet_face": ([vp, i, i, vp], i),
         "wcns_rhs": ([vp, vp, vp, d], i),
         "wcns_max_wavespeed": ([vp, vp, P(d)], i),
         "wcns_rk3_step": ([vp, vp, d], i),
@@ -161,7 +162,7 @@ class Solver:
 
     def __init__(self, n, lo, hi, bcs, gamma_g, gamma_l, pinf_l, precision="fp64", scheme="pp-wcns-is",
                  eps_is=1e-40, tols=(1e-10, 1e-10, 1e-8), hs_tols=(1e-11, 1e-11, 1e-9), dirichlet=None,
-                 stream=None):
+                 dirichlet_face=None, stream=None):
         import torch
         lib = load()
         self.lib = lib
@@ -196,6 +197,25 @@ class Solver:
         self.stream = stream
         _check(lib.wcns_set_options(self.h, C.byref(o)), "wcns_set_options")
         self.options = o
+        for (d, s), arr in (dirichlet_face or {}).items():
+            self.set_dirichlet_face(d, s, arr)
+
+    def set_dirichlet_face(self, axis, side, W_face):
+        """Per-face Dirichlet states: W_face array-like (nf, face cells) of
+        conservative states, or None to return to the uniform state."""
+        import numpy as np
+        if W_face is None:
+            _check(self.lib.wcns_set_dirichlet_face(self.h, int(axis), int(side), None), "wcns_set_dirichlet_face")
+            return
+        a = np.ascontiguousarray(W_face, dtype=np.float64)
+        nface = 1
+        for k in range(self.ndim):
+            if k != axis:
+                nface *= self.shape[self.ndim - k]
+        if a.size != self.nf * nface:
+            raise ValueError("face array of %d values, expected %d" % (a.size, self.nf * nface))
+        _check(self.lib.wcns_set_dirichlet_face(self.h, int(axis), int(side), C.c_void_p(a.ctypes.data)),
+               "wcns_set_dirichlet_face")
 
     def close(self):
         if getattr(self, "h", None):

@@ -150,6 +150,39 @@ def test_rhs_3d_fp64():
     assert_parity(got, ref, lambda X: o.rhs(X, dt), W)
 
 
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_rhs_with_dirichlet_face_states(ndim):
+    """Per-face Dirichlet states (wcns_set_dirichlet_face) on every axis and
+    side, with states that differ from the boundary cells: RHS and maximum
+    wave speeds (which include the ghost states) against the oracle."""
+    n = (40, 24) if ndim == 2 else (14, 12, 10)
+    W = P.random_admissible(n, seed=22)
+    rng = np.random.default_rng(23)
+    for axis in range(ndim):
+        for side in range(2):
+            bcs = tuple(tuple("dirichlet" if (d == axis and k == side) else "transmissive" for k in range(2))
+                        for d in range(ndim))
+            sl = [slice(None)] * (ndim + 1)
+            sl[ndim - axis] = 0 if side == 0 else -1
+            face = np.ascontiguousarray(W[tuple(sl)]).reshape(ndim + 4, -1).copy()
+            face[2 + axis] *= rng.uniform(-3.0, 3.0, size=face.shape[1])  # faster, either sign
+            # keep the energy consistent with the new momentum (same internal energy)
+            m_old = np.ascontiguousarray(W[tuple(sl)]).reshape(ndim + 4, -1)[2 + axis]
+            rho = face[0] + face[1]
+            face[2 + ndim] += 0.5 * (face[2 + axis] ** 2 - m_old ** 2) / rho
+            dface = {(axis, side): face}
+            o = Oracle(n, (0.0,) * ndim, (1.0,) * ndim, bcs, dirichlet_face=dface, **EOS)
+            s = Solver(n, (0.0,) * ndim, (1.0,) * ndim, bcs, dirichlet_face=dface, **EOS)
+            Wg = torch.from_numpy(W).cuda()
+            np.testing.assert_allclose(np.array(s.max_wavespeed(Wg))[:ndim], o.max_wavespeed(W)[:ndim],
+                                       rtol=1e-13)
+            dt = cfl_dt(o, W)
+            ref = o.rhs(W, dt)
+            got = s.rhs(Wg, dt).cpu().numpy()
+            assert_parity(got, ref, lambda X: o.rhs(X, dt), W)
+            s.close()
+
+
 @pytest.mark.parametrize("ndim", [1, 2, 3])
 def test_max_wavespeed(ndim):
     n = {1: (333,), 2: (45, 37), 3: (13, 11, 9)}[ndim]
