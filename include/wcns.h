@@ -105,6 +105,9 @@ typedef struct {
   long long nonfinite;       /* cells whose update was not finite */
   long long inadmissible;    /* input cells outside G (Sec. 2) */
   long long midpoints;       /* midpoint fluxes evaluated */
+  long long fp64_fallbacks;  /* mixed precision only: interpolated states and
+                                midpoints whose limiter could not be certified
+                                in FP32 and ran in FP64 */
 } wcns_stats;
 
 /* Create a solver for one grid, boundary set and fluid pair.

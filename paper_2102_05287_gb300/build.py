@@ -72,8 +72,9 @@ def build(force=False, verbose=False):
     if verbose:
         for l in logs:
             sys.stdout.write(l)
-    with open(os.path.join(BUILD, "ptxas.log"), "w") as f:
-        f.write("".join(logs))
+    if logs:  # keep the last compile's register / spill report when nothing was rebuilt
+        with open(os.path.join(BUILD, "ptxas.log"), "w") as f:
+            f.write("".join(logs))
     return LIB
 
 

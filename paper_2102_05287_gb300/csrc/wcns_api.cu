@@ -190,7 +190,9 @@ SweepArgs base_args(wcns_handle *h, int d) {
   a.tol.hs_ar = h->opt.hs_ar;
   a.tol.hs_a = h->opt.hs_a;
   a.tol.hs_rc = h->opt.hs_rc;
+  set_cert(a.tol);
   a.eps_is = h->opt.eps_is;
+  a.eps_is32 = (float)fmax(h->opt.eps_is, 1e-30);
   a.scheme = h->opt.scheme;
   a.ctl = h->ctl;
   a.stats = h->stats;
@@ -428,9 +430,7 @@ int wcns_create(const wcns_grid *g, const wcns_bcs *bcs, double gamma_g, double 
       for (int q = 0; q < 7; ++q) h->dirichlet[d][s][q] = bcs->dirichlet[d][s][q];
     }
   }
-  h->eos.r1 = 1.0 / (gamma_l - 1.0);
-  h->eos.r2 = 1.0 / (gamma_g - 1.0);
-  h->eos.q1 = gamma_l * pinf_l / (gamma_l - 1.0);
+  h->eos = make_eos(gamma_g, gamma_l, pinf_l);
   wcns_default_options(&h->opt);
   h->stream = 0;
   const size_t bytes = sizeof(double) * (size_t)h->nf * (size_t)N;
@@ -609,6 +609,7 @@ int wcns_get_stats(wcns_handle *h, wcns_stats *out) {
   out->nonfinite = (long long)s.nonfinite;
   out->inadmissible = (long long)s.inadmissible;
   out->midpoints = (long long)s.midpoints;
+  out->fp64_fallbacks = (long long)s.fp64_fallbacks;
   return WCNS_OK;
 }
 
@@ -796,9 +797,7 @@ extern "C" int wcns_rk3_step_noalloc(const wcns_grid *g, const wcns_bcs *bcs, do
       for (int q = 0; q < 7; ++q) h.dirichlet[d][s2][q] = bcs->dirichlet[d][s2][q];
     }
   }
-  h.eos.r1 = 1.0 / (gamma_l - 1.0);
-  h.eos.r2 = 1.0 / (gamma_g - 1.0);
-  h.eos.q1 = gamma_l * pinf_l / (gamma_l - 1.0);
+  h.eos = make_eos(gamma_g, gamma_l, pinf_l);
   h.opt = o;
   h.stream = (cudaStream_t)o.stream;
   h.launch_stream = h.stream;

@@ -226,7 +226,9 @@ SweepArgs stage_args(wcns_batch *b, int s, const double *Win, double *Wout, cons
   a.tol.hs_ar = b->opt.hs_ar;
   a.tol.hs_a = b->opt.hs_a;
   a.tol.hs_rc = b->opt.hs_rc;
+  set_cert(a.tol);
   a.eps_is = b->opt.eps_is;
+  a.eps_is32 = (float)fmax(b->opt.eps_is, 1e-30);
   a.scheme = b->opt.scheme;
   a.epilogue = EPI_COMBINE;
   a.read_L = 0;
@@ -351,9 +353,7 @@ int wcns_batch_create(int nprob, const int *ncells, const double *lo, const doub
   b->total = total;
   b->bc_lo = bc_lo;
   b->bc_hi = bc_hi;
-  b->eos.r1 = 1.0 / (gamma_l - 1.0);
-  b->eos.r2 = 1.0 / (gamma_g - 1.0);
-  b->eos.q1 = gamma_l * pinf_l / (gamma_l - 1.0);
+  b->eos = make_eos(gamma_g, gamma_l, pinf_l);
   wcns_default_options(&b->opt);
   int dev = 0;
   cudaGetDevice(&dev);
@@ -467,6 +467,7 @@ int wcns_batch_get_stats(wcns_batch *b, wcns_stats *out) {
   out->nonfinite = (long long)s.nonfinite;
   out->inadmissible = (long long)s.inadmissible;
   out->midpoints = (long long)s.midpoints;
+  out->fp64_fallbacks = (long long)s.fp64_fallbacks;
   return WCNS_OK;
 }
 

@@ -12,12 +12,35 @@ struct EosConst {
   double r1;  // 1/(gamma_l - 1)
   double r2;  // 1/(gamma_g - 1)
   double q1;  // gamma_l pinf_l / (gamma_l - 1)
+  double dr;  // r1 - r2
+  float r2f, drf, q1f;  // FP32 copies for the mixed path, rounded once here
 };
+
+inline EosConst make_eos(double gamma_g, double gamma_l, double pinf_l) {
+  EosConst e;
+  e.r1 = 1.0 / (gamma_l - 1.0);
+  e.r2 = 1.0 / (gamma_g - 1.0);
+  e.q1 = gamma_l * pinf_l / (gamma_l - 1.0);
+  e.dr = e.r1 - e.r2;
+  e.r2f = (float)e.r2;
+  e.drf = (float)e.dr;
+  e.q1f = (float)e.q1;
+  return e;
+}
 
 struct LimTol {
   double eps_ar, eps_a, eps_rc;  // Algorithms 1-6 tolerances
   double hs_ar, hs_a, hs_rc;     // hard-switch tolerances
+  // FP32 certification thresholds of the mixed path: eps (1 + 1e-6) rounded
+  // to FP32, so "x >= cert" implies "x >= eps"
+  float cert_ar, cert_a, cert_rc;
 };
+
+inline void set_cert(LimTol &t) {
+  t.cert_ar = (float)(t.eps_ar * (1.0 + 1e-6));
+  t.cert_a = (float)(t.eps_a * (1.0 + 1e-6));
+  t.cert_rc = (float)(t.eps_rc * (1.0 + 1e-6));
+}
 
 // Device counters (accumulated with integer atomics: order-independent).
 struct DevStats {
@@ -28,6 +51,7 @@ struct DevStats {
   unsigned long long nonfinite;
   unsigned long long inadmissible;
   unsigned long long midpoints;
+  unsigned long long fp64_fallbacks;  // mixed path: limiter work not certified in FP32
 };
 
 // Time-step control kept in device memory so that whole steps can run (and
@@ -68,6 +92,7 @@ struct SweepArgs {
   EosConst eos;
   LimTol tol;
   double eps_is;
+  float eps_is32;           // max(eps_is, 1e-30) in FP32 (mixed path)
   int scheme;
   int epilogue;
   int read_L;               // EPI_COMBINE: add the L array (earlier directions)

@@ -29,30 +29,69 @@ namespace wcns {
 #endif
 
 template <int NDIM, int DIR>
-using TileMixed = TileT<(DIR == 0) ? (NDIM == 1 ? 1 : 2) : 16, (DIR == 0) ? 128 : 16,
+using TileMixed = TileT<(DIR == 0) ? (NDIM == 1 ? 1 : 2) : 8, (DIR == 0) ? 128 : 32,
                         (DIR == 0) ? (NDIM == 1 ? 128 : 256) : 256>;
 
 // value = hi + lo: hi keeps the leading 24 bits of the double (truncated),
 // lo is the exact remainder rounded to FP32.  Integer operations only, so
-// the FP64 pipe is not involved.  Values outside FP32's normal range (never
-// met by admissible states, apart from exact zeros) fall back to a
-// conversion with lo = 0.
+// the FP64 pipe is not involved.  Magnitudes below FP32's normal range
+// (2^-126, never met by admissible states apart from exact zeros) give
+// hi = lo = 0 with the sign kept; magnitudes above it give hi = +-inf (NaN
+// stays NaN), lo = 0.
 __device__ __forceinline__ void split_hilo(double v, float &hi, float &lo) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(v);
   const unsigned int sign = (unsigned int)(b >> 63) << 31;
   const int e = (int)((b >> 52) & 0x7FFull);
   const int e32 = e - 1023 + 127;
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
   if (e32 <= 0 || e32 >= 255) {
-    hi = e == 0 ? 0.0f : __double2float_rn(v);
+    const unsigned int nan = (e == 0x7FF && m) ? 0x400000u : 0u;
+    hi = __uint_as_float(e32 <= 0 ? sign : (sign | 0x7F800000u | nan));
     lo = 0.0f;
     return;
   }
-  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
   hi = __uint_as_float(sign | ((unsigned int)e32 << 23) | (unsigned int)(m >> 29));
   const unsigned int low = (unsigned int)(m & 0x1FFFFFFFull);
   const int es = e - 1075 + 127;  // exponent of the last mantissa bit, biased for FP32
   const float scale = es > 0 ? __uint_as_float((unsigned int)es << 23) : 0.0f;
   lo = __uint_as_float(__float_as_uint((float)low * scale) | sign);
+}
+
+// Integer tests on FP64 values (no FP64-pipe compare): finite, and
+// finite-and-nonnegative (-0 counts as nonnegative, NaN and infinities
+// as neither).
+__device__ __forceinline__ bool finite64(double v) {
+  return (__double2hiint(v) & 0x7FF00000) != 0x7FF00000;
+}
+__device__ __forceinline__ bool nonneg64(double v) {
+  const long long b = __double_as_longlong(v);
+  return (b >= 0 && b < 0x7FF0000000000000ll) || b == (long long)0x8000000000000000ull;
+}
+
+// FP32 -> FP64 on the integer pipe (the FP64 pipe is the scarce one):
+// exact for normal numbers, zeros, infinities and NaNs; FP32 subnormals
+// (below 1.2e-38) become zeros of the same sign.
+__device__ __forceinline__ double f2d(float x) {
+  const unsigned int b = __float_as_uint(x);
+  const unsigned int e = (b >> 23) & 0xFFu;
+  const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+  if (e == 0u) return __longlong_as_double((long long)sign);
+  const unsigned long long e64 = e == 0xFFu ? 0x7FFull : (unsigned long long)(e + 896u);
+  const unsigned long long m = (unsigned long long)(b & 0x7FFFFFu) << 29;
+  return __longlong_as_double((long long)(sign | (e64 << 52) | m));
+}
+
+// 1/y for the mixed path's FP64 node work: Newton-Raphson refinement
+// r <- r + r (1 - y r) of an FP32 seed.  The seed, the correctly rounded
+// FP32 reciprocal of y's leading 24 bits, is within ~2^-22 of 1/y; one step
+// squares that to ~2^-44, far below the FP32 precision the rest of the
+// mixed path carries.  y must be finite, nonzero and within FP32's normal
+// range (densities and Gamma of admissible states are).
+__device__ __forceinline__ double recip_nr(double y) {
+  float hi, lo;
+  split_hilo(y, hi, lo);
+  const double r = f2d(__frcp_rn(hi));
+  return fma(r, fma(-y, r, 1.0), r);
 }
 
 // Shared-memory layout of a mixed tile.
@@ -93,7 +132,7 @@ __device__ __forceinline__ float margin(float mag) { return 9.5367431640625e-07f
 // alpha1, with |d pbar / d alpha1| = q1 (r2 + 1)/(Gamma + 1)^2 <= q1 (r2 + 1)),
 // and the FP32 evaluation itself.  Returns true only if certain.
 template <int NDIM>
-__device__ __forceinline__ bool rct2_certified(const EosConst &e, const float *x, const float *mag, double eps) {
+__device__ __forceinline__ bool rct2_certified(const EosConst &e, const float *x, const float *mag, float eps) {
   constexpr int E = 2 + NDIM, A = 3 + NDIM;
   const float rho = x[0] + x[1];
   const float drho = margin(mag[0] + mag[1] + fabsf(rho));
@@ -109,11 +148,11 @@ __device__ __forceinline__ bool rct2_certified(const EosConst &e, const float *x
   const float ke = 0.5f * __fdividef(m2, rho);
   const float dke = 0.5f * __fdividef(dm2, rlo) + __fdividef(ke * drho, rlo) + margin(ke);
   const float al = x[A];
-  const float Gam = (float)e.r2 + (float)(e.r1 - e.r2) * al;
-  const float pb = __fdividef((float)e.q1 * al, Gam + 1.0f);
-  const float dpb = (float)e.q1 * ((float)e.r2 + 1.0f) * margin(mag[A]) + margin(pb);
+  const float Gam = e.r2f + e.drf * al;
+  const float pb = __fdividef(e.q1f * al, Gam + 1.0f);
+  const float dpb = e.q1f * (e.r2f + 1.0f) * margin(mag[A]) + margin(pb);
   const float v = x[E] - ke - pb;
-  return v - (margin(mag[E]) + dke + dpb + margin(fabsf(x[E]) + ke + pb)) >= (float)eps;
+  return v - (margin(mag[E]) + dke + dpb + margin(fabsf(x[E]) + ke + pb)) >= eps;
 }
 
 // FP64 velocity, pressure and sound speed of a node from its conservative
@@ -153,9 +192,7 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
   const EosConst eos = a.eos;
   const LimTol tol = a.tol;
   // Tolerances rounded up into FP32, so "x >= epsf" implies "x >= eps".
-  const float epsf_ar = (float)(tol.eps_ar * (1.0 + 1e-6));
-  const float epsf_a = (float)(tol.eps_a * (1.0 + 1e-6));
-  const float epsf_rc = (float)(tol.eps_rc * (1.0 + 1e-6));
+  const float epsf_ar = tol.cert_ar, epsf_a = tol.cert_a, epsf_rc = tol.cert_rc;
 
   // ---- 1+2: stage nodes, FP64 node work, hi/lo split -----------------------
   for (int q = tid; q < T::NN; q += T::THREADS) {
@@ -199,7 +236,7 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
     }
     // Sec. 2 in FP64: p from rho e (the p + p_inf cancellation).
     const double rho = w[0] + w[1];
-    const double ir = 1.0 / rho;
+    const double ir = recip_nr(rho);
     double v[NDIM], m2 = 0.0;
 #pragma unroll
     for (int j = 0; j < NDIM; ++j) {
@@ -209,7 +246,7 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
     const double rhoe = w[E] - 0.5 * m2;
     const double Gam = mixGamma(eos, w[A]);
     const double Pi = mixPi(eos, w[A]);
-    const double p = (rhoe - Pi) / Gam;
+    const double p = (rhoe - Pi) * recip_nr(Gam);
     const double un = v[DIR];
     double g[NF];
     g[0] = w[0] * un;
@@ -239,8 +276,8 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
     }
     // FP32 sound speed: rho c^2 = gbar (p + pbar) (Sec. 2)
     const float a1 = vh[A] + vl[A];
-    const float Gam32 = (float)eos.r2 + (float)(eos.r1 - eos.r2) * a1;
-    const float pb32 = __fdividef((float)eos.q1 * a1, Gam32 + 1.0f);
+    const float Gam32 = eos.r2f + eos.drf * a1;
+    const float pb32 = __fdividef(eos.q1f * a1, Gam32 + 1.0f);
     const float rho32 = vh[0] + vh[1];
     const float pp = vh[E] + vl[E] + pb32;
     sm.c[slot] = sqrtf(__fdividef((1.0f + __fdividef(1.0f, Gam32)) * pp, rho32));
@@ -255,9 +292,11 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
     if (Gam32 * pp - margin(Gam32 * (fabsf(vh[E]) + pb32)) * 4.0f >= epsf_rc) okb |= 16u;
     sm.ok[slot] = okb;
     if (DIR == 0 && ln.valid && s >= 3 && s < 3 + T::TM - 1 && pos < n) {
-      const double rct = rhoe - Pi / (Gam + 1.0);
-      const bool adm = w[0] >= 0.0 && w[1] >= 0.0 && w[A] >= 0.0 && w[A] <= 1.0 && rct > 0.0 && isfinite(rhoe) &&
-                       isfinite(p);
+      // rho ctilde^2 = rho e - Pi/(Gamma + 1) > 0, multiplied through by
+      // Gamma + 1 > 0; 0 <= alpha1 <= 1 as an integer compare of the bits
+      const bool adm = nonneg64(w[0]) && nonneg64(w[1]) && nonneg64(w[A]) &&
+                       __double_as_longlong(w[A]) <= 0x3FF0000000000000ll && finite64(rhoe) && finite64(p) &&
+                       rhoe * (Gam + 1.0) - Pi > 0.0;
       if (!adm) atomicAdd(&a.stats->inadmissible, 1ull);
     }
   }
@@ -266,11 +305,11 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
   const double dt = geo.dt();
   const double lam = geo.lam();
   const float l2 = (float)(2.0 * lam);
-  const R epsR = fmaxf((float)a.eps_is, 1e-30f);
+  const R epsR = a.eps_is32;
   const unsigned int ALL = 31u;
 
   // ---- 3: midpoint fluxes ---------------------------------------------------
-  int nlim_i = 0, nhard_i = 0, nlim_f = 0, nhard_f = 0;
+  int nlim_i = 0, nhard_i = 0, nlim_f = 0, nhard_f = 0, nslow = 0;
   for (int q = tid; q < T::NM; q += T::THREADS) {
     const int l = DIR == 0 ? q / T::TM : q % T::TL;
     const int m = DIR == 0 ? q % T::TM : q / T::TL;
@@ -320,7 +359,7 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
         Wf[k][2 + j] = rho * u;
         ke += u * u;
       }
-      Wf[k][E] = pk * ((float)eos.r2 + (float)(eos.r1 - eos.r2) * al) + (float)eos.q1 * al + 0.5f * rho * ke;
+      Wf[k][E] = pk * (eos.r2f + eos.drf * al) + eos.q1f * al + 0.5f * rho * ke;
       Wf[k][A] = al;
     }
     ref.Ep = Wf[0][E] + hi_i[E];
@@ -415,8 +454,8 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
       for (int side = 0; side < 2; ++side) {
         const float *d = dV[side];
         const float a1 = ref.a1 + (lo_i[A] + d[A]);
-        const float Gam = (float)eos.r2 + (float)(eos.r1 - eos.r2) * a1;
-        const float pb = __fdividef((float)eos.q1 * a1, Gam + 1.0f);
+        const float Gam = eos.r2f + eos.drf * a1;
+        const float pb = __fdividef(eos.q1f * a1, Gam + 1.0f);
         const float rho = ref.rho + (lo_i[0] + lo_i[1] + d[0] + d[1]);
         cs[side] = sqrtf(__fdividef((1.0f + __fdividef(1.0f, Gam)) * (ref.p + (lo_i[E] + d[E]) + pb), rho));
       }
@@ -433,8 +472,8 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
             const float al = hi_i[A] + (lo_i[A] + d[A]);
             const float om = ((1.0f - hi_i[A]) - lo_i[A]) - d[A];
             const float pt = hi_i[E] + (lo_i[E] + d[E]);
-            const float Gam = (float)eos.r2 + (float)(eos.r1 - eos.r2) * al;
-            const float pb = __fdividef((float)eos.q1 * al, Gam + 1.0f);
+            const float Gam = eos.r2f + eos.drf * al;
+            const float pb = __fdividef(eos.q1f * al, Gam + 1.0f);
             cert = r1 - margin(fabsf(hi_i[0]) + fabsf(d[0])) >= epsf_ar &&
                    r2 - margin(fabsf(hi_i[1]) + fabsf(d[1])) >= epsf_ar &&
                    al - margin(fabsf(hi_i[A]) + fabsf(d[A])) >= epsf_a &&
@@ -442,6 +481,7 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
                    Gam * (pt + pb) - margin(Gam * (fabsf(hi_i[E]) + fabsf(d[E]) + pb)) * 4.0f >= epsf_rc;
           }
           if (cert) continue;
+          nslow += cnt;
           // FP64 path: node i plus deviation, V -> W, Algorithms 1-3.
           const int nk = side ? ni1 : ni;
           double Wn[NF], Wt[NF], V[NF];
@@ -548,16 +588,17 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
         const float om = omn - sgn * l2 * DA;
         cert = x[0] - margin(mag[0]) >= epsf_ar && x[1] - margin(mag[1]) >= epsf_ar &&
                x[A] - margin(mag[A]) >= epsf_a && om - margin(fabsf(omn) + fabsf(dal) + l2 * opsA) >= epsf_a &&
-               rct2_certified<NDIM>(eos, x, mag, tol.eps_rc * (1.0 + 1e-6));
+               rct2_certified<NDIM>(eos, x, mag, epsf_rc);
       }
       slow_flux = !cert;
+      nslow += cnt * (int)slow_flux;
     }
     // Assemble the FP64 split fluxes G^-_{i+1/2}, G^+_{i+1/2} (Sec. 3.2).
     double Gm[NF], Gp[NF];
 #pragma unroll
-    for (int f = 0; f < NF - 1; ++f) Gm[f] = Gp[f] = sm.G[f * T::NN + ni] + (double)dGh[f];
-    Gm[A] = (double)gmA;
-    Gp[A] = (double)gpA;
+    for (int f = 0; f < NF - 1; ++f) Gm[f] = Gp[f] = sm.G[f * T::NN + ni] + f2d(dGh[f]);
+    Gm[A] = f2d(gmA);
+    Gp[A] = f2d(gpA);
     if (slow_flux) {
       // The FP64 limiter of the FP64 path, on FP64 node states and the
       // FP64 first-order HLLC flux (its positivity is what the limiter
@@ -613,6 +654,7 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
   if (nhard_i) atomicAdd(&a.stats->interp_hard, (unsigned long long)nhard_i);
   if (nlim_f) atomicAdd(&a.stats->flux_limited, (unsigned long long)nlim_f);
   if (nhard_f) atomicAdd(&a.stats->flux_hard, (unsigned long long)nhard_f);
+  if (nslow) atomicAdd(&a.stats->fp64_fallbacks, (unsigned long long)nslow);
   __syncthreads();
 
   // ---- 4: cell update (FP64) -------------------------------------------------
@@ -621,6 +663,7 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
   for (int j = 0; j < NDIM; ++j) smax_local[j] = 0.0f;
   int done = 0;
   const double idx_ = geo.inv_dx();
+  const double bdt = a.rk_b * dt, bdt_idx = bdt * idx_;
   for (int q = tid; q < T::TL * (T::TM - 1); q += T::THREADS) {
     const int l = DIR == 0 ? q / (T::TM - 1) : q % T::TL;
     const int m = DIR == 0 ? q % (T::TM - 1) : q / T::TL;
@@ -630,26 +673,31 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
     ++done;
     const long long idx = ln.base + (long long)pos * ln.stride;
     const int ml = mslot(l, m), mr = mslot(l, m + 1);
-    double upd[NF];
+    if (a.epilogue != EPI_COMBINE) {
+      double upd[NF];
 #pragma unroll
-    for (int f = 0; f < NF - 1; ++f) upd[f] = (sm.F[f * T::NM + ml] - sm.F[f * T::NM + mr]) * idx_;
-    upd[A] = (sm.ap[ml] - sm.am[mr]) * idx_;
-    if (a.epilogue == EPI_WRITE) {
+      for (int f = 0; f < NF - 1; ++f) upd[f] = (sm.F[f * T::NM + ml] - sm.F[f * T::NM + mr]) * idx_;
+      upd[A] = (sm.ap[ml] - sm.am[mr]) * idx_;
+      if (a.epilogue == EPI_WRITE) {
 #pragma unroll
-      for (int f = 0; f < NF; ++f) a.L[(long long)f * N + idx] = upd[f];
-    } else if (a.epilogue == EPI_ACCUM) {
+        for (int f = 0; f < NF; ++f) a.L[(long long)f * N + idx] = upd[f];
+      } else {
 #pragma unroll
-      for (int f = 0; f < NF; ++f) a.L[(long long)f * N + idx] += upd[f];
+        for (int f = 0; f < NF; ++f) a.L[(long long)f * N + idx] += upd[f];
+      }
     } else {
       const int ns = nslot(l, m + 3);
       double w[NF];
       bool finite = true;
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
-        const double tot = a.read_L ? a.L[(long long)f * N + idx] + upd[f] : upd[f];
-        const double wn = a.rk_a != 0.0 ? a.Wn[(long long)f * N + idx] : 0.0;
-        w[f] = a.rk_a * wn + a.rk_b * (sm.W[f * T::NN + ns] + dt * tot);
-        finite = finite && isfinite(w[f]);
+        // a W^n + b W + b dt (L + flux difference / dx) (Sec. 5.3 combine)
+        const double diff = f < NF - 1 ? sm.F[f * T::NM + ml] - sm.F[f * T::NM + mr] : sm.ap[ml] - sm.am[mr];
+        double acc = a.rk_b * sm.W[f * T::NN + ns];
+        if (a.rk_a != 0.0) acc = fma(a.rk_a, a.Wn[(long long)f * N + idx], acc);
+        if (a.read_L) acc = fma(bdt, a.L[(long long)f * N + idx], acc);
+        w[f] = fma(bdt_idx, diff, acc);
+        finite = finite && finite64(w[f]);
         a.W_out[(long long)f * N + idx] = w[f];
       }
       if (!finite) atomicAdd(&a.stats->nonfinite, 1ull);
@@ -666,8 +714,8 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
       float m2 = 0.0f;
 #pragma unroll
       for (int j = 0; j < NDIM; ++j) m2 += wf[2 + j] * wf[2 + j];
-      const float Gam = (float)eos.r2 + (float)(eos.r1 - eos.r2) * wf[A];
-      const float pb = __fdividef((float)eos.q1 * wf[A], Gam + 1.0f);
+      const float Gam = eos.r2f + eos.drf * wf[A];
+      const float pb = __fdividef(eos.q1f * wf[A], Gam + 1.0f);
       const float rct = wf[E] - 0.5f * __fdividef(m2, rho) - pb;
       const float iG = __fdividef(1.0f, Gam);
       const float c = sqrtf(fmaxf((1.0f + iG) * iG * rct, 0.0f) / rho);

@@ -249,7 +249,7 @@ __device__ __forceinline__ void hllc_dev(const RefNode<NDIM, R> &ref, const EosC
   sstar = ss;
   R Gs[2][NF];
   const bool need[2] = {!(ss < R(0)), !(ss > R(0))};
-  const R rdiff = (R)(eos.r1 - eos.r2), q1 = (R)eos.q1;
+  const R rdiff = (R)eos.drf, q1 = (R)eos.q1f;
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
     if (!need[k]) continue;
@@ -267,7 +267,7 @@ __device__ __forceinline__ void hllc_dev(const RefNode<NDIM, R> &ref, const EosC
       du2 += d[2 + j] * (R(2) * ref.u[j] + d[2 + j]);
       uk2 += uK[j] * uK[j];
     }
-    const R GammaK = (R)eos.r2 + rdiff * al[k];
+    const R GammaK = (R)eos.r2f + rdiff * al[k];
     const R dE = d[E] * GammaK + (ref.p * rdiff + q1) * d[A] + R(0.5) * (drho * uk2 + ref.rho * du2);
     const R EpK = ref.Ep + dE + d[E];  // (E + p)_K
     // physical-flux deviations
@@ -300,7 +300,7 @@ __device__ __forceinline__ void hllc_dev(const RefNode<NDIM, R> &ref, const EosC
 // ---------------------------------------------------------------------------
 // Sec. 2: mixture EOS helpers (FP64).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double mixGamma(const EosConst &e, double a1) { return fma(a1, e.r1 - e.r2, e.r2); }
+__device__ __forceinline__ double mixGamma(const EosConst &e, double a1) { return fma(a1, e.dr, e.r2); }
 __device__ __forceinline__ double mixPi(const EosConst &e, double a1) { return a1 * e.q1; }
 // pbar = Pi (gbar - 1)/gbar = Pi / (Gamma + 1)
 __device__ __forceinline__ double mixPinf(const EosConst &e, double a1) {

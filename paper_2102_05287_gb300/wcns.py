@@ -50,7 +50,7 @@ class wcns_options(C.Structure):
 
 class wcns_stats(C.Structure):
     _fields_ = [(k, C.c_longlong) for k in ("interp_limited", "interp_hard", "flux_limited", "flux_hard",
-                                            "nonfinite", "inadmissible", "midpoints")]
+                                            "nonfinite", "inadmissible", "midpoints", "fp64_fallbacks")]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
