@@ -362,8 +362,10 @@ def run_gb300(args, world, rank, local):
     src_hash = hashlib.sha256(open(os.path.join(ROOT, "paper_2102_05287_gb300", "csrc", "wcns_sweep.cuh"),
                                    "rb").read()).hexdigest()[:16]
     achieved = flop_eq * ncell / (avg_ms * 1e-3) / 1e12
+    plain = ops["add"] + ops["mul"] + ops["minmax"] + ops["div"] + ops["sqrt"]
     roofline = {"bound": "alu", "achieved": achieved, "peak": p64, "unit": "TFLOP/s", "frac": achieved / p64,
                 "traffic": None,
+                "frac_div_sqrt_as_one_flop": plain * ncell / (avg_ms * 1e-3) / 1e12 / p64,
                 "kernel": "sweep_kernel<2,%d,double> (%s sweep)" % (dom, "xy"[dom]),
                 "avg_launch_ms": avg_ms,
                 "flop_eq_per_cell_dir": flop_eq,
@@ -372,7 +374,8 @@ def run_gb300(args, world, rank, local):
                 "note": "FP64-pipe roofline: add/mul/minmax count 1 flop, div/sqrt count their measured "
                         "cost in FMA-flop equivalents; op mix from the oracle's op-counting build with the "
                         "IS weights counted in their one-division form; peak = measured FP64 FMA rate of "
-                        "this GPU (of measured)"}
+                        "this GPU (of measured). frac_div_sqrt_as_one_flop counts every division and square "
+                        "root as a single flop instead (a lower bound on the fraction)."}
     traffic_file = os.path.join(ROOT, "profiles", "sweep_traffic.json")
     if os.path.exists(traffic_file):
         try:
@@ -557,10 +560,25 @@ def workload_batch(args):
     a, bb = states["mixed"], states["fp64"]
     err = {"l1_rel_rho": float(((a[0] + a[1]) - (bb[0] + bb[1])).abs().sum() / (bb[0] + bb[1]).abs().sum()),
            "l1_rel_alpha1": float((a[4] - bb[4]).abs().sum() / bb[4].abs().sum())}
+    # the oracle on the host: one CFL step of 32 seeded problems of the batch
+    import numpy as np
+    from oracle import Oracle
+    picks = np.random.default_rng(0).choice(len(rb.sizes), 32, replace=False)
+    cells, t0 = 0, time.perf_counter()
+    for k in picks:
+        n = int(rb.sizes[k])
+        W0 = np.ascontiguousarray(rb.W[:, int(rb.offsets[k]):int(rb.offsets[k + 1])])
+        o = Oracle((n,), (0.0,), (1.0,), (("transmissive", "transmissive"),), **rb.eos)
+        o.rk3_step(W0, 0.5 / (o.max_wavespeed(W0)[0] * n))
+        cells += n
+    el = time.perf_counter() - t0
+    cpu = {"value": 3 * cells / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "one SSPRK3 step of 32 seeded problems of the batch (%d cells), single thread, %.1f s"
+                     % (cells, el)}
     print(json.dumps({"workload": "riemann_batch_4096", "problems": len(rb.sizes), "cells": total,
                       "steps": args.steps, "warmup": args.warmup, "results": res,
                       "mixed_speedup_vs_fp64": res["fp64"]["ms_per_step"] / res["mixed"]["ms_per_step"],
-                      "mixed_vs_fp64_after_steps": err}), flush=True)
+                      "mixed_vs_fp64_after_steps": err, "cpu_baseline": cpu}), flush=True)
 
 
 def workload_3d(args):
@@ -589,9 +607,23 @@ def workload_3d(args):
         del W
         s.close()
         torch.cuda.empty_cache()
+    err = _errors(states["mixed"], states["fp64"], pr.eos, 3)
+    del states
+    # the oracle on the host: one CFL step of the same problem at 48^3,
+    # a per-cell-stage rate extrapolated to 384^3
+    from oracle import Oracle
+    small = P.bubble_collapse_3d(48)
+    o = Oracle(small.n, small.lo, small.hi, small.bcs, **small.eos)
+    t0 = time.perf_counter()
+    sm = o.max_wavespeed(small.W)
+    o.rk3_step(small.W, 0.5 / (sum(sm) * 48))
+    el = time.perf_counter() - t0
+    cpu = {"value": 3 * small.ncells / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "one SSPRK3 step of the same problem at 48^3 (single thread, %.1f s), "
+                     "rate extrapolated to 384^3" % el}
     print(json.dumps({"workload": "bubble_collapse_3d_384", "cells": pr.ncells, "results": res,
                       "mixed_speedup_vs_fp64": res["fp64"]["ms_per_step"] / res["mixed"]["ms_per_step"],
-                      "mixed_vs_fp64_after_steps": _errors(states["mixed"], states["fp64"], pr.eos, 3)}),
+                      "mixed_vs_fp64_after_steps": err, "cpu_baseline": cpu}),
           flush=True)
 
 

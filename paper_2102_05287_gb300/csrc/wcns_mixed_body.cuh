@@ -57,17 +57,6 @@ __device__ __forceinline__ void split_hilo(double v, float &hi, float &lo) {
   lo = __uint_as_float(__float_as_uint((float)low * scale) | sign);
 }
 
-// Integer tests on FP64 values (no FP64-pipe compare): finite, and
-// finite-and-nonnegative (-0 counts as nonnegative, NaN and infinities
-// as neither).
-__device__ __forceinline__ bool finite64(double v) {
-  return (__double2hiint(v) & 0x7FF00000) != 0x7FF00000;
-}
-__device__ __forceinline__ bool nonneg64(double v) {
-  const long long b = __double_as_longlong(v);
-  return (b >= 0 && b < 0x7FF0000000000000ll) || b == (long long)0x8000000000000000ull;
-}
-
 // FP32 -> FP64 on the integer pipe (the FP64 pipe is the scarce one):
 // exact for normal numbers, zeros, infinities and NaNs; FP32 subnormals
 // (below 1.2e-38) become zeros of the same sign.

@@ -54,6 +54,17 @@ template <int NDIM, int DIR>
 using Tile = TileT<(DIR == 0) ? (NDIM == 1 ? 1 : 2) : 16, (DIR == 0) ? 128 : 32,
                    (DIR == 0) ? (NDIM == 1 ? 128 : 256) : 256>;
 
+// Integer tests on FP64 values (no FP64-pipe compare): finite, and
+// finite-and-nonnegative (-0 counts as nonnegative, NaN and infinities
+// as neither).
+__device__ __forceinline__ bool finite64(double v) {
+  return (__double2hiint(v) & 0x7FF00000) != 0x7FF00000;
+}
+__device__ __forceinline__ bool nonneg64(double v) {
+  const long long b = __double_as_longlong(v);
+  return (b >= 0 && b < 0x7FF0000000000000ll) || b == (long long)0x8000000000000000ull;
+}
+
 template <class R>
 struct Prec;
 template <>
@@ -644,7 +655,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
     // input admissibility (Sec. 2), counted once per interior cell
     if (DIR == 0 && ln.valid && s >= 3 && s < 3 + T::TM - 1 && pos < n) {
       const bool ok = w[0] >= 0.0 && w[1] >= 0.0 && w[A] >= 0.0 && w[A] <= 1.0 && rct > 0.0 &&
-                      isfinite(rhoe) && isfinite(c);
+                      finite64(rhoe) && finite64(c);
       if (!ok) atomicAdd(&a.stats->inadmissible, 1ull);
     }
   }
@@ -887,7 +898,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
         const double tot = a.read_L ? a.L[(long long)f * N + idx] + upd[f] : upd[f];
         const double wn = a.rk_a != 0.0 ? a.Wn[(long long)f * N + idx] : 0.0;
         w[f] = a.rk_a * wn + a.rk_b * (sm.W[f * T::NN + ns] + dt * tot);
-        finite = finite && isfinite(w[f]);
+        finite = finite && finite64(w[f]);
         a.W_out[(long long)f * N + idx] = w[f];
       }
       if (!finite) atomicAdd(&a.stats->nonfinite, 1ull);
