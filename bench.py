@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--workload", default="shock_bubble",
-                    choices=["shock_bubble", "precision_2048", "convergence", "riemann_batch", "bubble_3d"],
+                    choices=["shock_bubble", "precision_2048", "convergence", "riemann_batch", "bubble_3d", "stress"],
                     help="shock_bubble (default): the headline line; the others measure the remaining "
                          "workloads and print their own JSON line")
     return ap.parse_args()
@@ -627,11 +627,92 @@ def workload_3d(args):
           flush=True)
 
 
+def workload_stress(args):
+    """Section 6 robustness problems at the paper's grids: Mach 10 shock /
+    water cylinder 1152x768 and Mach 100 water jet 1024x512, CFL 0.5.
+    PP-WCNS-IS in FP64 and mixed precision for a fixed number of steps
+    (default 1000): admissibility counters, limiter activity, throughput and
+    the minimum of every bounded quantity at the end; then the unlimited
+    WCNS-IS ablation, stepped until the device counters report a state
+    outside the admissible set (or the same number of steps)."""
+    import numpy as np
+    import torch
+    from paper_2102_05287_gb300 import problems as P
+    from paper_2102_05287_gb300.wcns import Solver
+    nsteps = args.steps if args.steps != 20 else 1000
+    out = []
+    for pr in (P.mach10_water_cylinder(1152, 768), P.mach100_water_jet(1024, 512)):
+        kw = {}
+        if "dirichlet" in pr.extra:
+            kw = dict(dirichlet=pr.extra["dirichlet"], dirichlet_face=pr.extra["dirichlet_face"])
+        row = {"problem": pr.name, "grid": list(pr.n), "steps": nsteps}
+        for prec in ("fp64", "mixed"):
+            s = Solver(pr.n, pr.lo, pr.hi, pr.bcs, precision=prec, **pr.eos, **kw)
+            W = torch.from_numpy(pr.W).cuda()
+            e0, e1 = _events(torch)
+            e0.record()
+            t = s.advance_steps(W, nsteps, cfl=0.5)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / nsteps
+            Wc = W.cpu().numpy()
+            a1 = Wc[-1]
+            rho = Wc[0] + Wc[1]
+            row[prec] = {"t": t, "ms_per_step": ms, "cell_stage_updates_per_s": 3 * pr.ncells / (ms * 1e-3),
+                         "stats": s.stats(), "min_a1r1": float(Wc[0].min()), "min_a2r2": float(Wc[1].min()),
+                         "min_alpha1": float(a1.min()), "min_1_minus_alpha1": float((1 - a1).min()),
+                         "min_rho_ctilde2": float(_rho_ct2(Wc, pr.eos, 2).min()),
+                         "max_rho": float(rho.max())}
+            s.close()
+        # mixed vs FP64 at the same time: the mixed run advanced to the FP64 run's end time
+        s = Solver(pr.n, pr.lo, pr.hi, pr.bcs, precision="mixed", **pr.eos, **kw)
+        Wm = torch.from_numpy(pr.W).cuda()
+        s.advance_to(Wm, 0.0, row["fp64"]["t"], cfl=0.5)
+        s.close()
+        W64 = torch.from_numpy(pr.W).cuda()
+        s = Solver(pr.n, pr.lo, pr.hi, pr.bcs, precision="fp64", **pr.eos, **kw)
+        s.advance_to(W64, 0.0, row["fp64"]["t"], cfl=0.5)
+        s.close()
+        row["mixed_vs_fp64_same_time"] = _errors(Wm.cpu(), W64.cpu(), pr.eos, 2)
+        # the problem's own sensitivity: FP64 from the initial state with
+        # every value perturbed by a seeded relative 1e-15
+        rng = np.random.default_rng(11)
+        Wp = torch.from_numpy(pr.W * (1.0 + 1e-15 * rng.uniform(-1.0, 1.0, pr.W.shape))).cuda()
+        s = Solver(pr.n, pr.lo, pr.hi, pr.bcs, precision="fp64", **pr.eos, **kw)
+        s.advance_to(Wp, 0.0, row["fp64"]["t"], cfl=0.5)
+        s.close()
+        row["fp64_vs_fp64_perturbed_1e-15_same_time"] = _errors(Wp.cpu(), W64.cpu(), pr.eos, 2)
+        del Wm, W64, Wp
+        s = Solver(pr.n, pr.lo, pr.hi, pr.bcs, scheme="wcns-is", **pr.eos, **kw)
+        W = torch.from_numpy(pr.W).cuda()
+        failed_at = None
+        for k in range(nsteps):
+            s.advance_steps(W, 1, cfl=0.5)
+            st = s.stats()
+            if st["inadmissible"] or st["nonfinite"]:
+                failed_at = k  # the state after step k was flagged when step k + 1 read it
+                break
+        row["unlimited_wcns_is"] = {"flagged_after_steps": failed_at, "stats": s.stats()}
+        s.close()
+        out.append(row)
+    print(json.dumps({"workload": "stress_section6", "results": out}), flush=True)
+
+
+def _rho_ct2(W, eos, ndim):
+    """rho ctilde^2 = rho e - pbar of every cell (Sec. 2), for reports."""
+    a1 = W[3 + ndim]
+    rho = W[0] + W[1]
+    rhoe = W[2 + ndim] - 0.5 * sum(W[2 + j] ** 2 for j in range(ndim)) / rho
+    G = a1 / (eos["gamma_l"] - 1) + (1 - a1) / (eos["gamma_g"] - 1)
+    Pi = a1 * eos["gamma_l"] * eos["pinf_l"] / (eos["gamma_l"] - 1)
+    return rhoe - Pi / (G + 1)
+
+
 def main():
     args = parse()
     if args.workload != "shock_bubble":
         {"precision_2048": workload_precision, "convergence": workload_convergence,
-         "riemann_batch": workload_batch, "bubble_3d": workload_3d}[args.workload](args)
+         "riemann_batch": workload_batch, "bubble_3d": workload_3d, "stress": workload_stress}[args.workload](args)
         return
     world, rank, local = dist_setup(args)
     if args.impl == "reference":

@@ -178,7 +178,10 @@ int wcns_advance_steps(wcns_handle *h, double *W, int nsteps, double cfl, double
 
 /* Advance W in place from t0 to t_end with CFL-limited steps (dt as above,
  * the last step clipped to land on t_end).  Returns the end time and the
- * number of steps taken in the host outputs (either may be NULL). */
+ * number of steps taken in the host outputs (either may be NULL).  The host
+ * checks the device step control every 8-256 steps: a non-finite time step
+ * (a state whose wave speed is not finite) ends the call with
+ * WCNS_E_NONFINITE, W holding the state of that moment. */
 int wcns_advance_to(wcns_handle *h, double *W, double t0, double t_end, double cfl,
                     double *t_out, long *steps_out);
 

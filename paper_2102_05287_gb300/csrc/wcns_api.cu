@@ -573,8 +573,10 @@ int wcns_advance_to(wcns_handle *h, double *W, double t0, double t_end, double c
     if (st) return st;
     CK(cudaMemcpyAsync(&c, h->ctl, sizeof(StepCtl), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    // a non-finite wave speed makes dt and t NaN: report it before the
+    // t < t_end test (false for NaN) could end the loop as if t_end was reached
+    if (!isfinite(c.t) || !isfinite(c.dt) || (c.active && c.dt <= 0.0)) return WCNS_E_NONFINITE;
     if (!c.active || !(c.t < t_end)) break;
-    if (!isfinite(c.t) || !isfinite(c.dt) || c.dt <= 0.0) return WCNS_E_NONFINITE;
     if (batch < 256) batch *= 2;
   }
   if (t_out) *t_out = c.t;

@@ -705,7 +705,12 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
       for (int j = 0; j < NDIM; ++j) m2 += wf[2 + j] * wf[2 + j];
       const float Gam = eos.r2f + eos.drf * wf[A];
       const float pb = __fdividef(eos.q1f * wf[A], Gam + 1.0f);
-      const float rct = wf[E] - 0.5f * __fdividef(m2, rho) - pb;
+      const float ke = 0.5f * __fdividef(m2, rho);
+      // rho ctilde^2 = E - ke - pbar loses digits to cancellation when the
+      // kinetic energy dominates: take it plus its FP32 error bound
+      // (8 2^-24 of the terms' magnitudes), so that c, and the wave speed
+      // that sets the next stage's lambda (Sec. 3.3), is never underestimated
+      const float rct = (wf[E] - ke - pb) + 4.76837158203125e-07f * (fabsf(wf[E]) + ke + pb);
       const float iG = __fdividef(1.0f, Gam);
       const float c = sqrtf(fmaxf((1.0f + iG) * iG * rct, 0.0f) / rho);
 #pragma unroll

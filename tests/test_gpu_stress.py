@@ -158,3 +158,39 @@ def test_jet_pp_stays_admissible(jet, precision):
     assert in_G(pr.eos, got, 2)
     assert got[0].max() > 100.0  # the jet has entered
     s.close()
+
+
+def test_unlimited_blow_up_is_reported_not_faulted():
+    """Failure detection on the host side of the ABI: the unlimited scheme
+    turns the Sedov state non-finite; wcns_advance_to stops with
+    WCNS_E_NONFINITE (it does not report reaching t_end), and the handle
+    stays usable afterwards."""
+    from paper_2102_05287_gb300.wcns import WcnsError, WCNS_E_NONFINITE
+    pr = P.sedov_multimaterial()
+    s = solver(pr, scheme="wcns-is")
+    W = torch.from_numpy(pr.W).cuda()
+    with pytest.raises(WcnsError) as ei:
+        s.advance_to(W, 0.0, pr.t_end, cfl=0.5)
+    assert ei.value.status == WCNS_E_NONFINITE
+    st = s.stats()
+    assert st["nonfinite"] > 0 or st["inadmissible"] > 0
+    ok = solver(pr)
+    W2 = torch.from_numpy(pr.W).cuda()
+    t, steps = ok.advance_to(W2, 0.0, 50 * pr.dt_fixed, cfl=0.5)
+    assert t == 50 * pr.dt_fixed and steps > 0
+    assert in_G(pr.eos, W2.cpu().numpy(), 1)
+    s.close()
+    ok.close()
+
+
+def test_invalid_arguments_are_rejected():
+    from paper_2102_05287_gb300.wcns import WcnsError
+    with pytest.raises(WcnsError):  # gamma_g > gamma_l breaks Lemma 1's convexity
+        Solver((16,), (0.0,), (1.0,), (("transmissive", "transmissive"),), gamma_g=5.0, gamma_l=4.4,
+               pinf_l=6e8)
+    s = Solver((16, 8), (0.0, 0.0), (1.0, 1.0), (("transmissive", "transmissive"),) * 2, **P.WORKLOAD_EOS)
+    with pytest.raises(WcnsError):  # the face is not a Dirichlet face
+        s.set_dirichlet_face(0, 0, np.zeros((6, 8)))
+    with pytest.raises(ValueError):  # wrong face size
+        s.set_dirichlet_face(0, 0, np.zeros((6, 9)))
+    s.close()
