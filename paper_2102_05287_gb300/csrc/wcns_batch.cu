@@ -56,9 +56,16 @@ struct BatchGeo {
   __device__ unsigned long long *smax_slot(int) const { return &b.smax[prob]; }
 };
 
-// MIXED selects the mixed-precision body (wcns_mixed_body.cuh).
+// MIXED selects the mixed-precision body (wcns_mixed_body.cuh).  Mixed
+// tiles target BATCH_MIXED_WARPS resident warps per SM (a register cap of
+// 65536 / (32 BATCH_MIXED_WARPS) per thread); the FP64 body keeps its
+// registers.
+#ifndef BATCH_MIXED_WARPS
+#define BATCH_MIXED_WARPS 24
+#endif
 template <bool MIXED, class T>
-__global__ void __launch_bounds__(T::THREADS) batch_sweep_kernel(const SweepArgs a, const BatchArgs b) {
+__global__ void __launch_bounds__(T::THREADS, MIXED ? BATCH_MIXED_WARPS * 32 / T::THREADS : 1)
+    batch_sweep_kernel(const SweepArgs a, const BatchArgs b) {
   extern __shared__ double smem_raw[];
   for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
     if constexpr (MIXED)
@@ -294,7 +301,7 @@ int autotune(wcns_batch *b, const double *W, double cfl) {
   int bv = 1, bg = b->sms;
   for (int v = 0; v < kNumVariants; ++v) {
     const int occ = b->opt.precision == WCNS_MIXED ? kVariants[v].occm() : kVariants[v].occ64();
-    for (int bps = 1; bps <= occ && bps <= 8; bps *= 2) {
+    for (int bps = 1; bps <= occ && bps <= 16; bps = (bps * 2 > occ && bps < occ) ? occ : bps * 2) {
       int grid = b->sms * bps;
       if (grid > b->ntiles[v]) grid = b->ntiles[v];
       cudaMemcpyAsync(trial, W, bytes, cudaMemcpyDeviceToDevice, b->cap);

@@ -24,12 +24,28 @@
 
 namespace wcns {
 
+// Resident blocks per SM the register allocation targets (256 threads a
+// block): 3 in 2D (85 registers; three 2D tiles fit in shared memory), 2 in
+// 3D (the 3D tiles need 78-85 KB); the 1D tiles have 128 threads.
 #ifndef MIXED_MIN_BLOCKS
 #define MIXED_MIN_BLOCKS 2
 #endif
+#ifndef MIXED_MIN_BLOCKS_2D
+#define MIXED_MIN_BLOCKS_2D 3
+#endif
 
+// Tile shapes (lines x midpoints, 256 threads): x sweeps MIXED_TL_X x
+// 256/MIXED_TL_X, y/z sweeps MIXED_TL_Y x 256/MIXED_TL_Y (x-columns x
+// midpoints).
+#ifndef MIXED_TL_X
+#define MIXED_TL_X 2
+#endif
+#ifndef MIXED_TL_Y
+#define MIXED_TL_Y 8
+#endif
 template <int NDIM, int DIR>
-using TileMixed = TileT<(DIR == 0) ? (NDIM == 1 ? 1 : 2) : 8, (DIR == 0) ? 128 : 32,
+using TileMixed = TileT<(DIR == 0) ? (NDIM == 1 ? 1 : MIXED_TL_X) : MIXED_TL_Y,
+                        (DIR == 0) ? (NDIM == 1 ? 128 : 256 / MIXED_TL_X) : 256 / MIXED_TL_Y,
                         (DIR == 0) ? (NDIM == 1 ? 128 : 256) : 256>;
 
 // value = hi + lo: hi keeps the leading 24 bits of the double (truncated),
@@ -738,7 +754,8 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
 }
 
 template <int NDIM, int DIR>
-__global__ void __launch_bounds__(TileMixed<NDIM, DIR>::THREADS, MIXED_MIN_BLOCKS) sweep_kernel_mixed(const SweepArgs a) {
+__global__ void __launch_bounds__(TileMixed<NDIM, DIR>::THREADS, NDIM == 2 ? MIXED_MIN_BLOCKS_2D : MIXED_MIN_BLOCKS)
+    sweep_kernel_mixed(const SweepArgs a) {
   extern __shared__ double smem_raw[];
   if (!a.ctl->active) return;
   using T = TileMixed<NDIM, DIR>;
