@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--workload", default="shock_bubble",
-                    choices=["shock_bubble", "precision_2048", "convergence", "riemann_batch", "bubble_3d", "stress"],
+                    choices=["shock_bubble", "precision_2048", "convergence", "riemann_batch", "bubble_3d", "stress",
+                             "full_runs"],
                     help="shock_bubble (default): the headline line; the others measure the remaining "
                          "workloads and print their own JSON line")
     return ap.parse_args()
@@ -698,6 +699,103 @@ def workload_stress(args):
     print(json.dumps({"workload": "stress_section6", "results": out}), flush=True)
 
 
+def workload_full_runs(args):
+    """The five configurations at their stated lengths, one JSON line:
+    1D water-air shock tube to t = 2.4e-4 (FP64, L1 against the exact
+    two-stiffened-gas Riemann solution, next to the oracle's), 2D
+    shock/bubble 1024x512 for 2000 steps (FP64 and mixed), the 4096-problem
+    batch for 500 steps (FP64 and mixed), 3D bubble collapse 384^3 for 500
+    steps (mixed).  Device counters, wall time and the mixed-vs-FP64
+    difference at the end."""
+    import numpy as np
+    import torch
+    from oracle import Oracle
+    from oracle import exact_riemann as ER
+    from paper_2102_05287_gb300 import problems as P
+    from paper_2102_05287_gb300.wcns import Batch, Solver
+    out = {}
+    # config 0
+    pr = P.water_air_shock_tube(200)
+    s = Solver(pr.n, pr.lo, pr.hi, pr.bcs, **pr.eos)
+    W = torch.from_numpy(pr.W).cuda()
+    t, steps = s.advance_to(W, 0.0, pr.t_end, cfl=0.5)
+    Wg = W.cpu().numpy()
+    o = Oracle(pr.n, pr.lo, pr.hi, pr.bcs, **pr.eos)
+    Wo, to, so = o.advance_to(pr.W, 0.0, pr.t_end, cfl=0.5)
+    x = (np.arange(200) + 0.5) / 200
+    ex, _ = ER.solve_five_equation(pr.eos, (999.999, 0.00005, 0.0, 1e9, 1 - 1e-6),
+                                   (0.001, 49.99995, 0.0, 1e5, 1e-6), 0.7, pr.t_end, x)
+    rex = ex[0] + ex[1]
+    out["config0_shock_tube_200"] = {
+        "t": t, "steps": steps, "oracle_steps": so, "stats": s.stats(),
+        "l1_rho_vs_exact": float(np.mean(np.abs(Wg[0] + Wg[1] - rex))),
+        "oracle_l1_rho_vs_exact": float(np.mean(np.abs(Wo[0] + Wo[1] - rex))),
+        "l1_rho_gpu_vs_oracle": float(np.abs((Wg[0] + Wg[1]) - (Wo[0] + Wo[1])).sum() / np.abs(Wo[0] + Wo[1]).sum())}
+    s.close()
+    # config 1
+    pr = P.shock_bubble_2d(1024, 512)
+    res, states = {}, {}
+    for prec in ("fp64", "mixed"):
+        s = Solver(pr.n, pr.lo, pr.hi, pr.bcs, precision=prec, **pr.eos)
+        W = torch.from_numpy(pr.W).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        t = s.advance_steps(W, 2000, cfl=0.5)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        res[prec] = {"t": t, "wall_s": el, "cell_stage_updates_per_s": 3 * 2000 * pr.ncells / el, "stats": s.stats()}
+        states[prec] = W.cpu()
+        s.close()
+    # compare at the same time: the mixed run advanced to the FP64 run's end time
+    s = Solver(pr.n, pr.lo, pr.hi, pr.bcs, precision="mixed", **pr.eos)
+    Wm = torch.from_numpy(pr.W).cuda()
+    s.advance_to(Wm, 0.0, res["fp64"]["t"], cfl=0.5)
+    s.close()
+    res["mixed_vs_fp64_same_time"] = _errors(Wm.cpu(), states["fp64"], pr.eos, 2)
+    # the problem's own sensitivity after 2000 steps: FP64 from the initial
+    # state perturbed by a seeded relative 1e-15
+    rng = np.random.default_rng(11)
+    Wp = torch.from_numpy(pr.W * (1.0 + 1e-15 * rng.uniform(-1.0, 1.0, pr.W.shape))).cuda()
+    s = Solver(pr.n, pr.lo, pr.hi, pr.bcs, precision="fp64", **pr.eos)
+    s.advance_to(Wp, 0.0, res["fp64"]["t"], cfl=0.5)
+    s.close()
+    res["fp64_vs_fp64_perturbed_1e-15_same_time"] = _errors(Wp.cpu(), states["fp64"], pr.eos, 2)
+    out["config1_shock_bubble_1024x512_2000_steps"] = res
+    # config 3
+    rb = P.riemann_batch()
+    res = {}
+    for prec in ("fp64", "mixed"):
+        b = Batch(rb.sizes, np.zeros(len(rb.sizes)), np.ones(len(rb.sizes)), "transmissive", "transmissive",
+                  precision=prec, **rb.eos)
+        W = torch.from_numpy(rb.W).cuda()
+        tt = torch.zeros(len(rb.sizes), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.advance(W, 500, cfl=0.5, t=tt)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        res[prec] = {"wall_s": el, "cell_stage_updates_per_s": 3 * 500 * int(rb.offsets[-1]) / el,
+                     "stats": b.stats(), "tuning": b.tuning(), "t_min": float(tt.min()), "t_max": float(tt.max())}
+        b.close()
+    out["config3_riemann_batch_4096_500_steps"] = res
+    # config 4
+    pr = P.bubble_collapse_3d(384)
+    s = Solver(pr.n, pr.lo, pr.hi, pr.bcs, precision="mixed", **pr.eos)
+    W = torch.from_numpy(pr.W).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    t = s.advance_steps(W, 500, cfl=0.5)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    Wc = W.cpu().numpy()
+    out["config4_bubble_collapse_384_500_steps_mixed"] = {
+        "t": t, "wall_s": el, "cell_stage_updates_per_s": 3 * 500 * pr.ncells / el, "stats": s.stats(),
+        "min_a1r1": float(Wc[0].min()), "min_a2r2": float(Wc[1].min()), "min_alpha1": float(Wc[-1].min()),
+        "max_alpha1": float(Wc[-1].max()), "min_rho_ctilde2": float(_rho_ct2(Wc, pr.eos, 3).min())}
+    s.close()
+    print(json.dumps({"workload": "full_runs", "results": out}), flush=True)
+
+
 def _rho_ct2(W, eos, ndim):
     """rho ctilde^2 = rho e - pbar of every cell (Sec. 2), for reports."""
     a1 = W[3 + ndim]
@@ -712,7 +810,8 @@ def main():
     args = parse()
     if args.workload != "shock_bubble":
         {"precision_2048": workload_precision, "convergence": workload_convergence,
-         "riemann_batch": workload_batch, "bubble_3d": workload_3d, "stress": workload_stress}[args.workload](args)
+         "riemann_batch": workload_batch, "bubble_3d": workload_3d, "stress": workload_stress,
+         "full_runs": workload_full_runs}[args.workload](args)
         return
     world, rank, local = dist_setup(args)
     if args.impl == "reference":

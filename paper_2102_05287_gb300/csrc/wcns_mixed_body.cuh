@@ -106,8 +106,9 @@ struct SmemMixed {
   // FP64: W, G per node; FP32: V hi/lo, G hi/lo per node, c, node flags
   static constexpr size_t NODE_BYTES = 8 * 2 * NF + 4 * 4 * NF + 4 + 4;
   static constexpr size_t MID_BYTES = 8 * (NF + 1);
-  static constexpr size_t BYTES = NODE_BYTES * T::NN + MID_BYTES * T::NM;
-  double *W, *G, *F, *am, *ap;
+  // + per-block scalars: dt, lambda, b dt, b dt / dx, 2 lambda (FP32)
+  static constexpr size_t BYTES = NODE_BYTES * T::NN + MID_BYTES * T::NM + 5 * 8;
+  double *W, *G, *F, *am, *ap, *scal;
   float *Vh, *Vl, *Gh, *Gl, *c;
   unsigned int *ok;
   __device__ SmemMixed(double *base) {
@@ -122,6 +123,7 @@ struct SmemMixed {
     Gl = Gh + NF * T::NN;
     c = Gl + NF * T::NN;
     ok = (unsigned int *)(c + T::NN);
+    scal = (double *)(ok + T::NN);  // c and ok together take 8 NN bytes: 8-byte aligned
   }
 };
 
@@ -305,11 +307,20 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
       if (!adm) atomicAdd(&a.stats->inadmissible, 1ull);
     }
   }
+  // block-wide scalars (dt, lambda_d of Sec. 3.3, combine coefficients),
+  // computed once instead of by every thread: FP64 work is the scarce one
+  if (tid == 0) {
+    const double dt0 = geo.dt(), lam0 = geo.lam(), bdt0 = a.rk_b * dt0;
+    sm.scal[0] = dt0;
+    sm.scal[1] = lam0;
+    sm.scal[2] = bdt0;
+    sm.scal[3] = bdt0 * geo.inv_dx();
+    reinterpret_cast<float *>(sm.scal + 4)[0] = (float)(2.0 * lam0);
+  }
   __syncthreads();
 
-  const double dt = geo.dt();
-  const double lam = geo.lam();
-  const float l2 = (float)(2.0 * lam);
+  const double lam = sm.scal[1];
+  const float l2 = reinterpret_cast<const float *>(sm.scal + 4)[0];
   const R epsR = a.eps_is32;
   const unsigned int ALL = 31u;
 
@@ -668,7 +679,7 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
   for (int j = 0; j < NDIM; ++j) smax_local[j] = 0.0f;
   int done = 0;
   const double idx_ = geo.inv_dx();
-  const double bdt = a.rk_b * dt, bdt_idx = bdt * idx_;
+  const double bdt = sm.scal[2], bdt_idx = sm.scal[3];
   for (int q = tid; q < T::TL * (T::TM - 1); q += T::THREADS) {
     const int l = DIR == 0 ? q / (T::TM - 1) : q % T::TL;
     const int m = DIR == 0 ? q % (T::TM - 1) : q / T::TL;
