@@ -113,7 +113,9 @@ typedef struct {
 /* Create a solver for one grid, boundary set and fluid pair.
  * gamma_g > 1, gamma_l > 1, pinf_l >= 0 and gamma_g <= gamma_l (Lemma 1,
  * Sec. 2: the admissible set is convex only then).  Periodic axes need both
- * faces periodic; symmetry needs n >= 3 on that axis.  Allocates the
+ * faces periodic; symmetry needs n >= 3 on that axis.  Launch-grid limits
+ * (65535 blocks in grid y and z): in 2D and 3D n[0] <= 524,280 and
+ * n[1] <= 131,070; in 3D also n[1], n[2] <= 65,535.  Allocates the
  * handle's device scratch (three states) on the current device.
  * Returns WCNS_E_INVALID_ARG on a bad argument, WCNS_E_CUDA on allocation
  * failure; *out is NULL on error. */

@@ -412,8 +412,9 @@ int wcns_create(const wcns_grid *g, const wcns_bcs *bcs, double gamma_g, double 
   // launch-grid limits of the sweeps (gridDim.y / gridDim.z <= 65535)
   {
     const long long ny = g->ndim > 1 ? g->n[1] : 1, nz = g->ndim > 2 ? g->n[2] : 1;
+    // x sweeps: 2 lines a block; y/z sweeps: 8 (mixed) or 16 (FP64) x-columns a block
     if ((ny + 1) / 2 > 65535 || nz > 65535 || (g->ndim > 2 && ny > 65535) ||
-        ((long long)g->n[0] + 31) / 32 > 65535)
+        (g->ndim > 1 && ((long long)g->n[0] + 7) / 8 > 65535))
       return WCNS_E_INVALID_ARG;
   }
   wcns_handle *h = (wcns_handle *)calloc(1, sizeof(wcns_handle));
@@ -766,7 +767,8 @@ extern "C" int wcns_rk3_step_noalloc(const wcns_grid *g, const wcns_bcs *bcs, do
   }
   {
     const long long ny = g->ndim > 1 ? g->n[1] : 1, nz = g->ndim > 2 ? g->n[2] : 1;
-    if ((ny + 1) / 2 > 65535 || nz > 65535 || (g->ndim > 2 && ny > 65535) || ((long long)g->n[0] + 31) / 32 > 65535)
+    if ((ny + 1) / 2 > 65535 || nz > 65535 || (g->ndim > 2 && ny > 65535) ||
+        (g->ndim > 1 && ((long long)g->n[0] + 7) / 8 > 65535))
       return WCNS_E_INVALID_ARG;
   }
   const int nf = g->ndim + 4;

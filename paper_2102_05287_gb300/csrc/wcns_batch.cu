@@ -128,9 +128,16 @@ __global__ void batch_begin_kernel(int nprob, const double *inv_dx, double *dt, 
 
 typedef cudaError_t (*BatchLauncher)(const SweepArgs &, const BatchArgs &, int grid, cudaStream_t);
 
-template <bool MIXED, int TM>
+// A batch tile: TH threads and TH - TRIM midpoints (TH - TRIM + 5 nodes).
+// Mixed tiles use TRIM = 5, so that the node stage is exactly one node per
+// thread (its FP64 work would otherwise leave most threads waiting at the
+// barrier for a few); the FP64 tiles keep TRIM = 0, which measured faster.
+template <int TH, int TRIM>
+using BatchTile = TileT<1, TH - TRIM, TH>;
+
+template <bool MIXED, int TH, int TRIM>
 cudaError_t launch_batch(const SweepArgs &a, const BatchArgs &b, int grid, cudaStream_t s) {
-  using T = TileT<1, TM, TM>;
+  using T = BatchTile<TH, TRIM>;
   const size_t bytes = batch_smem<MIXED, T>();
   static bool configured = false;
   if (!configured) {
@@ -143,9 +150,9 @@ cudaError_t launch_batch(const SweepArgs &a, const BatchArgs &b, int grid, cudaS
   return cudaGetLastError();
 }
 
-template <bool MIXED, int TM>
+template <bool MIXED, int TH, int TRIM>
 int max_blocks_per_sm() {
-  using T = TileT<1, TM, TM>;
+  using T = BatchTile<TH, TRIM>;
   int nb = 0;
   const size_t bytes = batch_smem<MIXED, T>();
   cudaFuncSetAttribute(batch_sweep_kernel<MIXED, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -155,18 +162,20 @@ int max_blocks_per_sm() {
   return nb > 0 ? nb : 1;
 }
 
+// Tile variants the autotuner chooses from; a variant serves the precision
+// whose launcher is set.
 struct Variant {
-  int tm;
+  int tm;  // midpoints per tile (tiles cover tm - 1 cells)
   BatchLauncher fp64, mixed;
   int (*occ64)(), (*occm)();
 };
 const Variant kVariants[] = {
-    {64, launch_batch<false, 64>, launch_batch<true, 64>, max_blocks_per_sm<false, 64>,
-     max_blocks_per_sm<true, 64>},
-    {128, launch_batch<false, 128>, launch_batch<true, 128>, max_blocks_per_sm<false, 128>,
-     max_blocks_per_sm<true, 128>},
-    {256, launch_batch<false, 256>, launch_batch<true, 256>, max_blocks_per_sm<false, 256>,
-     max_blocks_per_sm<true, 256>},
+    {BatchTile<64, 0>::TM, launch_batch<false, 64, 0>, nullptr, max_blocks_per_sm<false, 64, 0>, nullptr},
+    {BatchTile<128, 0>::TM, launch_batch<false, 128, 0>, nullptr, max_blocks_per_sm<false, 128, 0>, nullptr},
+    {BatchTile<256, 0>::TM, launch_batch<false, 256, 0>, nullptr, max_blocks_per_sm<false, 256, 0>, nullptr},
+    {BatchTile<64, 5>::TM, nullptr, launch_batch<true, 64, 5>, nullptr, max_blocks_per_sm<true, 64, 5>},
+    {BatchTile<128, 5>::TM, nullptr, launch_batch<true, 128, 5>, nullptr, max_blocks_per_sm<true, 128, 5>},
+    {BatchTile<256, 5>::TM, nullptr, launch_batch<true, 256, 5>, nullptr, max_blocks_per_sm<true, 256, 5>},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
@@ -264,7 +273,9 @@ int enqueue_batch_step(wcns_batch *b, double *W, double cfl, double *t_acc, int 
     // only the last stage's wave-speed maxima feed the next step's dt
     BatchArgs ba = batch_args(b, v, st == 2 ? b->smax : b->smax_scratch);
     const Variant &var = kVariants[v];
-    cudaError_t e = (b->opt.precision == WCNS_MIXED ? var.mixed : var.fp64)(a, ba, grid, s);
+    const BatchLauncher launch = b->opt.precision == WCNS_MIXED ? var.mixed : var.fp64;
+    if (!launch) return WCNS_E_UNSUPPORTED;
+    cudaError_t e = launch(a, ba, grid, s);
     b->launches++;
     if (e != cudaSuccess) return WCNS_E_CUDA;
   }
@@ -298,9 +309,11 @@ int autotune(wcns_batch *b, const double *W, double cfl) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float best = 1e30f;
-  int bv = 1, bg = b->sms;
+  int bv = b->opt.precision == WCNS_MIXED ? 4 : 1, bg = b->sms;  // fallbacks: 127-cell tiles
   for (int v = 0; v < kNumVariants; ++v) {
-    const int occ = b->opt.precision == WCNS_MIXED ? kVariants[v].occm() : kVariants[v].occ64();
+    const bool mixed = b->opt.precision == WCNS_MIXED;
+    if (!(mixed ? kVariants[v].mixed : kVariants[v].fp64)) continue;
+    const int occ = mixed ? kVariants[v].occm() : kVariants[v].occ64();
     for (int bps = 1; bps <= occ && bps <= 16; bps = (bps * 2 > occ && bps < occ) ? occ : bps * 2) {
       int grid = b->sms * bps;
       if (grid > b->ntiles[v]) grid = b->ntiles[v];

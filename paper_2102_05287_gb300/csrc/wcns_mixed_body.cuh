@@ -34,18 +34,28 @@ namespace wcns {
 #define MIXED_MIN_BLOCKS_2D 3
 #endif
 
-// Tile shapes (lines x midpoints, 256 threads): x sweeps MIXED_TL_X x
-// 256/MIXED_TL_X, y/z sweeps MIXED_TL_Y x 256/MIXED_TL_Y (x-columns x
-// midpoints).
+// Tile shapes (lines x midpoints): x sweeps 2 x 123 with 256 threads and
+// 1D 1 x 123 with 128 threads, so that the node stage (midpoints + 5 nodes
+// a line) is exactly one node per thread; y/z sweeps MIXED_TL_Y x
+// 256/MIXED_TL_Y (x-columns x midpoints).
 #ifndef MIXED_TL_X
 #define MIXED_TL_X 2
+#endif
+#ifndef MIXED_TM_X
+#define MIXED_TM_X (256 / MIXED_TL_X - 5)
+#endif
+#ifndef MIXED_TM_1D
+#define MIXED_TM_1D 123
 #endif
 #ifndef MIXED_TL_Y
 #define MIXED_TL_Y 8
 #endif
+#ifndef MIXED_TM_Y
+#define MIXED_TM_Y (256 / MIXED_TL_Y)
+#endif
 template <int NDIM, int DIR>
 using TileMixed = TileT<(DIR == 0) ? (NDIM == 1 ? 1 : MIXED_TL_X) : MIXED_TL_Y,
-                        (DIR == 0) ? (NDIM == 1 ? 128 : 256 / MIXED_TL_X) : 256 / MIXED_TL_Y,
+                        (DIR == 0) ? (NDIM == 1 ? MIXED_TM_1D : MIXED_TM_X) : MIXED_TM_Y,
                         (DIR == 0) ? (NDIM == 1 ? 128 : 256) : 256>;
 
 // value = hi + lo: hi keeps the leading 24 bits of the double (truncated),

@@ -50,8 +50,13 @@ struct TileT {
   static constexpr int NN = TL * NS;     // nodes per block
   static constexpr int NM = TL * TM;     // midpoints per block
 };
+// x tiles: 2 x 123 midpoints (1 x 123 in 1D), i.e. 256 (128) nodes for 256
+// (128) threads; y/z tiles: 16 x-columns x 32 midpoints.
+#ifndef FP64_TM_X
+#define FP64_TM_X 123
+#endif
 template <int NDIM, int DIR>
-using Tile = TileT<(DIR == 0) ? (NDIM == 1 ? 1 : 2) : 16, (DIR == 0) ? 128 : 32,
+using Tile = TileT<(DIR == 0) ? (NDIM == 1 ? 1 : 2) : 16, (DIR == 0) ? FP64_TM_X : 32,
                    (DIR == 0) ? (NDIM == 1 ? 128 : 256) : 256>;
 
 // Integer tests on FP64 values (no FP64-pipe compare): finite, and
