@@ -50,13 +50,22 @@ struct TileT {
   static constexpr int NN = TL * NS;     // nodes per block
   static constexpr int NM = TL * TM;     // midpoints per block
 };
-// x tiles: 2 x 123 midpoints (1 x 123 in 1D), i.e. 256 (128) nodes for 256
-// (128) threads; y/z tiles: 16 x-columns x 32 midpoints.
+// Tile shapes (lines x midpoints, measured on GB300): x tiles 2 x 123
+// midpoints (1 x 123 in 1D), i.e. 256 (128) nodes for 256 (128) threads;
+// y/z tiles 8 x-columns x 59 midpoints in 2D (512 nodes, two per thread)
+// and 16 x 32 in 3D.
 #ifndef FP64_TM_X
 #define FP64_TM_X 123
 #endif
+#ifndef FP64_3D_TL_X
+#define FP64_3D_TL_X 2
+#endif
+#ifndef FP64_3D_TM_X
+#define FP64_3D_TM_X FP64_TM_X
+#endif
 template <int NDIM, int DIR>
-using Tile = TileT<(DIR == 0) ? (NDIM == 1 ? 1 : 2) : 16, (DIR == 0) ? FP64_TM_X : 32,
+using Tile = TileT<(DIR == 0) ? (NDIM == 1 ? 1 : (NDIM == 3 ? FP64_3D_TL_X : 2)) : (NDIM == 2 ? 8 : 16),
+                   (DIR == 0) ? (NDIM == 3 ? FP64_3D_TM_X : FP64_TM_X) : (NDIM == 2 ? 59 : 32),
                    (DIR == 0) ? (NDIM == 1 ? 128 : 256) : 256>;
 
 // Integer tests on FP64 values (no FP64-pipe compare): finite, and
