@@ -139,13 +139,12 @@ template <bool MIXED, int TH, int TRIM>
 cudaError_t launch_batch(const SweepArgs &a, const BatchArgs &b, int grid, cudaStream_t s) {
   using T = BatchTile<TH, TRIM>;
   const size_t bytes = batch_smem<MIXED, T>();
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(batch_sweep_kernel<MIXED, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bytes);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static std::atomic<unsigned long long> configured{0};
+  cudaError_t e = configure_once(configured, [&] {
+    return cudaFuncSetAttribute(batch_sweep_kernel<MIXED, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)bytes);
+  });
+  if (e != cudaSuccess) return e;
   batch_sweep_kernel<MIXED, T><<<grid, T::THREADS, bytes, s>>>(a, b);
   return cudaGetLastError();
 }

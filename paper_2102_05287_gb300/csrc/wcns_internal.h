@@ -3,7 +3,25 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace wcns {
+
+// One-time configuration of a kernel's function attributes, which CUDA
+// keeps per device: `once` holds one bit per device ordinal (ordinals of 64
+// and above configure on every call).
+template <class F>
+inline cudaError_t configure_once(std::atomic<unsigned long long> &once, F &&configure) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+  if (bit && (once.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = configure();
+  if (e == cudaSuccess && bit) once.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
+
 
 // Per-phase EOS constants (Sec. 2): with Gamma(a1) = 1/(gbar-1) and
 // Pi(a1) = gbar pbar/(gbar-1),

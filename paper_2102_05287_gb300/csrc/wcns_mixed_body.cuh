@@ -787,15 +787,15 @@ template <int NDIM, int DIR>
 cudaError_t launch_sweep_mixed_t(const SweepArgs &a, cudaStream_t st) {
   using T = TileMixed<NDIM, DIR>;
   const size_t bytes = SmemMixed<NDIM, T>::BYTES;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(sweep_kernel_mixed<NDIM, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  static std::atomic<unsigned long long> configured{0};
+  cudaError_t e = configure_once(configured, [&] {
+    cudaError_t r = cudaFuncSetAttribute(sweep_kernel_mixed<NDIM, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)bytes);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(sweep_kernel_mixed<NDIM, DIR>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(sweep_kernel_mixed<NDIM, DIR>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    return r;
+  });
+  if (e != cudaSuccess) return e;
   const int nd = a.n[DIR];
   dim3 grid((nd + T::TM - 2) / (T::TM - 1), 1, 1);
   if (DIR == 0) {

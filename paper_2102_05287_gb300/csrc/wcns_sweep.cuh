@@ -963,13 +963,11 @@ template <int NDIM, int DIR, class R>
 cudaError_t launch_sweep_t(const SweepArgs &a, cudaStream_t st) {
   using T = Tile<NDIM, DIR>;
   const size_t bytes = Smem<NDIM, DIR, T>::BYTES;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<NDIM, DIR, R>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static std::atomic<unsigned long long> configured{0};
+  cudaError_t e = configure_once(configured, [&] {
+    return cudaFuncSetAttribute(sweep_kernel<NDIM, DIR, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  });
+  if (e != cudaSuccess) return e;
   const int nd = a.n[DIR];
   dim3 grid((nd + T::TM - 2) / (T::TM - 1), 1, 1);
   if (DIR == 0) {
