@@ -92,7 +92,8 @@ typedef struct {
                            does not print it): default 1e-40 (FP64), the FP32
                            stages of the mixed path use max(eps_is, 1e-30) */
   double eps_ar, eps_a, eps_rc;  /* limiter tolerances, Sec. 5.1: 1e-10, 1e-10, 1e-8 */
-  double hs_ar, hs_a, hs_rc;     /* hard-switch tolerances, Sec. 5.1: 1e-11, 1e-11, 1e-9 */
+  double hs_ar, hs_a, hs_rc;     /* hard-switch tolerances, Sec. 5.1: 1e-11, 1e-11, 1e-9;
+                                    all six finite and >= 0, else WCNS_E_INVALID_ARG */
   void *stream;         /* cudaStream_t for all work of this handle (NULL = default) */
 } wcns_options;
 

@@ -463,7 +463,7 @@ int wcns_set_options(wcns_handle *h, const wcns_options *o) {
   if (!h || !o) return WCNS_E_INVALID_ARG;
   if (o->precision != WCNS_FP64 && o->precision != WCNS_MIXED) return WCNS_E_INVALID_ARG;
   if (o->scheme < 0 || o->scheme > 2) return WCNS_E_INVALID_ARG;
-  if (!(o->eps_is > 0.0) || !(o->eps_ar >= 0.0) || !(o->eps_a >= 0.0) || !(o->eps_rc >= 0.0))
+  if (!valid_tolerances(*o))
     return WCNS_E_INVALID_ARG;
   h->opt = *o;
   h->stream = (cudaStream_t)o->stream;
@@ -778,7 +778,7 @@ extern "C" int wcns_rk3_step_noalloc(const wcns_grid *g, const wcns_bcs *bcs, do
   if (opt) o = *opt;
   if (o.precision != WCNS_FP64 && o.precision != WCNS_MIXED) return WCNS_E_INVALID_ARG;
   if (o.scheme < 0 || o.scheme > 2) return WCNS_E_INVALID_ARG;
-  if (!(o.eps_is > 0.0)) return WCNS_E_INVALID_ARG;
+  if (!valid_tolerances(o)) return WCNS_E_INVALID_ARG;
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return WCNS_E_CUDA;

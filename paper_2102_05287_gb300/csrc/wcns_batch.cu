@@ -427,7 +427,7 @@ int wcns_batch_create(int nprob, const int *ncells, const double *lo, const doub
 int wcns_batch_set_options(wcns_batch *b, const wcns_options *o) {
   if (!b || !o) return WCNS_E_INVALID_ARG;
   if (o->precision != WCNS_FP64 && o->precision != WCNS_MIXED) return WCNS_E_INVALID_ARG;
-  if (o->scheme < 0 || o->scheme > 2 || !(o->eps_is > 0.0)) return WCNS_E_INVALID_ARG;
+  if (o->scheme < 0 || o->scheme > 2 || !valid_tolerances(*o)) return WCNS_E_INVALID_ARG;
   if (b->opt.precision != o->precision || b->opt.scheme != o->scheme) b->tuned = 0;
   b->opt = *o;
   b->stream = (cudaStream_t)o->stream;

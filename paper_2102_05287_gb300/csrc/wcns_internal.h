@@ -54,6 +54,16 @@ struct LimTol {
   float cert_ar, cert_a, cert_rc;
 };
 
+// Limiter and hard-switch tolerances must be finite and >= 0 (the kernels
+// compare against them as bit patterns), the IS epsilon finite and > 0.
+template <class Options>
+inline bool valid_tolerances(const Options &o) {
+  const double v[6] = {o.eps_ar, o.eps_a, o.eps_rc, o.hs_ar, o.hs_a, o.hs_rc};
+  for (double x : v)
+    if (!(x >= 0.0) || !(x < 1e300)) return false;
+  return o.eps_is > 0.0 && o.eps_is < 1e300;
+}
+
 inline void set_cert(LimTol &t) {
   t.cert_ar = (float)(t.eps_ar * (1.0 + 1e-6));
   t.cert_a = (float)(t.eps_a * (1.0 + 1e-6));

@@ -78,6 +78,22 @@ __device__ __forceinline__ bool nonneg64(double v) {
   const long long b = __double_as_longlong(v);
   return (b >= 0 && b < 0x7FF0000000000000ll) || b == (long long)0x8000000000000000ull;
 }
+// x < t for a finite threshold t >= 0, as an integer compare of the bit
+// patterns (non-negative doubles order like their bits, negatives are
+// below): equal to the FP64 compare for every x that is not a NaN.
+__device__ __forceinline__ bool below64(double x, double t) {
+  const long long bx = __double_as_longlong(x), bt = __double_as_longlong(t);
+  return bx < bt && (bx != (long long)0x8000000000000000ull || bt != 0);
+}
+// x < 0 and x > 0 for every x that is not a NaN (-0 is neither).
+__device__ __forceinline__ bool negative64(double x) {
+  const long long b = __double_as_longlong(x);
+  return b < 0 && b != (long long)0x8000000000000000ull;
+}
+__device__ __forceinline__ bool positive64(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0 && b <= 0x7FF0000000000000ll;
+}
 
 template <class R>
 struct Prec;
@@ -162,7 +178,10 @@ __device__ __forceinline__ double wenois<double>(double um2, double um1, double 
   const double w2 = (5.0 / 16.0) * (b2 + tau) * (p01b * b3);
   const double w3 = (1.0 / 16.0) * (b3 + tau) * (p01b * b2);
   const double sum = (w0 + w1) + (w2 + w3);
-  if (sum > 1e-280 && sum < 1e280) return (w0 * s0 + w1 * s1 + w2 * s2 + w3 * s3) / sum;
+  // 1e-280 < sum < 1e280, as integer compares (sum is a sum of products of non-negative terms)
+  const long long sb = __double_as_longlong(sum);
+  if (sb > __double_as_longlong(1e-280) && sb < __double_as_longlong(1e280))
+    return (w0 * s0 + w1 * s1 + w2 * s2 + w3 * s3) / sum;
   const double r01 = tau / b01;
   const double v0 = (15.0 / 32.0) * (1.0 + (tau / b0) * r01);
   const double v1 = (5.0 / 32.0) * (1.0 + (tau / b1) * r01);
@@ -195,8 +214,14 @@ __device__ __forceinline__ void hllc(const R *WL, const R *vL, R pL, R rL, R cL,
   sstar = ss;
   // One side's flux F_K + s_(-/+) (W*_K - W_K); at s* = 0 the mean of both.
   R GL[NF], GR[NF];
-  const bool needL = !(ss < R(0));
-  const bool needR = !(ss > R(0));
+  bool needL, needR;
+  if constexpr (sizeof(R) == 8) {
+    needL = !negative64(ss);
+    needR = !positive64(ss);
+  } else {
+    needL = !(ss < R(0));
+    needR = !(ss > R(0));
+  }
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
     if ((side == 0 && !needL) || (side == 1 && !needR)) continue;
@@ -351,28 +376,41 @@ __device__ __forceinline__ bool rct2_below(const EosConst &e, const double *W, d
   constexpr int E = 2 + NDIM, A = 3 + NDIM;
   const double rho = W[0] + W[1];
   const double G1 = mixGamma(e, W[A]) + 1.0;
-  if (!(rho > 0.0) || !(G1 > 0.0)) return rho_ct2<NDIM>(e, W) < eps;
+  if (!positive64(rho) || !positive64(G1)) return rho_ct2<NDIM>(e, W) < eps;
   double m2 = 0.0;
 #pragma unroll
   for (int j = 0; j < NDIM; ++j) m2 = fma(W[2 + j], W[2 + j], m2);
-  return ((W[E] - eps) * rho - 0.5 * m2) * G1 - mixPi(e, W[A]) * rho < 0.0;
+  return negative64(((W[E] - eps) * rho - 0.5 * m2) * G1 - mixPi(e, W[A]) * rho);
 }
 
-// theta solving (1-theta) fA + theta fB = eps with the paper's three cases.
-__device__ __forceinline__ double lim_theta(double fA, double fB, double eps) {
-  if (fA < eps) return 0.0;
-  if (fB < eps) return (fA - eps) / (fA - fB);
-  return 1.0;
+// theta solving (1-theta) fA + theta fB = eps with the paper's three cases:
+// false for theta = 1 (nothing to blend), else true with th set.  The
+// threshold tests are integer compares (eps >= 0).
+__device__ __forceinline__ bool lim_theta(double fA, double fB, double eps, double &th) {
+  if (below64(fA, eps)) {
+    th = 0.0;
+    return true;
+  }
+  if (below64(fB, eps)) {
+    th = (fA - eps) / (fA - fB);
+    return true;
+  }
+  return false;
 }
 
 // The same three cases for rho ctilde^2, with the quotient evaluated only
 // when a blend is needed.
 template <int NDIM>
-__device__ __forceinline__ double lim_theta_rct(const EosConst &e, const double *A, const double *B, double eps) {
-  if (rct2_below<NDIM>(e, A, eps)) return 0.0;
-  if (!rct2_below<NDIM>(e, B, eps)) return 1.0;
+__device__ __forceinline__ bool lim_theta_rct(const EosConst &e, const double *A, const double *B, double eps,
+                                              double &th) {
+  if (rct2_below<NDIM>(e, A, eps)) {
+    th = 0.0;
+    return true;
+  }
+  if (!rct2_below<NDIM>(e, B, eps)) return false;
   const double fA = rho_ct2<NDIM>(e, A);
-  return (fA - eps) / (fA - rho_ct2<NDIM>(e, B));
+  th = (fA - eps) / (fA - rho_ct2<NDIM>(e, B));
+  return true;
 }
 
 template <int NDIM>
@@ -391,8 +429,8 @@ __device__ __forceinline__ double lim_quantity(const double *W, int which) {
 template <int NDIM>
 __device__ __forceinline__ bool hard_fail(const EosConst &e, const LimTol &t, const double *X) {
   constexpr int A = 3 + NDIM;
-  return X[0] < t.hs_ar || X[1] < t.hs_ar || X[A] < t.hs_a || 1.0 - X[A] < t.hs_a ||
-         rct2_below<NDIM>(e, X, t.hs_rc);
+  return below64(X[0], t.hs_ar) || below64(X[1], t.hs_ar) || below64(X[A], t.hs_a) ||
+         below64(1.0 - X[A], t.hs_a) || rct2_below<NDIM>(e, X, t.hs_rc);
 }
 
 // Sec. 5.1, Algorithms 1-3 + hard switch: limit Wt toward the node state Wn.
@@ -403,14 +441,15 @@ __device__ int interp_limit(const EosConst &e, const LimTol &t, const double *Wn
   int flags = 0;
 #pragma unroll 1
   for (int which = 0; which < 5; ++which) {
-    double th;
+    double th = 1.0;
+    bool lim;
     if (which < 4) {
       const double eps = which < 2 ? t.eps_ar : t.eps_a;
-      th = lim_theta(lim_quantity<NDIM>(Wn, which), lim_quantity<NDIM>(Wt, which), eps);
+      lim = lim_theta(lim_quantity<NDIM>(Wn, which), lim_quantity<NDIM>(Wt, which), eps, th);
     } else {
-      th = lim_theta_rct<NDIM>(e, Wn, Wt, t.eps_rc);
+      lim = lim_theta_rct<NDIM>(e, Wn, Wt, t.eps_rc, th);
     }
-    if (th < 1.0) {
+    if (lim && th < 1.0) {
       flags |= 1;
 #pragma unroll
       for (int q = 0; q < NF; ++q) Wt[q] = (1.0 - th) * Wn[q] + th * Wt[q];
@@ -444,17 +483,18 @@ __device__ int flux_limit(const EosConst &e, const LimTol &t, const double *Wi, 
   int flags = 0;
 #pragma unroll 1
   for (int which = 0; which < 5; ++which) {
-    double thp, thm;
+    double thp = 1.0, thm = 1.0;
+    bool lp, lm;
     if (which < 4) {
       const double eps = which < 2 ? t.eps_ar : t.eps_a;
-      thp = lim_theta(lim_quantity<NDIM>(Ap, which), lim_quantity<NDIM>(Bp, which), eps);
-      thm = lim_theta(lim_quantity<NDIM>(Am, which), lim_quantity<NDIM>(Bm, which), eps);
+      lp = lim_theta(lim_quantity<NDIM>(Ap, which), lim_quantity<NDIM>(Bp, which), eps, thp);
+      lm = lim_theta(lim_quantity<NDIM>(Am, which), lim_quantity<NDIM>(Bm, which), eps, thm);
     } else {
-      thp = lim_theta_rct<NDIM>(e, Ap, Bp, t.eps_rc);
-      thm = lim_theta_rct<NDIM>(e, Am, Bm, t.eps_rc);
+      lp = lim_theta_rct<NDIM>(e, Ap, Bp, t.eps_rc, thp);
+      lm = lim_theta_rct<NDIM>(e, Am, Bm, t.eps_rc, thm);
     }
-    const double th = fmin(thp, thm);
-    if (th < 1.0) {
+    const double th = (lp || lm) ? fmin(thp, thm) : 1.0;
+    if ((lp || lm) && th < 1.0) {
       flags |= 1;
 #pragma unroll
       for (int q = 0; q < NF; ++q) {

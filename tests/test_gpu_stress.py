@@ -194,3 +194,6 @@ def test_invalid_arguments_are_rejected():
     with pytest.raises(ValueError):  # wrong face size
         s.set_dirichlet_face(0, 0, np.zeros((6, 9)))
     s.close()
+    with pytest.raises(WcnsError):  # tolerances must be finite and >= 0
+        Solver((16,), (0.0,), (1.0,), (("transmissive", "transmissive"),), hs_tols=(-1e-11, 1e-11, 1e-9),
+               **P.WORKLOAD_EOS)
