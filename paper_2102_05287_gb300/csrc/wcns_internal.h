@@ -52,6 +52,9 @@ struct LimTol {
   // FP32 certification thresholds of the mixed path: eps (1 + 1e-6) rounded
   // to FP32, so "x >= cert" implies "x >= eps"
   float cert_ar, cert_a, cert_rc;
+  // every hard-switch tolerance <= its limiter tolerance: then a state that
+  // passed all threshold tests unblended cannot fail a hard-switch test
+  int hs_implied;
 };
 
 // Limiter and hard-switch tolerances must be finite and >= 0 (the kernels
@@ -68,6 +71,7 @@ inline void set_cert(LimTol &t) {
   t.cert_ar = (float)(t.eps_ar * (1.0 + 1e-6));
   t.cert_a = (float)(t.eps_a * (1.0 + 1e-6));
   t.cert_rc = (float)(t.eps_rc * (1.0 + 1e-6));
+  t.hs_implied = t.hs_ar <= t.eps_ar && t.hs_a <= t.eps_a && t.hs_rc <= t.eps_rc;
 }
 
 // Device counters (accumulated with integer atomics: order-independent).

@@ -439,6 +439,7 @@ template <int NDIM>
 __device__ int interp_limit(const EosConst &e, const LimTol &t, const double *Wn, double *Wt) {
   constexpr int NF = NDIM + 4;
   int flags = 0;
+  bool any = false;  // some threshold test fired
 #pragma unroll 1
   for (int which = 0; which < 5; ++which) {
     double th = 1.0;
@@ -449,13 +450,16 @@ __device__ int interp_limit(const EosConst &e, const LimTol &t, const double *Wn
     } else {
       lim = lim_theta_rct<NDIM>(e, Wn, Wt, t.eps_rc, th);
     }
+    any = any || lim;
     if (lim && th < 1.0) {
       flags |= 1;
 #pragma unroll
       for (int q = 0; q < NF; ++q) Wt[q] = (1.0 - th) * Wn[q] + th * Wt[q];
     }
   }
-  if (hard_fail<NDIM>(e, t, Wt)) {
+  // Wt passed every threshold test unblended: each quantity is >= its eps
+  // (rounding is monotone), hence >= its hard-switch tolerance
+  if ((any || !t.hs_implied) && hard_fail<NDIM>(e, t, Wt)) {
     flags |= 2;
 #pragma unroll
     for (int q = 0; q < NF; ++q) Wt[q] = Wn[q];
@@ -481,6 +485,7 @@ __device__ int flux_limit(const EosConst &e, const LimTol &t, const double *Wi, 
     Bm[q] = Wi1[q] + l2 * (Gp[q] - Fi1[q]);
   }
   int flags = 0;
+  bool any = false;  // some threshold test fired
 #pragma unroll 1
   for (int which = 0; which < 5; ++which) {
     double thp = 1.0, thm = 1.0;
@@ -493,6 +498,7 @@ __device__ int flux_limit(const EosConst &e, const LimTol &t, const double *Wi, 
       lp = lim_theta_rct<NDIM>(e, Ap, Bp, t.eps_rc, thp);
       lm = lim_theta_rct<NDIM>(e, Am, Bm, t.eps_rc, thm);
     }
+    any = any || lp || lm;
     const double th = (lp || lm) ? fmin(thp, thm) : 1.0;
     if ((lp || lm) && th < 1.0) {
       flags |= 1;
@@ -505,7 +511,8 @@ __device__ int flux_limit(const EosConst &e, const LimTol &t, const double *Wi, 
       }
     }
   }
-  if (hard_fail<NDIM>(e, t, Bp) || hard_fail<NDIM>(e, t, Bm)) {
+  // as in interp_limit: unblended half states that passed every test
+  if ((any || !t.hs_implied) && (hard_fail<NDIM>(e, t, Bp) || hard_fail<NDIM>(e, t, Bm))) {
     flags |= 2;
 #pragma unroll
     for (int q = 0; q < NF; ++q) {
