@@ -449,8 +449,8 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
       float UL[NF], UR[NF];
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
-        UL[f] = wenois<R>(U[0][f], U[1][f], 0.0f, U[3][f], U[4][f], epsR);
-        UR[f] = wenois<R>(U[5][f], U[4][f], U[3][f], 0.0f, U[1][f], epsR);
+        UL[f] = wenois_c0<R>(U[0][f], U[1][f], U[3][f], U[4][f], epsR);
+        UR[f] = wenois_p0<R>(U[5][f], U[4][f], U[3][f], U[1][f], epsR);
       }
       // Step 4: back-projection to primitive deviations.
       float dV[2][NF];

@@ -114,26 +114,15 @@ struct Prec<float> {
 // ---------------------------------------------------------------------------
 // Sec. 4.3: incremental-stencil WENO interpolation, left-biased to i+1/2 from
 // u_{i-2} .. u_{i+2}.  The right-biased value is the same formula on the
-// mirrored stencil.
+// mirrored stencil.  The weights are computed from the four sub-stencil
+// values s0..s3, the smoothness indicators b0, b1, b01, b2, b3 and tau5 by
+// wenois_tail; wenois gives them for a general stencil, wenois_c0 /
+// wenois_p0 for the two stencils of the deviation form (u_i = 0 in the
+// left-biased one, u_{i+1} = 0 in the mirrored one), with the zero terms
+// left out.
 // ---------------------------------------------------------------------------
 template <class R>
-__device__ __forceinline__ R wenois(R um2, R um1, R u0, R up1, R up2, R eps) {
-  const R s0 = R(0.5) * (u0 + up1);
-  const R s1 = R(0.5) * (R(3) * u0 - um1);
-  const R s2 = R(0.125) * (R(3) * u0 + R(6) * up1 - up2);
-  const R s3 = R(0.125) * (R(3) * um2 - R(10) * um1 + R(15) * u0);
-  const R e0 = u0 - up1, e1 = um1 - u0;
-  const R b0 = e0 * e0;
-  const R b1 = e1 * e1;
-  const R a01 = um1 - R(2) * u0 + up1, c01 = um1 - up1;
-  const R b01 = R(13.0 / 12.0) * a01 * a01 + R(0.25) * c01 * c01;
-  const R a2 = u0 - R(2) * up1 + up2, c2 = R(3) * u0 - R(4) * up1 + up2;
-  const R b2 = R(13.0 / 12.0) * a2 * a2 + R(0.25) * c2 * c2;
-  const R a3 = um2 - R(2) * um1 + u0, c3 = um2 - R(4) * um1 + R(3) * u0;
-  const R b3 = R(13.0 / 12.0) * a3 * a3 + R(0.25) * c3 * c3;
-  const R t5a = up2 - R(4) * up1 + R(6) * u0 - R(4) * um1 + um2;
-  const R t5b = up2 - R(2) * up1 + R(2) * um1 - um2;
-  const R tau = R(13.0 / 12.0) * t5a * t5a + R(0.25) * t5b * t5b;
+__device__ __forceinline__ R wenois_tail(R s0, R s1, R s2, R s3, R b0, R b1, R b01, R b2, R b3, R tau, R eps) {
   const R r01 = Prec<R>::clampratio(Prec<R>::div(tau, b01 + eps));
   const R r0 = Prec<R>::clampratio(Prec<R>::div(tau, b0 + eps));
   const R r1 = Prec<R>::clampratio(Prec<R>::div(tau, b1 + eps));
@@ -146,31 +135,21 @@ __device__ __forceinline__ R wenois(R um2, R um1, R u0, R up1, R up2, R eps) {
   return Prec<R>::div(w0 * s0 + w1 * s1 + w2 * s2 + w3 * s3, (w0 + w1) + (w2 + w3));
 }
 
-// FP64 specialisation with one division instead of six: multiplying every
-// eta_k by D = b0 b1 b01 b2 b3 (b = beta + eps) leaves the weights
+// FP64 with one division instead of six: multiplying every eta_k by
+// D = b0 b1 b01 b2 b3 (b = beta + eps) leaves the weights
 // omega_k = eta_k / sum(eta) unchanged and clears the five ratio divisions:
 //   eta0 D = d0 (b0 b01 + tau^2) b1 b2 b3,  eta1 D = d1 (b1 b01 + tau^2) b0 b2 b3,
 //   eta2 D = d2 (b2 + tau) b0 b1 b01 b3,    eta3 D = d3 (b3 + tau) b0 b1 b01 b2.
 // If the scaled sum leaves the comfortable FP64 range the direct form runs.
 template <>
-__device__ __forceinline__ double wenois<double>(double um2, double um1, double u0, double up1, double up2,
-                                                 double eps) {
-  const double s0 = 0.5 * (u0 + up1);
-  const double s1 = 0.5 * (3.0 * u0 - um1);
-  const double s2 = 0.125 * (3.0 * u0 + 6.0 * up1 - up2);
-  const double s3 = 0.125 * (3.0 * um2 - 10.0 * um1 + 15.0 * u0);
-  const double e0 = u0 - up1, e1 = um1 - u0;
-  const double a01 = um1 - 2.0 * u0 + up1, c01 = um1 - up1;
-  const double a2 = u0 - 2.0 * up1 + up2, c2 = 3.0 * u0 - 4.0 * up1 + up2;
-  const double a3 = um2 - 2.0 * um1 + u0, c3 = um2 - 4.0 * um1 + 3.0 * u0;
-  const double t5a = up2 - 4.0 * up1 + 6.0 * u0 - 4.0 * um1 + um2;
-  const double t5b = up2 - 2.0 * up1 + 2.0 * um1 - um2;
-  const double tau = (13.0 / 12.0) * t5a * t5a + 0.25 * t5b * t5b;
-  const double b0 = e0 * e0 + eps;
-  const double b1 = e1 * e1 + eps;
-  const double b01 = (13.0 / 12.0) * a01 * a01 + 0.25 * c01 * c01 + eps;
-  const double b2 = (13.0 / 12.0) * a2 * a2 + 0.25 * c2 * c2 + eps;
-  const double b3 = (13.0 / 12.0) * a3 * a3 + 0.25 * c3 * c3 + eps;
+__device__ __forceinline__ double wenois_tail<double>(double s0, double s1, double s2, double s3, double b0,
+                                                      double b1, double b01, double b2, double b3, double tau,
+                                                      double eps) {
+  b0 += eps;
+  b1 += eps;
+  b01 += eps;
+  b2 += eps;
+  b3 += eps;
   const double t2 = tau * tau;
   const double p23 = b2 * b3, p01b = (b0 * b1) * b01;
   const double w0 = (15.0 / 32.0) * (b0 * b01 + t2) * (b1 * p23);
@@ -188,6 +167,56 @@ __device__ __forceinline__ double wenois<double>(double um2, double um1, double 
   const double v2 = (5.0 / 16.0) * (1.0 + tau / b2);
   const double v3 = (1.0 / 16.0) * (1.0 + tau / b3);
   return (v0 * s0 + v1 * s1 + v2 * s2 + v3 * s3) / ((v0 + v1) + (v2 + v3));
+}
+
+// beta = (13/12) a^2 + (1/4) c^2 for the three-point indicators
+template <class R>
+__device__ __forceinline__ R beta3(R a, R c) {
+  return R(13.0 / 12.0) * a * a + R(0.25) * c * c;
+}
+
+template <class R>
+__device__ __forceinline__ R wenois(R um2, R um1, R u0, R up1, R up2, R eps) {
+  const R s0 = R(0.5) * (u0 + up1);
+  const R s1 = R(0.5) * (R(3) * u0 - um1);
+  const R s2 = R(0.125) * (R(3) * u0 + R(6) * up1 - up2);
+  const R s3 = R(0.125) * (R(3) * um2 - R(10) * um1 + R(15) * u0);
+  const R e0 = u0 - up1, e1 = um1 - u0;
+  const R b01 = beta3(um1 - R(2) * u0 + up1, um1 - up1);
+  const R b2 = beta3(u0 - R(2) * up1 + up2, R(3) * u0 - R(4) * up1 + up2);
+  const R b3 = beta3(um2 - R(2) * um1 + u0, um2 - R(4) * um1 + R(3) * u0);
+  const R tau = beta3(up2 - R(4) * up1 + R(6) * u0 - R(4) * um1 + um2, up2 - R(2) * up1 + R(2) * um1 - um2);
+  return wenois_tail<R>(s0, s1, s2, s3, e0 * e0, e1 * e1, b01, b2, b3, tau, eps);
+}
+
+// u0 = 0 (left-biased interpolation of deviations from node i)
+template <class R>
+__device__ __forceinline__ R wenois_c0(R um2, R um1, R up1, R up2, R eps) {
+  const R s0 = R(0.5) * up1;
+  const R s1 = R(-0.5) * um1;
+  const R s2 = R(0.75) * up1 - R(0.125) * up2;
+  const R s3 = R(0.375) * um2 - R(1.25) * um1;
+  const R a01 = um1 + up1, c01 = um1 - up1;
+  const R b01 = beta3(a01, c01);
+  const R b2 = beta3(up2 - R(2) * up1, up2 - R(4) * up1);
+  const R b3 = beta3(um2 - R(2) * um1, um2 - R(4) * um1);
+  const R tau = beta3((um2 + up2) - R(4) * a01, (up2 - um2) + R(2) * c01);
+  return wenois_tail<R>(s0, s1, s2, s3, up1 * up1, um1 * um1, b01, b2, b3, tau, eps);
+}
+
+// up1 = 0 (the mirrored, right-biased interpolation of deviations from node i)
+template <class R>
+__device__ __forceinline__ R wenois_p0(R um2, R um1, R u0, R up2, R eps) {
+  const R s0 = R(0.5) * u0;
+  const R s1 = R(0.5) * (R(3) * u0 - um1);
+  const R s2 = R(0.125) * (R(3) * u0 - up2);
+  const R s3 = R(0.125) * (R(3) * um2 - R(10) * um1 + R(15) * u0);
+  const R e1 = um1 - u0;
+  const R b01 = beta3(um1 - R(2) * u0, um1);
+  const R b2 = beta3(u0 + up2, R(3) * u0 + up2);
+  const R b3 = beta3(um2 - R(2) * um1 + u0, um2 - R(4) * um1 + R(3) * u0);
+  const R tau = beta3((um2 + up2) + R(6) * u0 - R(4) * um1, (up2 - um2) + R(2) * um1);
+  return wenois_tail<R>(s0, s1, s2, s3, u0 * u0, e1 * e1, b01, b2, b3, tau, eps);
 }
 
 // ---------------------------------------------------------------------------
@@ -808,8 +837,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
       double UL[NF], UR[NF];
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
-        UL[f] = wenois<double>(U[0][f], U[1][f], 0.0, U[3][f], U[4][f], epsR);
-        UR[f] = wenois<double>(U[5][f], U[4][f], U[3][f], 0.0, U[1][f], epsR);
+        UL[f] = wenois_c0<double>(U[0][f], U[1][f], U[3][f], U[4][f], epsR);
+        UR[f] = wenois_p0<double>(U[5][f], U[4][f], U[3][f], U[1][f], epsR);
       }
       // Steps 4-5: back-project, add node i, V -> W.
       double WL[NF], WR[NF], VL[NF], VR[NF];  // V: (a1r1, a2r2, vel.., p, a1)
