@@ -183,18 +183,61 @@ def algorithmic_ops(nx, ny):
     o.opcount_reset()
     o.rhs(pr.W, dt)
     c = o.opcount()
+    rows = o.opcount_rows()
     units = pr.ncells * pr.ndim  # cell-direction updates
     ops = {k: v / units for k, v in c.items()}
+    per_row = {r: {k: v / units for k, v in rc.items()} for r, rc in rows.items()}
     # The oracle forms the IS weights with the five ratio divisions and four
     # normalising divisions as printed (Sec. 4.3).  The same weights need one
     # division: scaling every eta_k by the product of the five (beta + eps)
     # costs 14 multiplications.  Count that form, so the roofline does not
     # credit the kernel with divisions the method does not need.
     is_calls = 2 * (pr.ndim + 4) * o.stats.midpoints / units
-    ops["div"] -= 8 * is_calls
-    ops["mul"] += 14 * is_calls
+    for d_ in (ops, per_row["wcns_is"]):
+        d_["div"] -= 8 * is_calls
+        d_["mul"] += 14 * is_calls
     ops["is_interpolations"] = is_calls
+    ops["per_step"] = per_row
     return ops
+
+
+# Steps the mixed-precision sweeps compute in FP64 on every cell (node
+# pressure and sound speed from the conservative state, the stored node
+# fluxes, the flux difference and state accumulation); all other steps run
+# in FP32 (the limiters' FP32-certified path; their FP64 theta solves only
+# run where certification fails, none on the bench workload).
+MIXED_FP64_STEPS = ("node_eos", "node_flux", "update")
+
+
+def mixed_roofline(ops, peaks, avg_ms, ncell, fallbacks):
+    """Roofline of the dominant mixed sweep: algorithmic FP64 flops at the
+    FP64 FMA peak plus FP32 flops at the FP32 FMA peak (divisions and square
+    roots as one flop each); the 'overlapped' form takes the larger of the
+    two times instead of their sum."""
+    f64 = f32 = 0.0
+    for step, c in ops["per_step"].items():
+        n = c["add"] + c["mul"] + c["div"] + c["sqrt"] + c["minmax"]
+        if step in MIXED_FP64_STEPS:
+            f64 += n
+        else:
+            f32 += n  # the wave-speed maximum included: reduced in FP32 in the combine epilogue
+    p64 = peaks.get("fp64_fma_tflops", 1.25) * 1e12
+    p32 = peaks.get("fp32_fma_tflops", 76.5) * 1e12
+    t64 = f64 * ncell / p64
+    t32 = f32 * ncell / p32
+    t = avg_ms * 1e-3
+    # achieved in FP64-equivalent flop/s: FP32 flops weighted by p64/p32
+    achieved = (f64 + f32 * p64 / p32) * ncell / t / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": p64 / 1e12,
+            "unit": "TFLOP/s (FP64-equivalent: FP32 flops weighted by the FP64:FP32 peak ratio)",
+            "frac": (t64 + t32) / t, "frac_overlapped": max(t64, t32) / t,
+            "fp64_flops_per_cell_dir": f64, "fp32_flops_per_cell_dir": f32,
+            "roofline_us": (t64 + t32) * 1e6, "roofline_us_overlapped": max(t64, t32) * 1e6,
+            "avg_launch_ms": avg_ms, "fp64_fallbacks": fallbacks, "traffic": None,
+            "note": "mixed sweep: FP64 steps %s at the measured FP64 FMA peak plus the other steps at the "
+                    "measured FP32 FMA peak, divisions and square roots as one flop, op mix per step from "
+                    "the oracle's op-counting build (IS weights in one-division form); frac = roofline "
+                    "time / live CUDA-event time of one launch (of measured)" % (MIXED_FP64_STEPS,)}
 
 
 # ---------------------------------------------------------------------------
@@ -319,7 +362,10 @@ def run_gb300(args, world, rank, local):
         for _ in range(args.warmup):
             sm_.advance_steps(Wm, 1, cfl=0.5)
         torch.cuda.synchronize()
+        sm_.profile_enable(16 * args.steps + 16)
+        sm_.profile_read()
         tm, _ = timed_steps(torch, sm_, Wm, args.steps, flush)
+        prof_m = sm_.profile_read()
         msm = barrier_and_max(world, sum(tm)) / args.steps
         # error of the mixed run against the FP64 run after the same steps
         a, b = Wm.double(), W64
@@ -332,7 +378,7 @@ def run_gb300(args, world, rank, local):
                      "steps": args.warmup + args.steps,
                      "l1_rel": {"rho": l1(rho_m, rho_d), "E": l1(a[4], b[4]), "alpha1": l1(a[5], b[5])},
                      "linf_rel": {"rho": linf(rho_m, rho_d), "E": linf(a[4], b[4]), "alpha1": linf(a[5], b[5])}},
-                 "stats": sm_.stats()}
+                 "stats": sm_.stats(), "profile": prof_m}
         sm_.close()
 
     # ---------------- end to end through the host-buffer entry point --------
@@ -373,7 +419,7 @@ def run_gb300(args, world, rank, local):
                 "kernel": "sweep_kernel<2,%d,double> (%s sweep)" % (dom, "xy"[dom]),
                 "avg_launch_ms": avg_ms,
                 "flop_eq_per_cell_dir": flop_eq,
-                "ops_per_cell_dir": ops,
+                "ops_per_cell_dir": {k: v for k, v in ops.items() if k != "per_step"},
                 "peak_source": peaks.get("source", "nominal FP64 1.25 TFLOP/s (fallback)"),
                 "note": "FP64-pipe roofline: add/mul/minmax count 1 flop, div/sqrt count their measured "
                         "cost in FMA-flop equivalents; op mix from the oracle's op-counting build with the "
@@ -391,6 +437,13 @@ def run_gb300(args, world, rank, local):
                 roofline["traffic"] = tr[k]["bytes_per_launch"]
         except Exception:
             pass
+    roofline["ops_per_step_per_cell_dir"] = ops["per_step"]
+    if mixed:
+        pm = mixed.pop("profile")
+        dm = max((d for d in range(2) if pm["launches"][d] > 0), key=lambda d: pm["ms"][d])
+        mixed["roofline"] = mixed_roofline(ops, peaks, pm["ms"][dm] / pm["launches"][dm], ncell,
+                                           mixed["stats"]["fp64_fallbacks"])
+        mixed["roofline"]["kernel"] = "sweep_kernel_mixed<2,%d> (%s sweep)" % (dm, "xy"[dm])
     cpu = None if args.no_cpu_baseline else cpu_baseline(args.nx, args.ny)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

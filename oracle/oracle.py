@@ -120,6 +120,8 @@ def _lib(counting=False):
         if counting:
             lib.oc_opcount_reset.argtypes = []
             lib.oc_opcount_get.argtypes = [P(C.c_ulonglong)]
+            lib.oc_opcount_rows.argtypes = [P(C.c_ulonglong)]
+            lib.oc_opcount_rows.restype = C.c_int
         _LIBS[key] = lib
     return _LIBS[key]
 
@@ -300,6 +302,24 @@ class Oracle:
         out = (C.c_ulonglong * 5)()
         self.lib.oc_opcount_get(out)
         return dict(zip(("add", "mul", "div", "sqrt", "minmax"), [int(x) for x in out]))
+
+    # step number -> name of the step of the method the operations belong to
+    OPCOUNT_ROWS = {0: "other", 2: "node_eos", 3: "projection", 4: "wcns_is", 5: "back_projection",
+                    6: "interp_limiter", 7: "midpoint_hllc", 8: "node_flux", 9: "hcs_split",
+                    10: "first_order_hllc", 11: "flux_limiter", 12: "update", 13: "max_wavespeed"}
+
+    def opcount_rows(self):
+        """Operation counts since the last reset, per step of the method:
+        {step name: {add, mul, div, sqrt, minmax}} (steps with no work left out)."""
+        assert self.counting
+        out = (C.c_ulonglong * (5 * 16))()
+        nrows = self.lib.oc_opcount_rows(out)
+        rows = {}
+        for r in range(nrows):
+            c = dict(zip(("add", "mul", "div", "sqrt", "minmax"), [int(x) for x in out[5 * r:5 * r + 5]]))
+            if any(c.values()):
+                rows[self.OPCOUNT_ROWS.get(r, "row%d" % r)] = c
+        return rows
 
 
 def wcnsis_left(u5, eps=1e-40):

@@ -42,11 +42,32 @@
 #include <cstring>
 #include <vector>
 
+// Steps of the method, for the op-counting build's per-step tallies.
+enum OcRow {
+  ROW_OTHER = 0,
+  ROW_NODE_EOS = 2,      // node primitives: velocities, p, c (Section 2)
+  ROW_PROJECT = 3,       // characteristic projection (Appendix A)
+  ROW_WCNS_IS = 4,       // WCNS-IS interpolation (Section 4.3)
+  ROW_BACKPROJECT = 5,   // back-projection and V -> W (Section 4.2)
+  ROW_INTERP_LIMIT = 6,  // interpolation limiter (Section 5.1)
+  ROW_MID_HLLC = 7,      // midpoint HLLC flux (Sections 3.1-3.2)
+  ROW_NODE_FLUX = 8,     // node fluxes G_j (Section 4.2, step 7)
+  ROW_HCS = 9,           // HCS reconstruction and the split (Sections 4.1, 3.2)
+  ROW_HLLC1 = 10,        // first-order HLLC flux and its split (Section 3.2)
+  ROW_FLUX_LIMIT = 11,   // flux limiter (Section 5.2)
+  ROW_UPDATE = 12,       // flux difference + alpha1 div u (Section 4)
+  ROW_WAVESPEED = 13,    // maximum wave speed (Section 3.3)
+};
+
 #ifdef ORACLE_COUNT_OPS
 #include "opcount.hpp"
 OracleOpCounts g_oracle_ops = {0, 0, 0, 0, 0};
+OracleOpCounts g_oracle_rows[ORACLE_NROWS] = {};
+int g_oracle_row = ROW_OTHER;
+#define OC_ROW(r) (g_oracle_row = (r))
 typedef Counted real;
 #else
+#define OC_ROW(r) ((void)0)
 typedef double real;
 static inline real o_sqrt(real a) { return std::sqrt(a); }
 static inline real o_min(real a, real b) { return a < b ? a : b; }
@@ -211,12 +232,14 @@ struct Node {
 static void node_prep(const Eos &e, int ndim, int d, const real *W, Node &nd) {
   const int nf = ndim + 4;
   for (int q = 0; q < nf; ++q) nd.W[q] = W[q];
+  OC_ROW(ROW_NODE_EOS);
   nd.t = thermo(e, ndim, W);
   nd.V[0] = W[0];
   nd.V[1] = W[1];
   for (int j = 0; j < ndim; ++j) nd.V[2 + j] = nd.t.vel[j];
   nd.V[2 + ndim] = nd.t.p;
   nd.V[3 + ndim] = W[3 + ndim];
+  OC_ROW(ROW_NODE_FLUX);
   phys_flux(ndim, d, W, nd.t, nd.F);
   nd.un = nd.t.vel[d];
   for (int q = 0; q < nf; ++q) nd.G[q] = nd.F[q];
@@ -571,6 +594,7 @@ static void midpoint_flux(const Eos &e, const oc_config &cfg, int ndim, int d, c
   st->midpoints++;
 
   // First-order HLLC flux from (W_i, W_{i+1}) and its split (Section 3.2).
+  OC_ROW(ROW_HLLC1);
   real GH[7], uH;
   hllc_flux(ndim, d, ni.W, ni.t, ni.F, ni1.W, ni1.t, ni1.F, GH, &uH);
   real GHm[7], GHp[7];
@@ -590,6 +614,7 @@ static void midpoint_flux(const Eos &e, const oc_config &cfg, int ndim, int d, c
 
   // Step 1 (W -> V) is done per node in node_prep.
   // Step 2: project the six nodes with Rinv_{i+1/2}.
+  OC_ROW(ROW_PROJECT);
   real R[49], Rinv[49];
   char_matrices(ndim, d, ni.W, ni.t, ni1.W, ni1.t, R, Rinv);
   real U[6][7];
@@ -597,6 +622,7 @@ static void midpoint_flux(const Eos &e, const oc_config &cfg, int ndim, int d, c
   // Step 3: left- and right-biased IS interpolation of every characteristic
   // variable.  The right-biased one is the left-biased formula applied to
   // the stencil mirrored about i+1/2.
+  OC_ROW(ROW_WCNS_IS);
   real UL[7], UR[7];
   for (int q = 0; q < nf; ++q) {
     real sl[5] = {U[0][q], U[1][q], U[2][q], U[3][q], U[4][q]};
@@ -605,6 +631,7 @@ static void midpoint_flux(const Eos &e, const oc_config &cfg, int ndim, int d, c
     UR[q] = wcnsis_left(sr, cfg.eps_is).value;
   }
   // Step 4: back-project.
+  OC_ROW(ROW_BACKPROJECT);
   real VL[7], VR[7];
   matvec(nf, R, UL, VL);
   matvec(nf, R, UR, VR);
@@ -613,6 +640,7 @@ static void midpoint_flux(const Eos &e, const oc_config &cfg, int ndim, int d, c
   prim_to_cons(e, ndim, VL, WL);
   prim_to_cons(e, ndim, VR, WR);
   // Interpolation limiter (Section 5.1): left toward W_i, right toward W_{i+1}.
+  OC_ROW(ROW_INTERP_LIMIT);
   if (cfg.scheme == OC_SCHEME_PP_WCNS_IS) {
     int hard = 0;
     st->interp_limited += interp_limit(e, cfg, ndim, ni.W, WL, &hard);
@@ -621,6 +649,7 @@ static void midpoint_flux(const Eos &e, const oc_config &cfg, int ndim, int d, c
     st->interp_hard += hard;
   }
   // Step 6: midpoint HLLC flux and velocity.
+  OC_ROW(ROW_MID_HLLC);
   Thermo tL = thermo(e, ndim, WL);
   Thermo tR = thermo(e, ndim, WR);
   real FL[7], FR[7];
@@ -630,6 +659,7 @@ static void midpoint_flux(const Eos &e, const oc_config &cfg, int ndim, int d, c
   hllc_flux(ndim, d, WL, tL, FL, WR, tR, FR, Gt, &ut);
   // Step 7 (node fluxes G_j, velocities u_j) is done per node in node_prep.
   // Step 8: HCS reconstruction of G-hat and u-hat.
+  OC_ROW(ROW_HCS);
   real Gh[7];
   for (int q = 0; q < nf; ++q) {
     real g[6];
@@ -648,6 +678,7 @@ static void midpoint_flux(const Eos &e, const oc_config &cfg, int ndim, int d, c
   Gp[A] = Gh[A] - ni1.W[A] * uh;
 
   // Flux limiter (Section 5.2).
+  OC_ROW(ROW_FLUX_LIMIT);
   if (cfg.scheme == OC_SCHEME_PP_WCNS_IS) {
     int hard = 0;
     st->flux_limited +=
@@ -781,6 +812,7 @@ static void rhs_impl(const oc_config &c, const double *W, double *dWdt, double d
   if (smax_given) {
     for (int d = 0; d < 3; ++d) smax[d] = smax_given[d];
   } else {
+    OC_ROW(ROW_WAVESPEED);
     max_wavespeed_impl(c, W, smax);
   }
   double tau[3], tsum = 0.0;
@@ -820,6 +852,7 @@ static void rhs_impl(const oc_config &c, const double *W, double *dWdt, double d
         midpoint_flux(e, c, c.ndim, d, np, lam, &Gm[(size_t)m * nf], &Gp[(size_t)m * nf], st);
       }
       // Semi-discrete update: dW_i/dt -= (G^-_{i+1/2} - G^+_{i-1/2}) / dx.
+      OC_ROW(ROW_UPDATE);
       for (int i = 0; i < n; ++i) {
         ijk[d] = i;
         long idx = cell_index(c, ijk);
@@ -1099,7 +1132,22 @@ int oc_flux_limit(const oc_config *c, int d, const double *Wi, const double *Wi1
 }
 
 #ifdef ORACLE_COUNT_OPS
-void oc_opcount_reset(void) { g_oracle_ops = OracleOpCounts{0, 0, 0, 0, 0}; }
+void oc_opcount_reset(void) {
+  g_oracle_ops = OracleOpCounts{0, 0, 0, 0, 0};
+  for (int r = 0; r < ORACLE_NROWS; ++r) g_oracle_rows[r] = OracleOpCounts{0, 0, 0, 0, 0};
+  g_oracle_row = ROW_OTHER;
+}
+// out[5 r + k] = count k (add, mul, div, sqrt, minmax) of step r, r < ORACLE_NROWS
+int oc_opcount_rows(unsigned long long *out) {
+  for (int r = 0; r < ORACLE_NROWS; ++r) {
+    out[5 * r + 0] = g_oracle_rows[r].add;
+    out[5 * r + 1] = g_oracle_rows[r].mul;
+    out[5 * r + 2] = g_oracle_rows[r].div;
+    out[5 * r + 3] = g_oracle_rows[r].sqrt;
+    out[5 * r + 4] = g_oracle_rows[r].minmax;
+  }
+  return ORACLE_NROWS;
+}
 // out = (add, mul, div, sqrt, minmax)
 void oc_opcount_get(unsigned long long *out5) {
   out5[0] = g_oracle_ops.add;

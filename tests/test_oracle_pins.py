@@ -627,3 +627,55 @@ def test_op_counting_build_counts_work():
     per_cell = (c["add"] + c["mul"]) / 64
     assert 1000 < per_cell < 20000
     assert c["div"] > 0 and c["sqrt"] > 0
+
+
+def test_op_counting_per_step():
+    """The op-counting build books every operation to one step of the
+    method: the steps sum to the total; the WCNS-IS step holds exactly two
+    interpolations (left, right) per characteristic field and midpoint, and
+    the HCS step exactly nf + 1 reconstructions (fluxes and velocity) plus
+    the two alpha1 split terms (Section 3.2); the first-order scheme has no
+    high-order step at all."""
+    import ctypes as C
+
+    from oracle.oracle import _lib
+    lib = _lib(True)
+    pr = P.advection_2d(8)
+    nf = pr.ndim + 4
+
+    def one_call(fn):
+        lib.oc_opcount_reset()
+        fn()
+        out = (C.c_ulonglong * 5)()
+        lib.oc_opcount_get(out)
+        return dict(zip(("add", "mul", "div", "sqrt", "minmax"), [int(x) for x in out]))
+
+    u5 = np.array([0.3, -1.2, 0.7, 2.5, -0.4])
+    o11 = np.zeros(11)
+    is_ops = one_call(lambda: lib.oc_wcnsis_left(u5.ctypes.data_as(C.POINTER(C.c_double)), 1e-40,
+                                                 o11.ctypes.data_as(C.POINTER(C.c_double))))
+    g6 = np.array([1.0, 2.0, 0.5, -1.0, 3.0, 0.25])
+    hcs_ops = one_call(lambda: lib.oc_hcs_recon(0.75, g6.ctypes.data_as(C.POINTER(C.c_double))))
+    assert is_ops["div"] >= 5 and hcs_ops["mul"] >= 4
+
+    o = Oracle(pr.n, pr.lo, pr.hi, pr.bcs, counting=True, **pr.eos)
+    o.opcount_reset()
+    o.rhs(pr.W, pr.dt_fixed)
+    tot, rows = o.opcount(), o.opcount_rows()
+    for k in tot:
+        assert sum(r[k] for r in rows.values()) == tot[k]
+    assert "other" not in rows
+    mid = o.stats.midpoints
+    for k in tot:
+        assert rows["wcns_is"][k] == 2 * nf * mid * is_ops[k]
+        split = 2 if k in ("add", "mul") else 0
+        assert rows["hcs_split"][k] == mid * ((nf + 1) * hcs_ops[k] + split)
+    # every step of the PP-WCNS-IS scheme does work on this problem
+    for step in ("node_eos", "node_flux", "projection", "wcns_is", "back_projection", "interp_limiter",
+                 "midpoint_hllc", "hcs_split", "first_order_hllc", "flux_limiter", "update", "max_wavespeed"):
+        assert step in rows, step
+
+    o1 = Oracle(pr.n, pr.lo, pr.hi, pr.bcs, counting=True, scheme="hllc1", **pr.eos)
+    o1.opcount_reset()
+    o1.rhs(pr.W, pr.dt_fixed)
+    assert set(o1.opcount_rows()) == {"node_eos", "node_flux", "first_order_hllc", "update", "max_wavespeed"}
