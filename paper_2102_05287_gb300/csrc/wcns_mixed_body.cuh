@@ -195,6 +195,138 @@ __device__ __forceinline__ void node_thermo64(const EosConst &eos, const double 
   c = sqrt(((Gam + 1.0) * rhoe - Pi) * (iG * iG) * ir);
 }
 
+// Small vectors passed by value to the out-of-line FP64 fallbacks below.
+template <int N>
+struct FVec {
+  float v[N];
+};
+template <int NF>
+struct LimitedState {
+  float d[NF];  // deviation of the limited state from node i
+  float c;      // its sound speed
+  int flags;    // interp_limit flags (0: unchanged, d and c not set)
+};
+
+// FP64 interpolation limiter of the mixed path (Sec. 5.1, Algorithms 1-3),
+// taken where the FP32 certification fails: node k's FP64 state Wn
+// (shared memory, stride nn), the interpolated state rebuilt in FP64 from
+// node i's hi/lo parts plus the deviation d, V -> W, then the limiter; a
+// limited state comes back as a deviation from node i and its sound speed.
+// Out of line so that its FP64 registers do not shape the FP32 fast path's
+// register allocation.
+template <int NDIM>
+__device__ __noinline__ LimitedState<NDIM + 4> mixed_interp_fallback(const EosConst eos, const LimTol tol,
+                                                                      const double *Wsm, int nn, int nk,
+                                                                      const FVec<NDIM + 4> hi_i,
+                                                                      const FVec<NDIM + 4> lo_i,
+                                                                      const FVec<NDIM + 4> d) {
+  constexpr int NF = NDIM + 4, E = 2 + NDIM, A = 3 + NDIM;
+  LimitedState<NF> out;
+  double Wn[NF], Wt[NF], V[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    Wn[f] = Wsm[f * nn + nk];
+    V[f] = ((double)hi_i.v[f] + (double)lo_i.v[f]) + (double)d.v[f];
+  }
+  const double rho = V[0] + V[1];
+  double k2s = 0.0;
+#pragma unroll
+  for (int k = 0; k < NDIM; ++k) {
+    Wt[2 + k] = rho * V[2 + k];
+    k2s = fma(V[2 + k], V[2 + k], k2s);
+  }
+  Wt[0] = V[0];
+  Wt[1] = V[1];
+  Wt[E] = fma(V[E], mixGamma(eos, V[A]), mixPi(eos, V[A])) + 0.5 * rho * k2s;
+  Wt[A] = V[A];
+  out.flags = interp_limit<NDIM>(eos, tol, Wn, Wt);
+  if (out.flags) {
+    const double r = Wt[0] + Wt[1];
+    const double ir = 1.0 / r;
+    double mm = 0.0, vv[NDIM];
+#pragma unroll
+    for (int k = 0; k < NDIM; ++k) {
+      vv[k] = Wt[2 + k] * ir;
+      mm = fma(Wt[2 + k], vv[k], mm);
+    }
+    const double pn = (Wt[E] - 0.5 * mm - mixPi(eos, Wt[A])) / mixGamma(eos, Wt[A]);
+    out.d[0] = (float)(Wt[0] - ((double)hi_i.v[0] + (double)lo_i.v[0]));
+    out.d[1] = (float)(Wt[1] - ((double)hi_i.v[1] + (double)lo_i.v[1]));
+#pragma unroll
+    for (int k = 0; k < NDIM; ++k)
+      out.d[2 + k] = (float)(vv[k] - ((double)hi_i.v[2 + k] + (double)lo_i.v[2 + k]));
+    out.d[E] = (float)(pn - ((double)hi_i.v[E] + (double)lo_i.v[E]));
+    out.d[A] = (float)(Wt[A] - ((double)hi_i.v[A] + (double)lo_i.v[A]));
+    // sound speed of the limited state
+    const double Gm_ = mixGamma(eos, Wt[A]);
+    const double pb = mixPi(eos, Wt[A]) / (Gm_ + 1.0);
+    out.c = (float)sqrt((1.0 + 1.0 / Gm_) * (pn + pb) * ir);
+  }
+  return out;
+}
+
+// FP64 flux limiter of the mixed path (Sec. 5.2, Algorithms 4-6), taken
+// where the FP32 certification fails: on FP64 node states and the FP64
+// first-order HLLC flux (its positivity is what the limiter falls back on,
+// so it is not taken from the FP32 deviations).  The high-order split
+// fluxes are rebuilt from node i's FP64 flux plus the FP32 deviations dGh;
+// the limited G^-, G^+ are written to the midpoint's shared-memory slot
+// (F: shared components, am / ap: alpha1 components).  Returns the
+// flux_limit flags (a non-finite high-order flux takes the hard switch).
+// Out of line for the same reason as mixed_interp_fallback.
+template <int NDIM, int DIR>
+__device__ __noinline__ int mixed_flux_fallback(const EosConst eos, const LimTol tol, const double *Wsm,
+                                                const double *Gsm, int nn, int ni, int ni1, double *Fsm,
+                                                double *am, double *ap, int nm, int ms, double ui64, float duh,
+                                                const FVec<NDIM + 4> dGh, double lam) {
+  constexpr int NF = NDIM + 4, A = 3 + NDIM;
+  double Wi[NF], Wi1[NF], Fi[NF], Fi1[NF], GH[NF], uH, Gm[NF], Gp[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    Wi[f] = Wsm[f * nn + ni];
+    Wi1[f] = Wsm[f * nn + ni1];
+    Fi[f] = Gsm[f * nn + ni];
+    Fi1[f] = Gsm[f * nn + ni1];
+  }
+#pragma unroll
+  for (int f = 0; f < NF - 1; ++f) Gm[f] = Gp[f] = Fi[f] + f2d(dGh.v[f]);
+  Fi[A] = Fi1[A] = 0.0;
+  {
+    double vi[NDIM], vi1[NDIM], pi_, pi1, ci_, ci1_;
+    node_thermo64<NDIM>(eos, Wi, vi, pi_, ci_);
+    node_thermo64<NDIM>(eos, Wi1, vi1, pi1, ci1_);
+    hllc<NDIM, DIR, double>(Wi, vi, pi_, Wi[0] + Wi[1], ci_, Wi1, vi1, pi1, Wi1[0] + Wi1[1], ci1_, GH, uH);
+  }
+  double GHm[NF], GHp[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) GHm[f] = GHp[f] = GH[f];
+  GHm[A] = GH[A] - Wi[A] * uH;
+  GHp[A] = GH[A] - Wi1[A] * uH;
+  const double uh64 = ui64 + (double)duh;
+  Gm[A] = Gsm[A * nn + ni] + (double)dGh.v[A] - Wi[A] * uh64;
+  Gp[A] = Gsm[A * nn + ni] + (double)dGh.v[A] - Wi1[A] * uh64;
+  bool finite = true;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) finite = finite && isfinite(Gm[f]) && isfinite(Gp[f]);
+  int fl;
+  if (finite) {
+    fl = flux_limit<NDIM>(eos, tol, Wi, Wi1, Fi, Fi1, GHm, GHp, lam, Gm, Gp);
+  } else {
+    // a non-finite high-order flux: the hard switch of Sec. 5.2
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      Gm[f] = GHm[f];
+      Gp[f] = GHp[f];
+    }
+    fl = 2;
+  }
+#pragma unroll
+  for (int f = 0; f < NF - 1; ++f) Fsm[f * nm + ms] = Gm[f];
+  am[ms] = Gm[A];
+  ap[ms] = Gp[A];
+  return fl;
+}
+
 template <int NDIM, int DIR, class T, class Geo>
 __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &geo, double *smem_raw) {
   using R = float;
@@ -367,54 +499,40 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
     for (int j = 0; j < NDIM; ++j) ref.u[j] = hi_i[2 + j];
     ref.p = hi_i[E];
     ref.a1 = hi_i[A];
-    // FP32 conservative states of nodes i, i+1 from the primitive hi parts
+    // FP32 conservative state of node nk from its primitive hi parts
     // (relative precision; used for (E + p)_ref and the half-state checks).
-    float Wf[2][NF];
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const int nk = k ? ni1 : ni;
-      float r1 = sm.Vh[0 * T::NN + nk], r2 = sm.Vh[1 * T::NN + nk], al = sm.Vh[A * T::NN + nk];
-      float pk = sm.Vh[E * T::NN + nk];
+    auto wf_node = [&](int nk, float *Wo) {
+      const float r1 = sm.Vh[0 * T::NN + nk], r2 = sm.Vh[1 * T::NN + nk], al = sm.Vh[A * T::NN + nk];
+      const float pk = sm.Vh[E * T::NN + nk];
       const float rho = r1 + r2;
       float ke = 0.0f;
-      Wf[k][0] = r1;
-      Wf[k][1] = r2;
+      Wo[0] = r1;
+      Wo[1] = r2;
 #pragma unroll
       for (int j = 0; j < NDIM; ++j) {
         const float u = sm.Vh[(2 + j) * T::NN + nk];
-        Wf[k][2 + j] = rho * u;
+        Wo[2 + j] = rho * u;
         ke += u * u;
       }
-      Wf[k][E] = pk * (eos.r2f + eos.drf * al) + eos.q1f * al + 0.5f * rho * ke;
-      Wf[k][A] = al;
-    }
-    ref.Ep = Wf[0][E] + hi_i[E];
-    const float ci = sm.c[ni], ci1 = sm.c[ni1];
-    const unsigned int ok_i = sm.ok[ni], ok_i1 = sm.ok[ni1];
-
-    float d1[NF];  // node i+1
-    dev(si + 1, d1);
-    // First-order HLLC in deviation form (Sec. 3.2).
-    float dGH[NF], sH;
+      Wo[E] = pk * (eos.r2f + eos.drf * al) + eos.q1f * al + 0.5f * rho * ke;
+      Wo[A] = al;
+    };
     {
-      float d0[NF];
-#pragma unroll
-      for (int f = 0; f < NF; ++f) d0[f] = 0.0f;
-      hllc_dev<NDIM, DIR, R>(ref, eos, d0, ci, d1, ci1, dGH, sH);
+      float W0[NF];
+      wf_node(ni, W0);
+      ref.Ep = W0[E] + hi_i[E];
     }
-    // Delta of alpha between the nodes and node-flux deviation of node i+1
-    const float dal = d1[A];
-    float dG1[NF];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) dG1[f] = gdev(si + 1, f);
+    const float ci = sm.c[ni], ci1 = sm.c[ni1];
 
+    // The high-order flux comes first; the first-order flux, the node states
+    // and the node-flux deviations the certification needs are formed after
+    // it, so that none of them is held in registers across WCNS-IS.
     float dGh[NF], duh;  // high-order G^ - G_i and u^ - u_i
     bool slow_flux = false;
-    if (a.scheme == SCHEME_HLLC1) {
-#pragma unroll
-      for (int f = 0; f < NF; ++f) dGh[f] = dGH[f];
-      duh = sH - ref.u[DIR];
-    } else {
+    if (a.scheme != SCHEME_HLLC1) {
+      float d1[NF];  // node i+1
+      dev(si + 1, d1);
+      const unsigned int ok_i = sm.ok[ni], ok_i1 = sm.ok[ni1];
       // Steps 1-2: projection with means of nodes i, i+1 (App. A).
       const float ar1 = 0.5f * (hi_i[0] + sm.Vh[0 * T::NN + ni1]);
       const float ar2 = 0.5f * (hi_i[1] + sm.Vh[1 * T::NN + ni1]);
@@ -508,50 +626,21 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
           }
           if (cert) continue;
           nslow += cnt;
-          // FP64 path: node i plus deviation, V -> W, Algorithms 1-3.
-          const int nk = side ? ni1 : ni;
-          double Wn[NF], Wt[NF], V[NF];
+          FVec<NF> hv, lv, dv;
 #pragma unroll
           for (int f = 0; f < NF; ++f) {
-            Wn[f] = sm.W[f * T::NN + nk];
-            V[f] = ((double)hi_i[f] + (double)lo_i[f]) + (double)d[f];
+            hv.v[f] = hi_i[f];
+            lv.v[f] = lo_i[f];
+            dv.v[f] = d[f];
           }
-          const double rho = V[0] + V[1];
-          double k2s = 0.0;
+          const LimitedState<NF> ls =
+              mixed_interp_fallback<NDIM>(eos, tol, sm.W, T::NN, side ? ni1 : ni, hv, lv, dv);
+          nlim_i += cnt * (ls.flags & 1);
+          nhard_i += cnt * (ls.flags >> 1);
+          if (ls.flags) {
 #pragma unroll
-          for (int k = 0; k < NDIM; ++k) {
-            Wt[2 + k] = rho * V[2 + k];
-            k2s = fma(V[2 + k], V[2 + k], k2s);
-          }
-          Wt[0] = V[0];
-          Wt[1] = V[1];
-          Wt[E] = fma(V[E], mixGamma(eos, V[A]), mixPi(eos, V[A])) + 0.5 * rho * k2s;
-          Wt[A] = V[A];
-          const int fl = interp_limit<NDIM>(eos, tol, Wn, Wt);
-          nlim_i += cnt * (fl & 1);
-          nhard_i += cnt * (fl >> 1);
-          if (fl) {
-            const double r = Wt[0] + Wt[1];
-            const double ir = 1.0 / r;
-            double mm = 0.0, vv[NDIM];
-#pragma unroll
-            for (int k = 0; k < NDIM; ++k) {
-              vv[k] = Wt[2 + k] * ir;
-              mm = fma(Wt[2 + k], vv[k], mm);
-            }
-            const double pn = (Wt[E] - 0.5 * mm - mixPi(eos, Wt[A])) / mixGamma(eos, Wt[A]);
-            const double ref64[5] = {(double)hi_i[0] + (double)lo_i[0], (double)hi_i[1] + (double)lo_i[1],
-                                     (double)hi_i[E] + (double)lo_i[E], (double)hi_i[A] + (double)lo_i[A], 0.0};
-            d[0] = (float)(Wt[0] - ref64[0]);
-            d[1] = (float)(Wt[1] - ref64[1]);
-#pragma unroll
-            for (int k = 0; k < NDIM; ++k) d[2 + k] = (float)(vv[k] - ((double)hi_i[2 + k] + (double)lo_i[2 + k]));
-            d[E] = (float)(pn - ref64[2]);
-            d[A] = (float)(Wt[A] - ref64[3]);
-            // sound speed of the limited state
-            const double Gm_ = mixGamma(eos, Wt[A]);
-            const double pb = mixPi(eos, Wt[A]) / (Gm_ + 1.0);
-            cs[side] = (float)sqrt((1.0 + 1.0 / Gm_) * (pn + pb) * ir);
+            for (int f = 0; f < NF; ++f) d[f] = ls.d[f];
+            cs[side] = ls.c;
           }
         }
       }
@@ -560,7 +649,8 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
       hllc_dev<NDIM, DIR, R>(ref, eos, dV[0], cs[0], dV[1], cs[1], dGt, ut);
 #pragma unroll
       for (int f = 0; f < NF; ++f)
-        dGh[f] = hcs<R>(dGt[f], gdev(m, f), gdev(m + 1, f), 0.0f, dG1[f], gdev(m + 4, f), gdev(m + 5, f));
+        dGh[f] = hcs<R>(dGt[f], gdev(m, f), gdev(m + 1, f), 0.0f, gdev(si + 1, f), gdev(m + 4, f),
+                        gdev(m + 5, f));
       {
         auto udev = [&](int s) {
           const int sl = nslot(l, s);
@@ -570,6 +660,31 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
                      udev(m + 5));
       }
     }
+    // First-order HLLC in deviation form (Sec. 3.2).
+    float d1[NF];  // node i+1
+    dev(si + 1, d1);
+    float dGH[NF], sH;
+    {
+      float d0[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) d0[f] = 0.0f;
+      hllc_dev<NDIM, DIR, R>(ref, eos, d0, ci, d1, ci1, dGH, sH);
+    }
+    if (a.scheme == SCHEME_HLLC1) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) dGh[f] = dGH[f];
+      duh = sH - ref.u[DIR];
+    }
+    // Delta of alpha between the nodes, node states and node-flux deviation
+    // of node i+1 for the flux-limiter certification
+    const float dal = d1[A];
+    const unsigned int ok_i = sm.ok[ni], ok_i1 = sm.ok[ni1];
+    float Wf[2][NF];
+    wf_node(ni, Wf[0]);
+    wf_node(ni1, Wf[1]);
+    float dG1[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) dG1[f] = gdev(si + 1, f);
     // alpha1 components of the split high-order flux (Sec. 3.2), evaluated
     // once: the certification below tests the very values the update applies.
     const float ai = hi_i[A], ai1 = hi_i[A] + dal, ui = ref.u[DIR];
@@ -620,61 +735,22 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
       nslow += cnt * (int)slow_flux;
     }
     // Assemble the FP64 split fluxes G^-_{i+1/2}, G^+_{i+1/2} (Sec. 3.2).
-    double Gm[NF], Gp[NF];
-#pragma unroll
-    for (int f = 0; f < NF - 1; ++f) Gm[f] = Gp[f] = sm.G[f * T::NN + ni] + f2d(dGh[f]);
-    Gm[A] = f2d(gmA);
-    Gp[A] = f2d(gpA);
-    if (slow_flux) {
-      // The FP64 limiter of the FP64 path, on FP64 node states and the
-      // FP64 first-order HLLC flux (its positivity is what the limiter
-      // falls back on, so it is not taken from the FP32 deviations).
-      double Wi[NF], Wi1[NF], Fi[NF], Fi1[NF], GH[NF], uH;
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        Wi[f] = sm.W[f * T::NN + ni];
-        Wi1[f] = sm.W[f * T::NN + ni1];
-        Fi[f] = sm.G[f * T::NN + ni];
-        Fi1[f] = sm.G[f * T::NN + ni1];
-      }
-      Fi[A] = Fi1[A] = 0.0;
-      {
-        double vi[NDIM], vi1[NDIM], pi_, pi1, ci_, ci1_;
-        node_thermo64<NDIM>(eos, Wi, vi, pi_, ci_);
-        node_thermo64<NDIM>(eos, Wi1, vi1, pi1, ci1_);
-        hllc<NDIM, DIR, double>(Wi, vi, pi_, Wi[0] + Wi[1], ci_, Wi1, vi1, pi1, Wi1[0] + Wi1[1], ci1_, GH, uH);
-      }
-      double GHm[NF], GHp[NF];
-#pragma unroll
-      for (int f = 0; f < NF; ++f) GHm[f] = GHp[f] = GH[f];
-      GHm[A] = GH[A] - Wi[A] * uH;
-      GHp[A] = GH[A] - Wi1[A] * uH;
-      const double ui64 = (double)hi_i[2 + DIR] + (double)lo_i[2 + DIR];
-      const double uh64 = ui64 + (double)duh;
-      Gm[A] = sm.G[A * T::NN + ni] + (double)dGh[A] - Wi[A] * uh64;
-      Gp[A] = sm.G[A * T::NN + ni] + (double)dGh[A] - Wi1[A] * uh64;
-      bool finite = true;
-#pragma unroll
-      for (int f = 0; f < NF; ++f) finite = finite && isfinite(Gm[f]) && isfinite(Gp[f]);
-      if (finite) {
-        const int fl = flux_limit<NDIM>(eos, tol, Wi, Wi1, Fi, Fi1, GHm, GHp, lam, Gm, Gp);
-        nlim_f += cnt * (fl & 1);
-        nhard_f += cnt * (fl >> 1);
-      } else {
-        // a non-finite high-order flux: the hard switch of Sec. 5.2
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-          Gm[f] = GHm[f];
-          Gp[f] = GHp[f];
-        }
-        nhard_f += cnt;
-      }
-    }
     const int ms = mslot(l, m);
+    if (!slow_flux) {
 #pragma unroll
-    for (int f = 0; f < NF - 1; ++f) sm.F[f * T::NM + ms] = Gm[f];
-    sm.am[ms] = Gm[A];
-    sm.ap[ms] = Gp[A];
+      for (int f = 0; f < NF - 1; ++f) sm.F[f * T::NM + ms] = sm.G[f * T::NN + ni] + f2d(dGh[f]);
+      sm.am[ms] = f2d(gmA);
+      sm.ap[ms] = f2d(gpA);
+    } else {
+      FVec<NF> dgv;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) dgv.v[f] = dGh[f];
+      const double ui64 = (double)hi_i[2 + DIR] + (double)lo_i[2 + DIR];
+      const int fl = mixed_flux_fallback<NDIM, DIR>(eos, tol, sm.W, sm.G, T::NN, ni, ni1, sm.F, sm.am, sm.ap,
+                                                    T::NM, ms, ui64, duh, dgv, lam);
+      nlim_f += cnt * (fl & 1);
+      nhard_f += cnt * (fl >> 1);
+    }
   }
   if (nlim_i) atomicAdd(&a.stats->interp_limited, (unsigned long long)nlim_i);
   if (nhard_i) atomicAdd(&a.stats->interp_hard, (unsigned long long)nhard_i);
