@@ -117,7 +117,9 @@ typedef struct {
  * faces periodic; symmetry needs n >= 3 on that axis.  Launch-grid limits
  * (65535 blocks in grid y and z): in 2D and 3D n[0] <= 524,280 and
  * n[1] <= 131,070; in 3D also n[1], n[2] <= 65,535.  Allocates the
- * handle's device scratch (three states) on the current device.
+ * handle's device scratch on the current device: three states (8 nf bytes
+ * a cell each) and, in 2D and 3D, a 24-byte-per-cell node cache the mixed
+ * precision sweeps of one RHS share.
  * Returns WCNS_E_INVALID_ARG on a bad argument, WCNS_E_CUDA on allocation
  * failure; *out is NULL on error. */
 int wcns_create(const wcns_grid *grid, const wcns_bcs *bcs, double gamma_g, double gamma_l,
@@ -214,12 +216,13 @@ long long wcns_launch_count(const wcns_handle *h);
  * point takes the grid, boundary set, fluids and options directly (no
  * handle) and advances the caller's device array W in place by one step
  * of size dt, exactly like wcns_rk3_step.  Its scratch (two stage states,
- * the RHS accumulator, step control and counters) lives in one
- * file-scope device array of WCNS_NOALLOC_MAX_DOUBLES doubles (64 MiB)
- * that every GPU loading the library holds until the process exits; a
- * problem needs 3 * nf * ncells doubles of it (up to 559,240 cells in 1D,
- * 466,033 in 2D, 399,457 in 3D) and larger ones are rejected with
- * WCNS_E_TOO_LARGE before any GPU work.
+ * the RHS accumulator, the node cache in 2D/3D, step control and counters)
+ * lives in one file-scope device array of WCNS_NOALLOC_MAX_DOUBLES doubles
+ * (64 MiB) that every GPU loading the library holds until the process
+ * exits; a problem needs 3 * nf * ncells doubles of it in 1D and
+ * (3 * nf + 3) * ncells in 2D/3D (up to 559,240 cells in 1D, 399,457 in
+ * 2D, 349,525 in 3D) and larger ones are rejected with WCNS_E_TOO_LARGE
+ * before any GPU work.
  * The first call on a device looks the array's device address up once
  * (cudaGetSymbolAddress with that device current); make that first call
  * before any stream capture.  Every call shares the one array and finds

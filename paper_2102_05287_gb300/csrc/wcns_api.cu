@@ -24,6 +24,11 @@ struct wcns_handle {
   wcns_options opt;
   cudaStream_t stream;
   double *W1, *W2, *L, *Wh;  // stage states, RHS accumulator, host-API state
+  // node cache of the mixed path in 2D/3D (p, 1/rho: FP64; c, certification
+  // bits: 32-bit), one entry per cell, carved from one allocation
+  double *node_p, *node_ir;
+  float *node_c;
+  unsigned int *node_ok;
   double *trace_W1, *trace_W2;  // optional copies of the stage states
   StepCtl *ctl;
   DevStats *stats;
@@ -196,6 +201,18 @@ SweepArgs base_args(wcns_handle *h, int d) {
   a.scheme = h->opt.scheme;
   a.ctl = h->ctl;
   a.stats = h->stats;
+  a.accum_scale = h->inv_dx[d];
+  a.l_unit = 1.0;
+  // mixed path, 2D/3D: the first sweep of an RHS fills the node cache, the
+  // later ones (same stage input) read it
+  if (h->node_p && h->opt.precision == WCNS_MIXED && h->ndim > 1) {
+    a.node_p = h->node_p;
+    a.node_ir = h->node_ir;
+    a.node_c = h->node_c;
+    a.node_ok = h->node_ok;
+    a.node_write = d == 0;
+    a.node_read = d > 0;
+  }
   return a;
 }
 
@@ -260,11 +277,18 @@ int enqueue_step(wcns_handle *h, double *W, double dt_fixed, double cfl) {
       a.W_in = Win;
       a.Wn = W;
       a.L = h->L;
+      // mixed path: L holds the raw x flux difference plus the other
+      // directions' differences scaled by dx_x/dx_d; the combine applies
+      // 1/dx_x (one FP64 multiply per field less in the x sweep)
+      const bool raw = h->opt.precision == WCNS_MIXED && h->ndim > 1;
       if (d < h->ndim - 1) {
         a.epilogue = d == 0 ? EPI_WRITE : EPI_ACCUM;
+        a.l_raw = raw && d == 0;
+        if (raw && d > 0) a.accum_scale = h->inv_dx[d] / h->inv_dx[0];
       } else {
         a.epilogue = EPI_COMBINE;
         a.read_L = h->ndim > 1;
+        a.l_unit = raw ? h->inv_dx[0] : 1.0;
         a.rk_a = ra[s];
         a.rk_b = rb[s];
         a.W_out = Wout;
@@ -439,6 +463,15 @@ int wcns_create(const wcns_grid *g, const wcns_bcs *bcs, double gamma_g, double 
   if (e == cudaSuccess) e = cudaMalloc(&h->W1, bytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->W2, bytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->L, bytes);
+  if (e == cudaSuccess && h->ndim > 1) {
+    // node cache: [p | 1/rho] doubles, then [c | bits] 32-bit words
+    e = cudaMalloc(&h->node_p, (2 * sizeof(double) + 2 * sizeof(float)) * (size_t)N);
+    if (e == cudaSuccess) {
+      h->node_ir = h->node_p + N;
+      h->node_c = (float *)(h->node_ir + N);
+      h->node_ok = (unsigned int *)(h->node_c + N);
+    }
+  }
   if (e == cudaSuccess) e = cudaMalloc(&h->ctl, sizeof(StepCtl));
   if (e == cudaSuccess) e = cudaMalloc(&h->stats, sizeof(DevStats));
   if (e == cudaSuccess) e = cudaMemset(h->stats, 0, sizeof(DevStats));
@@ -701,6 +734,7 @@ void wcns_destroy(wcns_handle *h) {
   cudaFree(h->W1);
   cudaFree(h->W2);
   cudaFree(h->L);
+  cudaFree(h->node_p);
   cudaFree(h->Wh);
   cudaFree(h->ctl);
   cudaFree(h->stats);
@@ -712,7 +746,8 @@ void wcns_destroy(wcns_handle *h) {
 
 // ---------------------------------------------------------------------------
 // Allocation-free SSPRK3 step.  Its scratch is one file-scope device array:
-//   [ W1 | W2 | L ]  (3 * nf * ncells doubles)  followed by  StepCtl, DevStats
+//   [ W1 | W2 | L ]  (3 * nf * ncells doubles), in 2D/3D then the node cache
+//   (3 * ncells doubles), and StepCtl, DevStats
 // in a separate small region.  Host code must not pass the array's name to
 // a kernel (in host code it is a host-side stand-in, not a device address):
 // its device address is looked up once per device with cudaGetSymbolAddress.
@@ -772,7 +807,8 @@ extern "C" int wcns_rk3_step_noalloc(const wcns_grid *g, const wcns_bcs *bcs, do
       return WCNS_E_INVALID_ARG;
   }
   const int nf = g->ndim + 4;
-  if (3ll * nf * N > WCNS_NOALLOC_MAX_DOUBLES) return WCNS_E_TOO_LARGE;
+  // three states, plus the mixed sweeps' node cache in 2D/3D (3 doubles a cell)
+  if ((3ll * nf + (g->ndim > 1 ? 3 : 0)) * N > WCNS_NOALLOC_MAX_DOUBLES) return WCNS_E_TOO_LARGE;
   wcns_options o;
   wcns_default_options(&o);
   if (opt) o = *opt;
@@ -809,6 +845,12 @@ extern "C" int wcns_rk3_step_noalloc(const wcns_grid *g, const wcns_bcs *bcs, do
   h.W1 = states;
   h.W2 = states + M;
   h.L = states + 2 * M;
+  if (h.ndim > 1) {  // node cache, laid out as in wcns_create
+    h.node_p = states + 3 * M;
+    h.node_ir = h.node_p + N;
+    h.node_c = (float *)(h.node_ir + N);
+    h.node_ok = (unsigned int *)(h.node_c + N);
+  }
   // small region: StepCtl | DevStats | uniform Dirichlet states [3][2][7]
   constexpr size_t kStatsOff = ((sizeof(StepCtl) + 15) / 16) * 16;
   constexpr size_t kBcOff = ((kStatsOff + sizeof(DevStats) + 15) / 16) * 16;

@@ -131,6 +131,23 @@ struct SweepArgs {
   double rk_a, rk_b;        // combine coefficients
   int stage;                // 0, 1, 2: lambda from ctl->smax[stage]; the combine
                             // epilogue reduces into ctl->smax[stage + 1]
+  // Mixed path, 2D/3D: node quantities shared by the sweeps of one RHS
+  // evaluation (all sweeps read the same stage input).  The first sweep
+  // stores, for every cell it owns, p and 1/rho (FP64), the FP32 sound
+  // speed and the certification bits; the later sweeps load them for every
+  // node that is a cell or a copy of one (Dirichlet ghosts are computed).
+  double *node_p, *node_ir;
+  float *node_c;
+  unsigned int *node_ok;
+  int node_write, node_read;
+  // Scaling of the L array (mixed path): with l_raw = 1 (inside a step)
+  // the first sweep stores its flux difference without the 1/dx factor,
+  // later sweeps add diff * accum_scale (= inv_dx_d / inv_dx_0) and the
+  // combine multiplies L by l_unit (= inv_dx_0).  Otherwise l_raw = 0,
+  // accum_scale = inv_dx_d and l_unit = 1: L is the right-hand side itself.
+  int l_raw;
+  double accum_scale;
+  double l_unit;
   const double *W_in;       // stage input state
   const double *Wn;         // W^n (combine with rk_a != 0)
   double *W_out;            // combine output

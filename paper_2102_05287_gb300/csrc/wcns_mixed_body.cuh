@@ -353,6 +353,7 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
     double w[NF];
     bool dirichlet = false, flip = false;
     int src = pos;
+    long long idx = 0;  // cell of a non-Dirichlet node
     if (pos < -3 || pos > n + 2) {
       src = min(max(pos, 0), n - 1);
     } else if (pos < 0 || pos >= n) {
@@ -378,24 +379,44 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
         for (int f = 0; f < NF; ++f) w[f] = pos < 0 ? a.dir_lo[f] : a.dir_hi[f];
       }
     } else {
-      const long long idx = ln.base + (long long)src * ln.stride;
+      idx = ln.base + (long long)src * ln.stride;
 #pragma unroll
       for (int f = 0; f < NF; ++f) w[f] = __ldg(a.W_in + (long long)f * N + idx);
       if (flip) w[2 + DIR] = -w[2 + DIR];
     }
-    // Sec. 2 in FP64: p from rho e (the p + p_inf cancellation).
-    const double rho = w[0] + w[1];
-    const double ir = recip_nr(rho);
-    double v[NDIM], m2 = 0.0;
+    // Sec. 2 in FP64: p from rho e (the p + p_inf cancellation).  A later
+    // sweep of the same RHS loads p and 1/rho of the node's cell from the
+    // node cache (a symmetry ghost's mirrored momentum changes neither).
+    bool cached = false;
+    if constexpr (DIR != 0) cached = a.node_read && !dirichlet;
+    double p, ir, v[NDIM];
+    if (cached) {
+      p = a.node_p[idx];
+      ir = a.node_ir[idx];
 #pragma unroll
-    for (int j = 0; j < NDIM; ++j) {
-      v[j] = w[2 + j] * ir;
-      m2 = fma(w[2 + j], v[j], m2);
+      for (int j = 0; j < NDIM; ++j) v[j] = w[2 + j] * ir;
+    } else {
+      const double rho = w[0] + w[1];
+      ir = recip_nr(rho);
+      double m2 = 0.0;
+#pragma unroll
+      for (int j = 0; j < NDIM; ++j) {
+        v[j] = w[2 + j] * ir;
+        m2 = fma(w[2 + j], v[j], m2);
+      }
+      const double rhoe = w[E] - 0.5 * m2;
+      const double Gam = mixGamma(eos, w[A]);
+      const double Pi = mixPi(eos, w[A]);
+      p = (rhoe - Pi) * recip_nr(Gam);
+      if (DIR == 0 && ln.valid && s >= 3 && s < 3 + T::TM - 1 && pos < n) {
+        // rho ctilde^2 = rho e - Pi/(Gamma + 1) > 0, multiplied through by
+        // Gamma + 1 > 0; 0 <= alpha1 <= 1 as an integer compare of the bits
+        const bool adm = nonneg64(w[0]) && nonneg64(w[1]) && nonneg64(w[A]) &&
+                         __double_as_longlong(w[A]) <= 0x3FF0000000000000ll && finite64(rhoe) && finite64(p) &&
+                         rhoe * (Gam + 1.0) - Pi > 0.0;
+        if (!adm) atomicAdd(&a.stats->inadmissible, 1ull);
+      }
     }
-    const double rhoe = w[E] - 0.5 * m2;
-    const double Gam = mixGamma(eos, w[A]);
-    const double Pi = mixPi(eos, w[A]);
-    const double p = (rhoe - Pi) * recip_nr(Gam);
     const double un = v[DIR];
     double g[NF];
     g[0] = w[0] * un;
@@ -423,30 +444,36 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
       sm.Gh[f * T::NN + slot] = gh;
       sm.Gl[f * T::NN + slot] = gl;
     }
-    // FP32 sound speed: rho c^2 = gbar (p + pbar) (Sec. 2)
-    const float a1 = vh[A] + vl[A];
-    const float Gam32 = eos.r2f + eos.drf * a1;
-    const float pb32 = __fdividef(eos.q1f * a1, Gam32 + 1.0f);
-    const float rho32 = vh[0] + vh[1];
-    const float pp = vh[E] + vl[E] + pb32;
-    sm.c[slot] = sqrtf(__fdividef((1.0f + __fdividef(1.0f, Gam32)) * pp, rho32));
-    // Node quantities certified above the limiter tolerances (the first
-    // test of Algorithms 1-3); bit set = certified.  hi is the value
-    // truncated toward zero, so hi >= eps > 0 implies value >= eps.
+    float c32;
     unsigned int okb = 0;
-    if (vh[0] >= epsf_ar) okb |= 1u;
-    if (vh[1] >= epsf_ar) okb |= 2u;
-    if (vh[A] >= epsf_a) okb |= 4u;
-    if (((1.0f - vh[A]) - vl[A]) * (1.0f - 2.4e-7f) >= epsf_a) okb |= 8u;
-    if (Gam32 * pp - margin(Gam32 * (fabsf(vh[E]) + pb32)) * 4.0f >= epsf_rc) okb |= 16u;
+    if (cached) {
+      c32 = a.node_c[idx];
+      okb = a.node_ok[idx];
+    } else {
+      // FP32 sound speed: rho c^2 = gbar (p + pbar) (Sec. 2)
+      const float a1 = vh[A] + vl[A];
+      const float Gam32 = eos.r2f + eos.drf * a1;
+      const float pb32 = __fdividef(eos.q1f * a1, Gam32 + 1.0f);
+      const float rho32 = vh[0] + vh[1];
+      const float pp = vh[E] + vl[E] + pb32;
+      c32 = sqrtf(__fdividef((1.0f + __fdividef(1.0f, Gam32)) * pp, rho32));
+      // Node quantities certified above the limiter tolerances (the first
+      // test of Algorithms 1-3); bit set = certified.  hi is the value
+      // truncated toward zero, so hi >= eps > 0 implies value >= eps.
+      if (vh[0] >= epsf_ar) okb |= 1u;
+      if (vh[1] >= epsf_ar) okb |= 2u;
+      if (vh[A] >= epsf_a) okb |= 4u;
+      if (((1.0f - vh[A]) - vl[A]) * (1.0f - 2.4e-7f) >= epsf_a) okb |= 8u;
+      if (Gam32 * pp - margin(Gam32 * (fabsf(vh[E]) + pb32)) * 4.0f >= epsf_rc) okb |= 16u;
+    }
+    sm.c[slot] = c32;
     sm.ok[slot] = okb;
-    if (DIR == 0 && ln.valid && s >= 3 && s < 3 + T::TM - 1 && pos < n) {
-      // rho ctilde^2 = rho e - Pi/(Gamma + 1) > 0, multiplied through by
-      // Gamma + 1 > 0; 0 <= alpha1 <= 1 as an integer compare of the bits
-      const bool adm = nonneg64(w[0]) && nonneg64(w[1]) && nonneg64(w[A]) &&
-                       __double_as_longlong(w[A]) <= 0x3FF0000000000000ll && finite64(rhoe) && finite64(p) &&
-                       rhoe * (Gam + 1.0) - Pi > 0.0;
-      if (!adm) atomicAdd(&a.stats->inadmissible, 1ull);
+    // the first sweep fills the node cache for the cells its tile owns
+    if (DIR == 0 && a.node_write && ln.valid && s >= 3 && s < 3 + T::TM - 1 && pos < n) {
+      a.node_p[idx] = p;
+      a.node_ir[idx] = ir;
+      a.node_c[idx] = c32;
+      a.node_ok[idx] = okb;
     }
   }
   // block-wide scalars (dt, lambda_d of Sec. 3.3, combine coefficients),
@@ -455,7 +482,7 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
     const double dt0 = geo.dt(), lam0 = geo.lam(), bdt0 = a.rk_b * dt0;
     sm.scal[0] = dt0;
     sm.scal[1] = lam0;
-    sm.scal[2] = bdt0;
+    sm.scal[2] = bdt0 * a.l_unit;  // multiplies the L array (see SweepArgs::l_raw)
     sm.scal[3] = bdt0 * geo.inv_dx();
     reinterpret_cast<float *>(sm.scal + 4)[0] = (float)(2.0 * lam0);
   }
@@ -766,6 +793,8 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
   int done = 0;
   const double idx_ = geo.inv_dx();
   const double bdt = sm.scal[2], bdt_idx = sm.scal[3];
+  // stage 1 of SSPRK3 has b = 1 and a = 0: skip those FP64 operations
+  const bool b_one = a.rk_b == 1.0, has_a = a.rk_a != 0.0;
   for (int q = tid; q < T::TL * (T::TM - 1); q += T::THREADS) {
     const int l = DIR == 0 ? q / (T::TM - 1) : q % T::TL;
     const int m = DIR == 0 ? q % (T::TM - 1) : q / T::TL;
@@ -776,16 +805,18 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
     const long long idx = ln.base + (long long)pos * ln.stride;
     const int ml = mslot(l, m), mr = mslot(l, m + 1);
     if (a.epilogue != EPI_COMBINE) {
-      double upd[NF];
+      double diff[NF];
 #pragma unroll
-      for (int f = 0; f < NF - 1; ++f) upd[f] = (sm.F[f * T::NM + ml] - sm.F[f * T::NM + mr]) * idx_;
-      upd[A] = (sm.ap[ml] - sm.am[mr]) * idx_;
+      for (int f = 0; f < NF - 1; ++f) diff[f] = sm.F[f * T::NM + ml] - sm.F[f * T::NM + mr];
+      diff[A] = sm.ap[ml] - sm.am[mr];
       if (a.epilogue == EPI_WRITE) {
+        // inside a step the raw difference; the combine applies 1/dx
 #pragma unroll
-        for (int f = 0; f < NF; ++f) a.L[(long long)f * N + idx] = upd[f];
+        for (int f = 0; f < NF; ++f) a.L[(long long)f * N + idx] = a.l_raw ? diff[f] : diff[f] * idx_;
       } else {
 #pragma unroll
-        for (int f = 0; f < NF; ++f) a.L[(long long)f * N + idx] += upd[f];
+        for (int f = 0; f < NF; ++f)
+          a.L[(long long)f * N + idx] = fma(diff[f], a.accum_scale, a.L[(long long)f * N + idx]);
       }
     } else {
       const int ns = nslot(l, m + 3);
@@ -795,8 +826,9 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
       for (int f = 0; f < NF; ++f) {
         // a W^n + b W + b dt (L + flux difference / dx) (Sec. 5.3 combine)
         const double diff = f < NF - 1 ? sm.F[f * T::NM + ml] - sm.F[f * T::NM + mr] : sm.ap[ml] - sm.am[mr];
-        double acc = a.rk_b * sm.W[f * T::NN + ns];
-        if (a.rk_a != 0.0) acc = fma(a.rk_a, a.Wn[(long long)f * N + idx], acc);
+        const double wi = sm.W[f * T::NN + ns];
+        double acc = b_one ? wi : a.rk_b * wi;
+        if (has_a) acc = fma(a.rk_a, a.Wn[(long long)f * N + idx], acc);
         if (a.read_L) acc = fma(bdt, a.L[(long long)f * N + idx], acc);
         w[f] = fma(bdt_idx, diff, acc);
         finite = finite && finite64(w[f]);

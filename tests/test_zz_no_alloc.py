@@ -75,10 +75,14 @@ def test_noalloc_rejects_problems_beyond_its_scratch():
     lib = wcns.load()
     g = wcns.wcns_grid()
     g.ndim = 2
-    g.n[0], g.n[1] = 2048, 1024  # 3 * 6 * 2M doubles > 8M
+    g.n[0], g.n[1] = 2048, 1024  # (3 * 6 + 3) * 2M doubles > 8M
     g.lo[0], g.lo[1], g.hi[0], g.hi[1] = 0.0, 0.0, 2.0, 1.0
     b = wcns.wcns_bcs()
     W = torch.zeros(6, 1024, 2048, dtype=torch.float64, device="cuda")
     st = lib.wcns_rk3_step_noalloc(C.byref(g), C.byref(b), 1.4, 4.4, 6e8, None, C.c_void_p(W.data_ptr()), 1e-7)
     assert st == wcns.WCNS_E_TOO_LARGE
     assert "too large" in lib.wcns_strerror(st).decode()
+    # just above the 2D limit of 399,457 cells (21 doubles a cell)
+    g.n[0], g.n[1] = 800, 500
+    st = lib.wcns_rk3_step_noalloc(C.byref(g), C.byref(b), 1.4, 4.4, 6e8, None, C.c_void_p(W.data_ptr()), 1e-7)
+    assert st == wcns.WCNS_E_TOO_LARGE
