@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(T::THREADS, MIXED ? BATCH_MIXED_WARPS * 32 / T
   extern __shared__ double smem_raw[];
   for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
     if constexpr (MIXED)
-      sweep_body_mixed<1, 0, T>(a, BatchGeo<T>(b, t), smem_raw);
+      sweep_body_mixed<1, 0, T, false>(a, BatchGeo<T>(b, t), smem_raw);
     else
       sweep_body<1, 0, double, T>(a, BatchGeo<T>(b, t), smem_raw);
     __syncthreads();

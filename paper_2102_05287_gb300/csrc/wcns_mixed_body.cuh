@@ -20,6 +20,8 @@
 //     nothing else is needed.  Otherwise the FP64 limiter code runs on FP64
 //     states rebuilt from the same deviations.
 #pragma once
+#include <type_traits>
+
 #include "wcns_sweep.cuh"
 
 namespace wcns {
@@ -117,10 +119,12 @@ struct SmemMixed {
   static constexpr size_t NODE_BYTES = 8 * 2 * NF + 4 * 4 * NF + 4 + 4;
   static constexpr size_t MID_BYTES = 8 * (NF + 1);
   // + per-block scalars: dt, lambda, b dt, b dt / dx, 2 lambda (FP32)
-  static constexpr size_t BYTES = NODE_BYTES * T::NN + MID_BYTES * T::NM + 5 * 8;
+  // + the list of midpoints deferred to the FP64 fallback pass and its length
+  static constexpr size_t BYTES = NODE_BYTES * T::NN + MID_BYTES * T::NM + 5 * 8 + 4 * T::NM + 16;
   double *W, *G, *F, *am, *ap, *scal;
   float *Vh, *Vl, *Gh, *Gl, *c;
-  unsigned int *ok;
+  unsigned int *ok, *nslow;
+  int *slow;
   __device__ SmemMixed(double *base) {
     W = base;
     G = W + NF * T::NN;
@@ -134,6 +138,8 @@ struct SmemMixed {
     c = Gl + NF * T::NN;
     ok = (unsigned int *)(c + T::NN);
     scal = (double *)(ok + T::NN);  // c and ok together take 8 NN bytes: 8-byte aligned
+    slow = (int *)(scal + 5);
+    nslow = (unsigned int *)(slow + T::NM);
   }
 };
 
@@ -327,7 +333,11 @@ __device__ __noinline__ int mixed_flux_fallback(const EosConst eos, const LimTol
   return fl;
 }
 
-template <int NDIM, int DIR, class T, class Geo>
+// DEFER: midpoints whose FP32 certification fails are collected and
+// computed in a second pass with the FP64 fallbacks (the grid sweeps);
+// otherwise every midpoint runs the full code in one pass (the batched 1D
+// kernels, whose persistent 64-thread tiles were measured faster that way).
+template <int NDIM, int DIR, class T, bool DEFER = true, class Geo>
 __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &geo, double *smem_raw) {
   using R = float;
   using S = SmemMixed<NDIM, T>;
@@ -485,6 +495,7 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
     sm.scal[2] = bdt0 * a.l_unit;  // multiplies the L array (see SweepArgs::l_raw)
     sm.scal[3] = bdt0 * geo.inv_dx();
     reinterpret_cast<float *>(sm.scal + 4)[0] = (float)(2.0 * lam0);
+    *sm.nslow = 0u;
   }
   __syncthreads();
 
@@ -495,7 +506,13 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
 
   // ---- 3: midpoint fluxes ---------------------------------------------------
   int nlim_i = 0, nhard_i = 0, nlim_f = 0, nhard_f = 0, nslow = 0;
-  for (int q = tid; q < T::NM; q += T::THREADS) {
+  // One midpoint.  The fast instance (SLOW false) certifies both limiters
+  // in FP32 and, where a certification fails, returns false without
+  // writing anything; the slow instance computes those midpoints with the
+  // FP64 limiter fallbacks.  Two instances keep the fallbacks' registers
+  // out of the fast loop's allocation.
+  auto midpoint = [&](const int q, auto slow_tag) -> bool {
+    constexpr bool SLOW = decltype(slow_tag)::value;
     const int l = DIR == 0 ? q / T::TM : q % T::TL;
     const int m = DIR == 0 ? q % T::TM : q / T::TL;
     const int si = m + 2;
@@ -557,8 +574,6 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
     float dGh[NF], duh;  // high-order G^ - G_i and u^ - u_i
     bool slow_flux = false;
     if (a.scheme != SCHEME_HLLC1) {
-      float d1[NF];  // node i+1
-      dev(si + 1, d1);
       const unsigned int ok_i = sm.ok[ni], ok_i1 = sm.ok[ni1];
       // Steps 1-2: projection with means of nodes i, i+1 (App. A).
       const float ar1 = 0.5f * (hi_i[0] + sm.Vh[0 * T::NN + ni1]);
@@ -567,35 +582,55 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
       const float cb = 0.5f * (ci + ci1);
       const float irc = __fdividef(1.0f, rb * cb);
       const float k1 = ar1 * irc / cb, k2 = ar2 * irc / cb;
-      float U[6][NF];
+      // Steps 2-3 field by field: the projected deviations of two
+      // characteristic fields at a time (stencil nodes j = 0..5 are
+      // i-2..i+3; node i itself, j = 2, has zero deviation and enters
+      // neither stencil of the deviation form) and their left / right
+      // WCNS-IS interpolations (Sec. 4.3), so that only two fields'
+      // stencils are held in registers at once.
+      auto devc = [&](int j, int c) {
+        const int sl = nslot(l, m + j);
+        return (sm.Vh[c * T::NN + sl] - hi_i[c]) + (sm.Vl[c * T::NN + sl] - lo_i[c]);
+      };
+      float UL[NF], UR[NF];
+      float dp[6];  // pressure deviations, shared by the three fields that involve p
 #pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        float dv[NF];
-        if (j == 2) {
+      for (int j = 0; j < 6; ++j) dp[j] = j == 2 ? 0.0f : devc(j, E);
+      {
+        float a[6], b[6];
+        // acoustic fields: 0 = (u_n - c), NF-1 = (u_n + c)
 #pragma unroll
-          for (int f = 0; f < NF; ++f) dv[f] = 0.0f;
-        } else if (j == 3) {
-#pragma unroll
-          for (int f = 0; f < NF; ++f) dv[f] = d1[f];
-        } else {
-          dev(m + j, dv);
+        for (int j = 0; j < 6; ++j) {
+          const float du = j == 2 ? 0.0f : devc(j, 2 + DIR);
+          a[j] = du - irc * dp[j];
+          b[j] = du + irc * dp[j];
         }
-        U[j][0] = dv[2 + DIR] - irc * dv[E];
-        U[j][1] = dv[0] - k1 * dv[E];
-        U[j][2] = dv[1] - k2 * dv[E];
+        UL[0] = wenois_c0<R>(a[0], a[1], a[3], a[4], epsR);
+        UR[0] = wenois_p0<R>(a[5], a[4], a[3], a[1], epsR);
+        UL[NF - 1] = wenois_c0<R>(b[0], b[1], b[3], b[4], epsR);
+        UR[NF - 1] = wenois_p0<R>(b[5], b[4], b[3], b[1], epsR);
+        // entropy / partial-density fields 1 and 2
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+          a[j] = (j == 2 ? 0.0f : devc(j, 0)) - k1 * dp[j];
+          b[j] = (j == 2 ? 0.0f : devc(j, 1)) - k2 * dp[j];
+        }
+        UL[1] = wenois_c0<R>(a[0], a[1], a[3], a[4], epsR);
+        UR[1] = wenois_p0<R>(a[5], a[4], a[3], a[1], epsR);
+        UL[2] = wenois_c0<R>(b[0], b[1], b[3], b[4], epsR);
+        UR[2] = wenois_p0<R>(b[5], b[4], b[3], b[1], epsR);
+        // tangential velocities and alpha1: plain deviations
         int row = 3;
 #pragma unroll
-        for (int k = 0; k < NDIM; ++k)
-          if (k != DIR) U[j][row++] = dv[2 + k];
-        U[j][NF - 2] = dv[A];
-        U[j][NF - 1] = dv[2 + DIR] + irc * dv[E];
-      }
-      // Step 3: WCNS-IS (Sec. 4.3) on deviations.
-      float UL[NF], UR[NF];
+        for (int k = 0; k <= NDIM; ++k) {
+          if (k == DIR) continue;
+          const int c = k < NDIM ? 2 + k : A;
+          const int f = k < NDIM ? row++ : NF - 2;
 #pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        UL[f] = wenois_c0<R>(U[0][f], U[1][f], U[3][f], U[4][f], epsR);
-        UR[f] = wenois_p0<R>(U[5][f], U[4][f], U[3][f], U[1][f], epsR);
+          for (int j = 0; j < 6; ++j) a[j] = j == 2 ? 0.0f : devc(j, c);
+          UL[f] = wenois_c0<R>(a[0], a[1], a[3], a[4], epsR);
+          UR[f] = wenois_p0<R>(a[5], a[4], a[3], a[1], epsR);
+        }
       }
       // Step 4: back-projection to primitive deviations.
       float dV[2][NF];
@@ -652,6 +687,7 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
                    Gam * (pt + pb) - margin(Gam * (fabsf(hi_i[E]) + fabsf(d[E]) + pb)) * 4.0f >= epsf_rc;
           }
           if (cert) continue;
+          if constexpr (!SLOW) return false;
           nslow += cnt;
           FVec<NF> hv, lv, dv;
 #pragma unroll
@@ -683,7 +719,7 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
           const int sl = nslot(l, s);
           return (sm.Vh[(2 + DIR) * T::NN + sl] - hi_i[2 + DIR]) + (sm.Vl[(2 + DIR) * T::NN + sl] - lo_i[2 + DIR]);
         };
-        duh = hcs<R>(ut - ref.u[DIR] - lo_i[2 + DIR], udev(m), udev(m + 1), 0.0f, d1[2 + DIR], udev(m + 4),
+        duh = hcs<R>(ut - ref.u[DIR] - lo_i[2 + DIR], udev(m), udev(m + 1), 0.0f, udev(m + 3), udev(m + 4),
                      udev(m + 5));
       }
     }
@@ -724,8 +760,9 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
     // node-flux deviations and of G_i + dG in FP64.
     if (a.scheme == SCHEME_PP) {
       bool cert = ok_i == ALL && ok_i1 == ALL;
-#pragma unroll 1
-      for (int st = 0; st < 4 && cert; ++st) {
+#pragma unroll
+      for (int st = 0; st < 4; ++st) {
+        if (!cert) break;
         // st: 0 = W_i^{HLLC,+}, 1 = W_{i+1}^{HLLC,-}, 2 = W_i^{+}, 3 = W_{i+1}^{-}
         const bool hl = st < 2;
         const bool right = st & 1;
@@ -759,6 +796,9 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
                rct2_certified<NDIM>(eos, x, mag, epsf_rc);
       }
       slow_flux = !cert;
+      if constexpr (!SLOW) {
+        if (slow_flux) return false;
+      }
       nslow += cnt * (int)slow_flux;
     }
     // Assemble the FP64 split fluxes G^-_{i+1/2}, G^+_{i+1/2} (Sec. 3.2).
@@ -778,6 +818,16 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
       nlim_f += cnt * (fl & 1);
       nhard_f += cnt * (fl >> 1);
     }
+    return true;
+  };
+  if constexpr (DEFER) {
+    for (int q = tid; q < T::NM; q += T::THREADS)
+      if (!midpoint(q, std::false_type{})) sm.slow[atomicAdd(sm.nslow, 1u)] = q;
+    __syncthreads();
+    const int nsl = (int)*sm.nslow;
+    for (int k = tid; k < nsl; k += T::THREADS) midpoint(sm.slow[k], std::true_type{});
+  } else {
+    for (int q = tid; q < T::NM; q += T::THREADS) midpoint(q, std::true_type{});
   }
   if (nlim_i) atomicAdd(&a.stats->interp_limited, (unsigned long long)nlim_i);
   if (nhard_i) atomicAdd(&a.stats->interp_hard, (unsigned long long)nhard_i);
