@@ -384,9 +384,12 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
       if (face) {
 #pragma unroll
         for (int f = 0; f < NF; ++f) w[f] = __ldg(face + (long long)f * a.face_n + ln.face);
+      } else if (pos < 0) {  // two direct loops: a selected pointer into the
+#pragma unroll                     // parameter arrays would copy them to local memory
+        for (int f = 0; f < NF; ++f) w[f] = a.dir_lo[f];
       } else {
 #pragma unroll
-        for (int f = 0; f < NF; ++f) w[f] = pos < 0 ? a.dir_lo[f] : a.dir_hi[f];
+        for (int f = 0; f < NF; ++f) w[f] = a.dir_hi[f];
       }
     } else {
       idx = ln.base + (long long)src * ln.stride;

@@ -32,6 +32,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "wcns_internal.h"
 
 namespace wcns {
@@ -219,6 +221,68 @@ __device__ __forceinline__ R wenois_p0(R um2, R um1, R u0, R up2, R eps) {
   return wenois_tail<R>(s0, s1, s2, s3, u0 * u0, e1 * e1, b01, b2, b3, tau, eps);
 }
 
+// FP64 forms of the two deviation-form stencils with every smoothness
+// indicator, tau5 and eps scaled by 4: the weights depend only on ratios
+// of these quantities and on products with equal numbers of them, so they
+// are unchanged in exact arithmetic, and 4 beta = (13/3) a^2 + c^2 takes
+// the eps addition into an FMA.  e4 = 4 eps.
+__device__ __forceinline__ double beta3x4(double a, double c, double e4) {
+  return fma((13.0 / 3.0) * a, a, fma(c, c, e4));
+}
+
+// IS weights and interpolated value from the scaled indicators (eps
+// already included): one division, as wenois_tail<double>.
+__device__ __forceinline__ double wenois_tail_x4(double s0, double s1, double s2, double s3, double b0, double b1,
+                                                 double b01, double b2, double b3, double tau) {
+  const double t2 = tau * tau;
+  const double p23 = b2 * b3, p01b = (b0 * b1) * b01;
+  const double w0 = (15.0 / 32.0) * (b0 * b01 + t2) * (b1 * p23);
+  const double w1 = (5.0 / 32.0) * (b1 * b01 + t2) * (b0 * p23);
+  const double w2 = (5.0 / 16.0) * (b2 + tau) * (p01b * b3);
+  const double w3 = (1.0 / 16.0) * (b3 + tau) * (p01b * b2);
+  const double sum = (w0 + w1) + (w2 + w3);
+  // 1e-280 < sum < 1e280, as integer compares (sum is a sum of products of non-negative terms)
+  const long long sb = __double_as_longlong(sum);
+  if (sb > __double_as_longlong(1e-280) && sb < __double_as_longlong(1e280))
+    return (w0 * s0 + w1 * s1 + w2 * s2 + w3 * s3) / sum;
+  const double r01 = tau / b01;
+  const double v0 = (15.0 / 32.0) * (1.0 + (tau / b0) * r01);
+  const double v1 = (5.0 / 32.0) * (1.0 + (tau / b1) * r01);
+  const double v2 = (5.0 / 16.0) * (1.0 + tau / b2);
+  const double v3 = (1.0 / 16.0) * (1.0 + tau / b3);
+  return (v0 * s0 + v1 * s1 + v2 * s2 + v3 * s3) / ((v0 + v1) + (v2 + v3));
+}
+
+// u0 = 0: as wenois_c0, indicators scaled by 4
+__device__ __forceinline__ double wenois_c0_x4(double um2, double um1, double up1, double up2, double e4) {
+  const double s0 = 0.5 * up1;
+  const double s1 = -0.5 * um1;
+  const double s2 = 0.75 * up1 - 0.125 * up2;
+  const double s3 = 0.375 * um2 - 1.25 * um1;
+  const double a01 = um1 + up1, c01 = um1 - up1;
+  const double b01 = beta3x4(a01, c01, e4);
+  const double b2 = beta3x4(up2 - 2.0 * up1, up2 - 4.0 * up1, e4);
+  const double b3 = beta3x4(um2 - 2.0 * um1, um2 - 4.0 * um1, e4);
+  const double ta = (um2 + up2) - 4.0 * a01, tc = (up2 - um2) + 2.0 * c01;
+  const double tau = fma((13.0 / 3.0) * ta, ta, tc * tc);
+  return wenois_tail_x4(s0, s1, s2, s3, fma(4.0 * up1, up1, e4), fma(4.0 * um1, um1, e4), b01, b2, b3, tau);
+}
+
+// up1 = 0: as wenois_p0, indicators scaled by 4
+__device__ __forceinline__ double wenois_p0_x4(double um2, double um1, double u0, double up2, double e4) {
+  const double s0 = 0.5 * u0;
+  const double s1 = 0.5 * (3.0 * u0 - um1);
+  const double s2 = 0.125 * (3.0 * u0 - up2);
+  const double s3 = 0.125 * (3.0 * um2 - 10.0 * um1 + 15.0 * u0);
+  const double e1 = um1 - u0;
+  const double b01 = beta3x4(um1 - 2.0 * u0, um1, e4);
+  const double b2 = beta3x4(u0 + up2, 3.0 * u0 + up2, e4);
+  const double b3 = beta3x4(um2 - 2.0 * um1 + u0, um2 - 4.0 * um1 + 3.0 * u0, e4);
+  const double ta = (um2 + up2) + 6.0 * u0 - 4.0 * um1, tc = (up2 - um2) + 2.0 * um1;
+  const double tau = fma((13.0 / 3.0) * ta, ta, tc * tc);
+  return wenois_tail_x4(s0, s1, s2, s3, fma(4.0 * u0, u0, e4), fma(4.0 * e1, e1, e4), b01, b2, b3, tau);
+}
+
 // ---------------------------------------------------------------------------
 // Sec. 3.1-3.2: HLLC flux in direction DIR from two states given by their
 // conservative vector, velocity, pressure, density and sound speed.
@@ -326,13 +390,12 @@ __device__ __forceinline__ void hllc_dev(const RefNode<NDIM, R> &ref, const EosC
   const R mL = rho[0] * (sL - un[0]), mR = rho[1] * (sR - un[1]);
   const R ss = Prec<R>::div(pdev[1] - pdev[0] + mL * un[0] - mR * un[1], mL - mR);
   sstar = ss;
-  R Gs[2][NF];
-  const bool need[2] = {!(ss < R(0)), !(ss > R(0))};
   const R rdiff = (R)eos.drf, q1 = (R)eos.q1f;
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    if (!need[k]) continue;
-    const R *d = dv[k];
+  // One side's flux deviation F_K - G(ref) + s_(-/+) (W*_K - W_K) into Gk;
+  // the side is a compile-time constant, so no array is indexed at run time.
+  auto side_flux = [&](auto kc, R *Gk) {
+    constexpr int k = decltype(kc)::value;
+    const R *d = k ? dR : dL;
     const R u = un[k];
     const R sK = k ? sR : sL;
     const R sw = k ? fmax(R(0), sR) : fmin(R(0), sL);
@@ -350,8 +413,8 @@ __device__ __forceinline__ void hllc_dev(const RefNode<NDIM, R> &ref, const EosC
     const R dE = d[E] * GammaK + (ref.p * rdiff + q1) * d[A] + R(0.5) * (drho * uk2 + ref.rho * du2);
     const R EpK = ref.Ep + dE + d[E];  // (E + p)_K
     // physical-flux deviations
-    Gs[k][0] = d[0] * u + ref.r1 * d[2 + DIR] + sw * (chim1 * a1r1[k]);
-    Gs[k][1] = d[1] * u + ref.r2 * d[2 + DIR] + sw * (chim1 * a2r2[k]);
+    Gk[0] = d[0] * u + ref.r1 * d[2 + DIR] + sw * (chim1 * a1r1[k]);
+    Gk[1] = d[1] * u + ref.r2 * d[2 + DIR] + sw * (chim1 * a2r2[k]);
 #pragma unroll
     for (int j = 0; j < NDIM; ++j) {
       R dF;
@@ -360,19 +423,23 @@ __device__ __forceinline__ void hllc_dev(const RefNode<NDIM, R> &ref, const EosC
       else
         dF = drho * uK[j] * u + ref.rho * (d[2 + j] * u + ref.u[j] * d[2 + DIR]);
       const R dm = (j == DIR) ? rho[k] * sK * chim1 : chim1 * (rho[k] * uK[j]);
-      Gs[k][2 + j] = dF + sw * dm;
+      Gk[2 + j] = dF + sw * dm;
     }
     const R dEstar = chim1 * EpK + (R(1) + chim1) * rho[k] * ss * (ss - u);
-    Gs[k][E] = (dE + d[E]) * u + ref.Ep * d[2 + DIR] + sw * dEstar;
-    Gs[k][A] = al[k] * ss - ref.a1 * ref.u[DIR];
-  }
-  if (need[0] && need[1]) {
+    Gk[E] = (dE + d[E]) * u + ref.Ep * d[2 + DIR] + sw * dEstar;
+    Gk[A] = al[k] * ss - ref.a1 * ref.u[DIR];
+  };
+  const bool needL = !(ss < R(0)), needR = !(ss > R(0));
+  if (needL && needR) {  // s* = 0: the mean of both sides
+    R GL[NF], GR[NF];
+    side_flux(std::integral_constant<int, 0>{}, GL);
+    side_flux(std::integral_constant<int, 1>{}, GR);
 #pragma unroll
-    for (int q = 0; q < NF; ++q) dG[q] = R(0.5) * (Gs[0][q] + Gs[1][q]);
+    for (int q = 0; q < NF; ++q) dG[q] = R(0.5) * (GL[q] + GR[q]);
+  } else if (needL) {
+    side_flux(std::integral_constant<int, 0>{}, dG);
   } else {
-    const int k = need[0] ? 0 : 1;
-#pragma unroll
-    for (int q = 0; q < NF; ++q) dG[q] = Gs[k][q];
+    side_flux(std::integral_constant<int, 1>{}, dG);
   }
 }
 
@@ -697,9 +764,12 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
       if (face) {
 #pragma unroll
         for (int f = 0; f < NF; ++f) w[f] = __ldg(face + (long long)f * a.face_n + ln.face);
+      } else if (pos < 0) {  // two direct loops: a selected pointer into the
+#pragma unroll                     // parameter arrays would copy them to local memory
+        for (int f = 0; f < NF; ++f) w[f] = a.dir_lo[f];
       } else {
 #pragma unroll
-        for (int f = 0; f < NF; ++f) w[f] = pos < 0 ? a.dir_lo[f] : a.dir_hi[f];
+        for (int f = 0; f < NF; ++f) w[f] = a.dir_hi[f];
       }
     } else {
       const long long idx = ln.base + (long long)src * ln.stride;
@@ -753,7 +823,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
 
   const double dt = geo.dt();
   const double lam = geo.lam();
-  const double epsR = a.eps_is;
+  const double eps4 = 4.0 * a.eps_is;  // IS epsilon for the indicators scaled by 4
 
   // ---- 3: midpoint fluxes ---------------------------------------------------
   int nlim_i = 0, nhard_i = 0, nlim_f = 0, nhard_f = 0;
@@ -837,8 +907,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
       double UL[NF], UR[NF];
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
-        UL[f] = wenois_c0<double>(U[0][f], U[1][f], U[3][f], U[4][f], epsR);
-        UR[f] = wenois_p0<double>(U[5][f], U[4][f], U[3][f], U[1][f], epsR);
+        UL[f] = wenois_c0_x4(U[0][f], U[1][f], U[3][f], U[4][f], eps4);
+        UR[f] = wenois_p0_x4(U[5][f], U[4][f], U[3][f], U[1][f], eps4);
       }
       // Steps 4-5: back-project, add node i, V -> W.
       double WL[NF], WR[NF], VL[NF], VR[NF];  // V: (a1r1, a2r2, vel.., p, a1)
