@@ -823,12 +823,22 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
     }
     return true;
   };
+  bool barrier_done = false;
   if constexpr (DEFER) {
+    int deferred = 0;
     for (int q = tid; q < T::NM; q += T::THREADS)
-      if (!midpoint(q, std::false_type{})) sm.slow[atomicAdd(sm.nslow, 1u)] = q;
-    __syncthreads();
-    const int nsl = (int)*sm.nslow;
-    for (int k = tid; k < nsl; k += T::THREADS) midpoint(sm.slow[k], std::true_type{});
+      if (!midpoint(q, std::false_type{})) {
+        sm.slow[atomicAdd(sm.nslow, 1u)] = q;
+        deferred = 1;
+      }
+    // one barrier when nothing was deferred (it also orders the flux
+    // stores before the cell update); the second pass only when needed
+    if (__syncthreads_or(deferred)) {
+      const int nsl = (int)*sm.nslow;
+      for (int k = tid; k < nsl; k += T::THREADS) midpoint(sm.slow[k], std::true_type{});
+    } else {
+      barrier_done = true;
+    }
   } else {
     for (int q = tid; q < T::NM; q += T::THREADS) midpoint(q, std::true_type{});
   }
@@ -837,7 +847,7 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
   if (nlim_f) atomicAdd(&a.stats->flux_limited, (unsigned long long)nlim_f);
   if (nhard_f) atomicAdd(&a.stats->flux_hard, (unsigned long long)nhard_f);
   if (nslow) atomicAdd(&a.stats->fp64_fallbacks, (unsigned long long)nslow);
-  __syncthreads();
+  if (!barrier_done) __syncthreads();
 
   // ---- 4: cell update (FP64) -------------------------------------------------
   float smax_local[NDIM];

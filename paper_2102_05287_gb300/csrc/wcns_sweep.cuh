@@ -231,33 +231,39 @@ __device__ __forceinline__ double beta3x4(double a, double c, double e4) {
 }
 
 // IS weights and interpolated value from the scaled indicators (eps
-// already included): one division, as wenois_tail<double>.
-__device__ __forceinline__ double wenois_tail_x4(double s0, double s1, double s2, double s3, double b0, double b1,
-                                                 double b01, double b2, double b3, double tau) {
+// already included), one division.  With the linear weights
+// d = (15, 5, 10, 2)/32 and D = b0 b1 b01 b2 b3, the scaled weights
+// eta_k D / (5/32) factor as
+//   (b2 b3) [3 (b0 b01 + tau^2) b1 | (b1 b01 + tau^2) b0]   for k = 0, 1,
+//   (b0 b1 b01) [2 (b2 + tau) b3 | 0.4 (b3 + tau) b2]       for k = 2, 3;
+// the factors 3 and 2 are carried by the sub-stencil values: s0x3 = 3 s0,
+// s2x2 = 2 s2 (the callers form them at no extra cost).
+__device__ __forceinline__ double wenois_tail_x4(double s0x3, double s1, double s2x2, double s3, double b0,
+                                                 double b1, double b01, double b2, double b3, double tau) {
   const double t2 = tau * tau;
-  const double p23 = b2 * b3, p01b = (b0 * b1) * b01;
-  const double w0 = (15.0 / 32.0) * (b0 * b01 + t2) * (b1 * p23);
-  const double w1 = (5.0 / 32.0) * (b1 * b01 + t2) * (b0 * p23);
-  const double w2 = (5.0 / 16.0) * (b2 + tau) * (p01b * b3);
-  const double w3 = (1.0 / 16.0) * (b3 + tau) * (p01b * b2);
-  const double sum = (w0 + w1) + (w2 + w3);
-  // 1e-280 < sum < 1e280, as integer compares (sum is a sum of products of non-negative terms)
-  const long long sb = __double_as_longlong(sum);
-  if (sb > __double_as_longlong(1e-280) && sb < __double_as_longlong(1e280))
-    return (w0 * s0 + w1 * s1 + w2 * s2 + w3 * s3) / sum;
+  const double Q = b2 * b3, Pb = (b0 * b1) * b01;
+  const double A0 = fma(b0, b01, t2) * b1;  // weight 0 / 3
+  const double A1 = fma(b1, b01, t2) * b0;  // weight 1
+  const double B2 = (b2 + tau) * b3;        // weight 2 / 2
+  const double B3 = 0.4 * (b3 + tau) * b2;  // weight 3
+  const double num = fma(Q, fma(A0, s0x3, A1 * s1), Pb * fma(B2, s2x2, B3 * s3));
+  const double den = fma(Q, fma(3.0, A0, A1), Pb * fma(2.0, B2, B3));
+  // 1e-280 < den < 1e280, as integer compares (den is a sum of products of non-negative terms)
+  const long long db = __double_as_longlong(den);
+  if (db > __double_as_longlong(1e-280) && db < __double_as_longlong(1e280)) return num / den;
+  // outside that range: the weights from the ratios tau / b, as printed
   const double r01 = tau / b01;
-  const double v0 = (15.0 / 32.0) * (1.0 + (tau / b0) * r01);
-  const double v1 = (5.0 / 32.0) * (1.0 + (tau / b1) * r01);
-  const double v2 = (5.0 / 16.0) * (1.0 + tau / b2);
-  const double v3 = (1.0 / 16.0) * (1.0 + tau / b3);
-  return (v0 * s0 + v1 * s1 + v2 * s2 + v3 * s3) / ((v0 + v1) + (v2 + v3));
+  const double v0 = 1.0 + (tau / b0) * r01, v1 = 1.0 + (tau / b1) * r01;
+  const double v2 = 1.0 + tau / b2, v3 = 1.0 + tau / b3;
+  return ((5.0 / 32.0) * (v0 * s0x3 + v1 * s1 + v2 * s2x2) + (1.0 / 16.0) * v3 * s3) /
+         ((15.0 / 32.0) * v0 + (5.0 / 32.0) * v1 + (5.0 / 16.0) * v2 + (1.0 / 16.0) * v3);
 }
 
 // u0 = 0: as wenois_c0, indicators scaled by 4
 __device__ __forceinline__ double wenois_c0_x4(double um2, double um1, double up1, double up2, double e4) {
-  const double s0 = 0.5 * up1;
+  const double s0x3 = 1.5 * up1;                  // 3 s0
   const double s1 = -0.5 * um1;
-  const double s2 = 0.75 * up1 - 0.125 * up2;
+  const double s2x2 = 1.5 * up1 - 0.25 * up2;     // 2 s2
   const double s3 = 0.375 * um2 - 1.25 * um1;
   const double a01 = um1 + up1, c01 = um1 - up1;
   const double b01 = beta3x4(a01, c01, e4);
@@ -265,14 +271,14 @@ __device__ __forceinline__ double wenois_c0_x4(double um2, double um1, double up
   const double b3 = beta3x4(um2 - 2.0 * um1, um2 - 4.0 * um1, e4);
   const double ta = (um2 + up2) - 4.0 * a01, tc = (up2 - um2) + 2.0 * c01;
   const double tau = fma((13.0 / 3.0) * ta, ta, tc * tc);
-  return wenois_tail_x4(s0, s1, s2, s3, fma(4.0 * up1, up1, e4), fma(4.0 * um1, um1, e4), b01, b2, b3, tau);
+  return wenois_tail_x4(s0x3, s1, s2x2, s3, fma(4.0 * up1, up1, e4), fma(4.0 * um1, um1, e4), b01, b2, b3, tau);
 }
 
 // up1 = 0: as wenois_p0, indicators scaled by 4
 __device__ __forceinline__ double wenois_p0_x4(double um2, double um1, double u0, double up2, double e4) {
-  const double s0 = 0.5 * u0;
+  const double s0x3 = 1.5 * u0;                   // 3 s0
   const double s1 = 0.5 * (3.0 * u0 - um1);
-  const double s2 = 0.125 * (3.0 * u0 - up2);
+  const double s2x2 = 0.25 * (3.0 * u0 - up2);    // 2 s2
   const double s3 = 0.125 * (3.0 * um2 - 10.0 * um1 + 15.0 * u0);
   const double e1 = um1 - u0;
   const double b01 = beta3x4(um1 - 2.0 * u0, um1, e4);
@@ -280,7 +286,7 @@ __device__ __forceinline__ double wenois_p0_x4(double um2, double um1, double u0
   const double b3 = beta3x4(um2 - 2.0 * um1 + u0, um2 - 4.0 * um1 + 3.0 * u0, e4);
   const double ta = (um2 + up2) + 6.0 * u0 - 4.0 * um1, tc = (up2 - um2) + 2.0 * um1;
   const double tau = fma((13.0 / 3.0) * ta, ta, tc * tc);
-  return wenois_tail_x4(s0, s1, s2, s3, fma(4.0 * u0, u0, e4), fma(4.0 * e1, e1, e4), b01, b2, b3, tau);
+  return wenois_tail_x4(s0x3, s1, s2x2, s3, fma(4.0 * u0, u0, e4), fma(4.0 * e1, e1, e4), b01, b2, b3, tau);
 }
 
 // ---------------------------------------------------------------------------
