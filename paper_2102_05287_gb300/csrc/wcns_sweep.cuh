@@ -1102,8 +1102,12 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
   if ((tid & 31) == 0 && midpoints_done) atomicAdd(&a.stats->midpoints, (unsigned long long)midpoints_done);
 }
 
+// Resident blocks per SM the FP64 register allocation targets.
+#ifndef FP64_MIN_BLOCKS
+#define FP64_MIN_BLOCKS 1
+#endif
 template <int NDIM, int DIR, class R>
-__global__ void __launch_bounds__(Tile<NDIM, DIR>::THREADS, 1) sweep_kernel(const SweepArgs a) {
+__global__ void __launch_bounds__(Tile<NDIM, DIR>::THREADS, FP64_MIN_BLOCKS) sweep_kernel(const SweepArgs a) {
   extern __shared__ double smem_raw[];
   if (!a.ctl->active) return;  // a finished advance: the step is a no-op
   using T = Tile<NDIM, DIR>;
