@@ -26,14 +26,17 @@
 
 namespace wcns {
 
-// Resident blocks per SM the register allocation targets (256 threads a
-// block): 3 in 2D (85 registers; three 2D tiles fit in shared memory), 2 in
-// 3D (the 3D tiles need 78-85 KB); the 1D tiles have 128 threads.
+// Resident blocks per SM the register allocation targets: 3 in 2D (256
+// threads, 80 registers; three 2D tiles fit in shared memory), 3 in 3D (192
+// threads, 96 registers), 2 in 1D (128 threads).
 #ifndef MIXED_MIN_BLOCKS
 #define MIXED_MIN_BLOCKS 2
 #endif
 #ifndef MIXED_MIN_BLOCKS_2D
 #define MIXED_MIN_BLOCKS_2D 3
+#endif
+#ifndef MIXED_MIN_BLOCKS_3D
+#define MIXED_MIN_BLOCKS_3D 3
 #endif
 
 // Tile shapes (lines x midpoints): x sweeps 2 x 123 with 256 threads and
@@ -56,9 +59,34 @@ namespace wcns {
 #define MIXED_TM_Y (256 / MIXED_TL_Y)
 #endif
 template <int NDIM, int DIR>
-using TileMixed = TileT<(DIR == 0) ? (NDIM == 1 ? 1 : MIXED_TL_X) : MIXED_TL_Y,
-                        (DIR == 0) ? (NDIM == 1 ? MIXED_TM_1D : MIXED_TM_X) : MIXED_TM_Y,
-                        (DIR == 0) ? (NDIM == 1 ? 128 : 256) : 256>;
+using TileMixed2 = TileT<(DIR == 0) ? (NDIM == 1 ? 1 : MIXED_TL_X) : MIXED_TL_Y,
+                         (DIR == 0) ? (NDIM == 1 ? MIXED_TM_1D : MIXED_TM_X) : MIXED_TM_Y,
+                         (DIR == 0) ? (NDIM == 1 ? 128 : 256) : 256>;
+// 3D tiles (seven fields a node, 232 bytes of shared memory per node) have
+// their own shape: 192 threads, x tiles 2 x 91 (192 nodes), y/z tiles
+// 8 x 24 (192 midpoints), 57 / 67 KB, so that three blocks fit an SM
+// (measured on the 3D bubble collapse: 10 % faster than 256-thread tiles
+// at two blocks per SM).
+#ifndef MIXED3_THREADS
+#define MIXED3_THREADS 192
+#endif
+#ifndef MIXED3_TL_X
+#define MIXED3_TL_X 2
+#endif
+#ifndef MIXED3_TM_X
+#define MIXED3_TM_X (MIXED3_THREADS / MIXED3_TL_X - 5)
+#endif
+#ifndef MIXED3_TL_Y
+#define MIXED3_TL_Y 8
+#endif
+#ifndef MIXED3_TM_Y
+#define MIXED3_TM_Y (MIXED3_THREADS / MIXED3_TL_Y)
+#endif
+template <int NDIM, int DIR>
+using TileMixed = typename std::conditional<
+    NDIM == 3,
+    TileT<DIR == 0 ? MIXED3_TL_X : MIXED3_TL_Y, DIR == 0 ? MIXED3_TM_X : MIXED3_TM_Y, MIXED3_THREADS>,
+    TileMixed2<NDIM, DIR>>::type;
 
 // value = hi + lo: hi keeps the leading 24 bits of the double (truncated),
 // lo is the exact remainder rounded to FP32.  Integer operations only, so
@@ -946,7 +974,8 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
 }
 
 template <int NDIM, int DIR>
-__global__ void __launch_bounds__(TileMixed<NDIM, DIR>::THREADS, NDIM == 2 ? MIXED_MIN_BLOCKS_2D : MIXED_MIN_BLOCKS)
+__global__ void __launch_bounds__(TileMixed<NDIM, DIR>::THREADS,
+                                  NDIM == 2 ? MIXED_MIN_BLOCKS_2D : (NDIM == 3 ? MIXED_MIN_BLOCKS_3D : MIXED_MIN_BLOCKS))
     sweep_kernel_mixed(const SweepArgs a) {
   extern __shared__ double smem_raw[];
   if (!a.ctl->active) return;
