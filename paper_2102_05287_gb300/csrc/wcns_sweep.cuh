@@ -65,13 +65,10 @@ struct TileT {
 #ifndef FP64_3D_TM_X
 #define FP64_3D_TM_X FP64_TM_X
 #endif
-#ifndef FP64_2D_TL_X
-#define FP64_2D_TL_X 2
-#endif
 template <int NDIM, int DIR>
-using Tile = TileT<(DIR == 0) ? (NDIM == 1 ? 1 : (NDIM == 3 ? FP64_3D_TL_X : FP64_2D_TL_X)) : (NDIM == 2 ? 8 : 16),
+using Tile = TileT<(DIR == 0) ? (NDIM == 1 ? 1 : (NDIM == 3 ? FP64_3D_TL_X : 2)) : (NDIM == 2 ? 8 : 16),
                    (DIR == 0) ? (NDIM == 3 ? FP64_3D_TM_X : FP64_TM_X) : (NDIM == 2 ? 59 : 32),
-                   (DIR == 0) ? (NDIM == 1 ? 128 : (NDIM == 2 ? 128 * FP64_2D_TL_X : 256)) : 256>;
+                   (DIR == 0) ? (NDIM == 1 ? 128 : 256) : 256>;
 
 // Integer tests on FP64 values (no FP64-pipe compare): finite, and
 // finite-and-nonnegative (-0 counts as nonnegative, NaN and infinities
