@@ -16,6 +16,12 @@
 
 using namespace wcns;
 
+// Mixed batch tiles: the single-pass midpoint loop (false) or the fast pass
+// with certification failures deferred to a second pass (true).
+#ifndef BATCH_MIXED_DEFER
+#define BATCH_MIXED_DEFER false
+#endif
+
 namespace {
 
 struct BatchArgs {
@@ -69,7 +75,7 @@ __global__ void __launch_bounds__(T::THREADS, MIXED ? BATCH_MIXED_WARPS * 32 / T
   extern __shared__ double smem_raw[];
   for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
     if constexpr (MIXED)
-      sweep_body_mixed<1, 0, T, false>(a, BatchGeo<T>(b, t), smem_raw);
+      sweep_body_mixed<1, 0, T, BATCH_MIXED_DEFER>(a, BatchGeo<T>(b, t), smem_raw);
     else
       sweep_body<1, 0, double, T>(a, BatchGeo<T>(b, t), smem_raw);
     __syncthreads();
