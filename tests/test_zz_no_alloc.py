@@ -47,10 +47,15 @@ def c_grid_bcs(pr):
     return g, b
 
 
+PROBLEMS = {"shock_bubble_2d_96x48": lambda: P.shock_bubble_2d(96, 48, seed=5),
+            "bubble_collapse_3d_24": lambda: P.bubble_collapse_3d(n=24)}
+
+
+@pytest.mark.parametrize("problem", sorted(PROBLEMS))
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_noalloc_step_matches_handle_step_twice(precision):
+def test_noalloc_step_matches_handle_step_twice(precision, problem):
     lib = wcns.load()
-    pr = P.shock_bubble_2d(96, 48, seed=5)
+    pr = PROBLEMS[problem]()
     stream = torch.cuda.current_stream()
     ref = wcns.Solver(pr.n, pr.lo, pr.hi, pr.bcs, precision=precision, stream=stream, **pr.eos)
     g, b = c_grid_bcs(pr)
@@ -59,7 +64,8 @@ def test_noalloc_step_matches_handle_step_twice(precision):
     o.stream = C.c_void_p(stream.cuda_stream)
     W_ref = torch.from_numpy(pr.W).cuda()
     W_na = torch.from_numpy(pr.W).cuda()
-    dt = 0.4 / (ref.max_wavespeed(W_ref)[0] * pr.n[0] / 2.0 + ref.max_wavespeed(W_ref)[1] * pr.n[1])
+    sm = ref.max_wavespeed(W_ref)
+    dt = 0.4 / sum(sm[d] * pr.n[d] / (pr.hi[d] - pr.lo[d]) for d in range(pr.ndim))
     for call in range(2):
         ref.rk3_step(W_ref, dt)
         st = lib.wcns_rk3_step_noalloc(C.byref(g), C.byref(b), pr.eos["gamma_g"], pr.eos["gamma_l"],
