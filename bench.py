@@ -12,6 +12,20 @@ Arms:
                     slow, plain reference; bounded sample of the same
                     workload)
 
+Rooflines (the path has no dense contraction; it is ALU bound):
+  roofline                  FP64 sweep: the oracle's op mix per cell and
+                            direction (op-counting build, IS weights in their
+                            one-division form) over the live CUDA-event time
+                            of the dominant sweep, against the FP64 FMA peak
+                            measured live by csrc/peaks.cu
+  variants.mixed.roofline   mixed sweep: the FP64 steps (node EOS, node
+                            fluxes, update) at the FP64 peak plus all other
+                            steps at the FP32 peak
+  --workload riemann_batch  step-level fractions of the batched mode
+
+Other workloads (--workload): precision_2048, convergence, riemann_batch,
+bubble_3d, stress, full_runs; each prints its own JSON line.
+
 Multi-GPU (torchrun, one rank per GPU): independent replicas of the
 workload, one per rank (weak scaling; no data-path collective).  Rank 0
 prints one JSON line.
