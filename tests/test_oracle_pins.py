@@ -679,3 +679,34 @@ def test_op_counting_per_step():
     o1.opcount_reset()
     o1.rhs(pr.W, pr.dt_fixed)
     assert set(o1.opcount_rows()) == {"node_eos", "node_flux", "first_order_hllc", "update", "max_wavespeed"}
+
+
+def test_ssprk3_is_third_order_in_time():
+    """The oracle's SSPRK3 (Shu-Osher three-stage form, Sec. 5.3) converges
+    at third order in time: on a fixed grid, with a semi-discrete operator
+    that is smooth in the state (the first-order HLLC scheme on a smooth
+    acoustic and volume-fraction wave), halving dt divides the difference
+    between successive solutions by ~2^3.  A wrong stage coefficient drops
+    the order to one or two.  (The PP-WCNS-IS operator's nonlinear weights
+    switch near critical points of the characteristic fields, so its time
+    convergence is not a clean power law; the integrator is the same.)"""
+    eos = dict(P.WORKLOAD_EOS)
+    N = 32
+    x = (np.arange(N) + 0.5) / N
+    a1 = 0.5 + 0.1 * np.sin(2 * np.pi * x)
+    p = 1e5 + 1e4 * np.sin(2 * np.pi * x)
+    W0 = P.conservative(eos, a1 * 1000.0, (1 - a1) * 1.0, [np.full(N, 5.0)], p, a1)
+    o = Oracle((N,), (0.0,), (1.0,), (("periodic", "periodic"),), scheme="hllc1", **eos)
+    t_end = 16 * 0.8 / (o.max_wavespeed(W0)[0] * N)  # 16 steps at CFL 0.8 on the coarsest level
+    res = []
+    for k in range(4):
+        n = 16 * 2 ** k
+        W = W0.copy()
+        for _ in range(n):
+            W = o.rk3_step(W, t_end / n)
+        res.append(W)
+    dev = np.abs(res[-1] - W0).max(axis=1)
+    for f in (0, 1, 2, 3):  # partial densities, momentum, energy
+        d = [np.abs(res[k] - res[k + 1])[f].max() / dev[f] for k in range(3)]
+        orders = [np.log2(d[k] / d[k + 1]) for k in range(2)]
+        assert all(2.8 < q < 3.25 for q in orders), (f, d, orders)
