@@ -710,3 +710,36 @@ def test_ssprk3_is_third_order_in_time():
         d = [np.abs(res[k] - res[k + 1])[f].max() / dev[f] for k in range(3)]
         orders = [np.log2(d[k] / d[k + 1]) for k in range(2)]
         assert all(2.8 < q < 3.25 for q in orders), (f, d, orders)
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_symmetry_boundary_equals_mirrored_full_domain(ndim):
+    """A symmetry wall is a mirror (Sec. 6 set-ups): data mirrored about the
+    wall, with the normal momentum negated, computed on the full domain
+    through interior stencils only, gives on the original half exactly the
+    RHS of the half domain with the wall as its boundary.  The wave-speed
+    maxima (and so lambda of the flux limiter) are equal by symmetry."""
+    n = (14, 10) if ndim == 2 else (10, 9, 8)
+    half = P.random_admissible(n, seed=51 + ndim, jumps=True)
+    ax = 0  # the wall is normal to the last grid axis (y in 2D, z in 3D)
+    d = ndim - 1  # its direction index
+    mirror = np.flip(half, axis=1 + ax).copy()
+    mirror[2 + d] *= -1.0
+    full = np.concatenate([mirror, half], axis=1 + ax)
+    nf_ = list(n)
+    nf_[d] *= 2
+    lo_h = (0.0,) * ndim
+    hi_h = (1.0,) * ndim
+    lo_f = tuple(-1.0 if k == d else 0.0 for k in range(ndim))
+    bc_h = tuple(("symmetry", "transmissive") if k == d else ("transmissive", "transmissive") for k in range(ndim))
+    bc_f = tuple(("transmissive", "transmissive") for _ in range(ndim))
+    oh = Oracle(n, lo_h, hi_h, bc_h, **EOS)
+    of = Oracle(tuple(nf_), lo_f, hi_h, bc_f, **EOS)
+    sm_h, sm_f = oh.max_wavespeed(half), of.max_wavespeed(full)
+    np.testing.assert_array_equal(sm_h[:ndim], sm_f[:ndim])
+    dt = 0.4 / sum(sm_h[k] * n[k] for k in range(ndim))
+    L_h = oh.rhs(half, dt)
+    L_f = of.rhs(full, dt)
+    upper = [slice(None)] * (ndim + 1)
+    upper[1 + ax] = slice(n[d], None)
+    np.testing.assert_allclose(L_f[tuple(upper)], L_h, rtol=1e-12, atol=1e-12 * np.abs(L_h).max())
