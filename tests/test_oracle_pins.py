@@ -762,3 +762,32 @@ def test_periodic_rhs_commutes_with_shifts(ndim):
             Ls = o.rhs(np.roll(W, k, axis=axis).copy(), dt)
             np.testing.assert_allclose(Ls, np.roll(L, k, axis=axis), rtol=1e-13,
                                        atol=1e-13 * np.abs(L).max())
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_rhs_commutes_with_axis_permutations(ndim):
+    """The directions are treated alike (the split of Sec. 3.3 included):
+    on a cubic grid with the same boundaries on every axis, permuting the
+    axes of the data and the velocity components permutes the RHS."""
+    n = (16,) * ndim if ndim == 2 else (9,) * 3
+    W = P.random_admissible(n, seed=71 + ndim, jumps=True)
+    bcs = tuple(("transmissive", "transmissive") for _ in range(ndim))
+    o = Oracle(n, (0.0,) * ndim, (1.0,) * ndim, bcs, **EOS)
+    # array axes of a field: (z, y, x) order, i.e. grid axis d is array axis ndim - d
+    perm = [1, 0] if ndim == 2 else [1, 2, 0]  # new grid axis d takes old axis perm[d]
+
+    def permute(X):
+        fields = X[2:2 + ndim].copy()
+        out = np.empty_like(X)
+        arr_axes = [ndim - perm[ndim - 1 - a] for a in range(ndim)]  # for numpy transpose of one field
+        for q in range(X.shape[0]):
+            out[q] = np.transpose(X[q], [ax - 1 for ax in arr_axes])
+        for dnew in range(ndim):
+            out[2 + dnew] = np.transpose(fields[perm[dnew]], [ax - 1 for ax in arr_axes])
+        return out
+
+    sm = o.max_wavespeed(W)
+    dt = 0.4 / sum(sm[k] * n[k] for k in range(ndim))
+    L = o.rhs(W, dt)
+    Lp = o.rhs(permute(W), dt)
+    np.testing.assert_allclose(Lp, permute(L), rtol=1e-13, atol=1e-13 * np.abs(L).max())
