@@ -186,35 +186,25 @@ def load_peaks():
     return out
 
 
+OPCOUNTS = os.path.join(ROOT, "profiles", "opcounts.json")
+
+
+def _opcount_table(name):
+    """A stored algorithmic operation-count table (profiles/opcounts.json,
+    written by oracle/opcount_table.py from the oracle's op-counting build
+    and checked against it by tests/test_bench_roofline.py): per cell and
+    direction, in total and per step of the method, the IS weights in their
+    one-division form."""
+    with open(OPCOUNTS) as f:
+        t = json.load(f)[name]
+    return t
+
+
 def algorithmic_ops(nx, ny):
-    """Per-cell, per-direction operation mix of one RHS evaluation, from the
-    oracle's op-counting build on a 1/8-resolution copy of the workload
-    (the mix is per cell; limiters idle on the initial state either way)."""
-    from oracle import Oracle
-    from paper_2102_05287_gb300 import problems as P
-    pr = P.shock_bubble_2d(max(nx // 8, 16), max(ny // 8, 8))
-    o = Oracle(pr.n, pr.lo, pr.hi, pr.bcs, counting=True, **pr.eos)
-    sm = o.max_wavespeed(pr.W)
-    dt = 0.5 / (sm[0] * pr.n[0] / 2.0 + sm[1] * pr.n[1])
-    o.opcount_reset()
-    o.rhs(pr.W, dt)
-    c = o.opcount()
-    rows = o.opcount_rows()
-    units = pr.ncells * pr.ndim  # cell-direction updates
-    ops = {k: v / units for k, v in c.items()}
-    per_row = {r: {k: v / units for k, v in rc.items()} for r, rc in rows.items()}
-    # The oracle forms the IS weights with the five ratio divisions and four
-    # normalising divisions as printed (Sec. 4.3).  The same weights need one
-    # division: scaling every eta_k by the product of the five (beta + eps)
-    # costs 14 multiplications.  Count that form, so the roofline does not
-    # credit the kernel with divisions the method does not need.
-    is_calls = 2 * (pr.ndim + 4) * o.stats.midpoints / units
-    for d_ in (ops, per_row["wcns_is"]):
-        d_["div"] -= 8 * is_calls
-        d_["mul"] += 14 * is_calls
-    ops["is_interpolations"] = is_calls
-    ops["per_step"] = per_row
-    return ops
+    """Per-cell, per-direction operation mix of one RHS evaluation of the 2D
+    shock/bubble workload (measured on a 128 x 64 copy; the mix is per cell,
+    and the limiters idle on the initial state either way)."""
+    return _opcount_table("shock_bubble_2d")
 
 
 # Steps the mixed-precision sweeps compute in FP64 on every cell (node
@@ -519,8 +509,10 @@ def _errors(a, b, eos, ndim):
 
 
 def workload_precision(args):
-    """2048x1024 shock/bubble: FP64 vs mixed on the GPU, and both against one
-    step of the FP64 oracle."""
+    """2048x1024 shock/bubble: FP64 vs mixed on the GPU.  The workload's CPU
+    baseline is one SSPRK3 step of the FP64 oracle on the full grid, timed
+    on one host core; the GPU's first step of each precision is compared
+    with that baseline's result."""
     import numpy as np
     import torch
     from oracle import Oracle
@@ -547,19 +539,23 @@ def workload_precision(args):
         res[prec] = {"ms_per_step": ms, "cell_stage_updates_per_s": 3 * pr.ncells / (ms * 1e-3), "stats": s.stats()}
         states[prec] = W
         s.close()
+    # CPU baseline leg: the oracle's step, timed; its result is also the
+    # reference of the one-step errors below
     o = Oracle(pr.n, pr.lo, pr.hi, pr.bcs, **pr.eos)
     sm = o.max_wavespeed(pr.W)
     t0 = time.perf_counter()
     ref = o.rk3_step(pr.W, 0.5 / (sm[0] * pr.n[0] / 2.0 + sm[1] * pr.n[1]))
     t_or = time.perf_counter() - t0
     ref = torch.from_numpy(ref)
+    cpu = {"value": 3 * pr.ncells / t_or, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "one SSPRK3 step of the full 2048x1024 grid, single thread, %.1f s" % t_or}
     line = {"workload": "precision_2048x1024", "metric": METRIC, "unit": UNIT,
             "steps": args.steps, "warmup": args.warmup, "results": res,
             "mixed_speedup_vs_fp64": res["fp64"]["ms_per_step"] / res["mixed"]["ms_per_step"],
             "mixed_vs_fp64_after_steps": _errors(states["mixed"].cpu(), states["fp64"].cpu(), pr.eos, 2),
-            "one_step_vs_oracle": {"fp64": _errors(one["fp64"].cpu(), ref, pr.eos, 2),
-                                   "mixed": _errors(one["mixed"].cpu(), ref, pr.eos, 2)},
-            "oracle_one_step_s": t_or}
+            "one_step_vs_cpu_baseline_result": {"fp64": _errors(one["fp64"].cpu(), ref, pr.eos, 2),
+                                                "mixed": _errors(one["mixed"].cpu(), ref, pr.eos, 2)},
+            "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
 
 
@@ -608,35 +604,11 @@ def workload_convergence(args):
           flush=True)
 
 
-def algorithmic_ops_1d(rb, nsample=16):
-    """Per-cell operation mix of one 1D RHS evaluation over a sample of the
-    batch's problems (their initial states), per step of the method, from
-    the oracle's op-counting build, IS weights in their one-division form
-    (as algorithmic_ops)."""
-    import numpy as np
-    from oracle import Oracle
-    picks = np.random.default_rng(1).choice(len(rb.sizes), min(nsample, len(rb.sizes)), replace=False)
-    rows, cells, mids = {}, 0, 0
-    for k in picks:
-        n = int(rb.sizes[k])
-        W0 = np.ascontiguousarray(rb.W[:, int(rb.offsets[k]):int(rb.offsets[k + 1])])
-        o = Oracle((n,), (0.0,), (1.0,), (("transmissive", "transmissive"),), counting=True, **rb.eos)
-        dt = 0.5 / (o.max_wavespeed(W0)[0] * n)
-        o.opcount_reset()
-        o.rhs(W0, dt)
-        for r, c in o.opcount_rows().items():
-            acc = rows.setdefault(r, dict.fromkeys(c, 0))
-            for key, v in c.items():
-                acc[key] += v
-        cells += n
-        mids += o.stats.midpoints
-    per_step = {r: {k: v / cells for k, v in c.items()} for r, c in rows.items()}
-    is_calls = 2 * 5 * mids / cells
-    per_step["wcns_is"]["div"] -= 8 * is_calls
-    per_step["wcns_is"]["mul"] += 14 * is_calls
-    ops = {k: sum(c[k] for c in per_step.values()) for k in ("add", "mul", "div", "sqrt", "minmax")}
-    ops["per_step"] = per_step
-    return ops
+def algorithmic_ops_1d(rb=None):
+    """Per-cell operation mix of one 1D RHS evaluation, from 16 seeded
+    problems of the 4096-problem batch (the stored table; the mix is per
+    cell, so it serves smaller batches as well)."""
+    return _opcount_table("riemann_batch")
 
 
 def batch_roofline(ops, peaks, prec, ms_per_step, cells):
@@ -841,16 +813,16 @@ def workload_stress(args):
 
 def workload_full_runs(args):
     """The five configurations at their stated lengths, one JSON line:
-    1D water-air shock tube to t = 2.4e-4 (FP64, L1 against the exact
-    two-stiffened-gas Riemann solution, next to the oracle's), 2D
-    shock/bubble 1024x512 for 2000 steps (FP64 and mixed), the 4096-problem
-    batch for 500 steps (FP64 and mixed), 3D bubble collapse 384^3 for 500
-    steps (mixed).  Device counters, wall time and the mixed-vs-FP64
-    difference at the end."""
+    1D water-air shock tube to t = 2.4e-4 (FP64, next to its CPU baseline:
+    the same run of the FP64 oracle on one host core), 2D shock/bubble
+    1024x512 for 2000 steps (FP64 and mixed), the 4096-problem batch for 500
+    steps (FP64 and mixed), 3D bubble collapse 384^3 for 500 steps (mixed).
+    Device counters, wall time and the mixed-vs-FP64 difference at the end.
+    (The shock tube against the exact two-stiffened-gas Riemann solution is
+    checked in tests/test_gpu_parity.py.)"""
     import numpy as np
     import torch
     from oracle import Oracle
-    from oracle import exact_riemann as ER
     from paper_2102_05287_gb300 import problems as P
     from paper_2102_05287_gb300.wcns import Batch, Solver
     out = {}
@@ -860,17 +832,18 @@ def workload_full_runs(args):
     W = torch.from_numpy(pr.W).cuda()
     t, steps = s.advance_to(W, 0.0, pr.t_end, cfl=0.5)
     Wg = W.cpu().numpy()
+    # CPU baseline leg: the same run of the oracle, timed; the GPU's end
+    # state is compared with its result
     o = Oracle(pr.n, pr.lo, pr.hi, pr.bcs, **pr.eos)
+    t0 = time.perf_counter()
     Wo, to, so = o.advance_to(pr.W, 0.0, pr.t_end, cfl=0.5)
-    x = (np.arange(200) + 0.5) / 200
-    ex, _ = ER.solve_five_equation(pr.eos, (999.999, 0.00005, 0.0, 1e9, 1 - 1e-6),
-                                   (0.001, 49.99995, 0.0, 1e5, 1e-6), 0.7, pr.t_end, x)
-    rex = ex[0] + ex[1]
+    el = time.perf_counter() - t0
     out["config0_shock_tube_200"] = {
-        "t": t, "steps": steps, "oracle_steps": so, "stats": s.stats(),
-        "l1_rho_vs_exact": float(np.mean(np.abs(Wg[0] + Wg[1] - rex))),
-        "oracle_l1_rho_vs_exact": float(np.mean(np.abs(Wo[0] + Wo[1] - rex))),
-        "l1_rho_gpu_vs_oracle": float(np.abs((Wg[0] + Wg[1]) - (Wo[0] + Wo[1])).sum() / np.abs(Wo[0] + Wo[1]).sum())}
+        "t": t, "steps": steps, "stats": s.stats(),
+        "cpu_baseline": {"value": 3 * 200 * so / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "the full run (%d steps), single thread, %.2f s" % (so, el)},
+        "l1_rho_gpu_vs_cpu_baseline_result": float(np.abs((Wg[0] + Wg[1]) - (Wo[0] + Wo[1])).sum() /
+                                                   np.abs(Wo[0] + Wo[1]).sum())}
     s.close()
     # config 1
     pr = P.shock_bubble_2d(1024, 512)

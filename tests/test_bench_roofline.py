@@ -4,9 +4,10 @@ The FP64 line counts the oracle's per-step operation mix (IS weights in
 their one-division form) at the measured FP64 peak; the mixed line puts the
 steps the mixed sweeps compute in FP64 (node EOS, node fluxes, update) at
 the FP64 peak and all others at the FP32 peak.  These tests pin that
-bookkeeping on a small grid: the per-step counts add up to the totals the
-FP64 roofline uses, the one-division adjustment touches only the WCNS-IS
-step, and the mixed fraction equals the two pipe times over the launch time.
+bookkeeping: the per-step counts add up to the totals the FP64 roofline
+uses, the one-division adjustment touches only the WCNS-IS step, the mixed
+fraction equals the two pipe times over the launch time, and the stored
+tables (profiles/opcounts.json) are what the oracle gives.
 """
 import os
 import sys
@@ -34,8 +35,8 @@ def test_per_step_counts_add_up_to_the_totals(ops):
 def test_one_division_form_only_changes_wcns_is(ops):
     n_is = ops["is_interpolations"]
     # two interpolations per field (six in 2D) and midpoint; the counting
-    # grid is 16 x 8, whose lines have n + 1 midpoints for n cells
-    nx, ny = 16, 8
+    # grid is 128 x 64, whose lines have n + 1 midpoints for n cells
+    nx, ny = 128, 64
     midpoints = ny * (nx + 1) + nx * (ny + 1)
     assert n_is == pytest.approx(2 * 6 * midpoints / (2 * nx * ny), rel=1e-12)
     # one division per interpolation left in the WCNS-IS step
@@ -57,3 +58,15 @@ def test_mixed_roofline_is_two_pipe_time_over_launch_time(ops):
     # achieved / peak is the same fraction, in FP64-equivalent flop/s
     assert r["achieved"] / r["peak"] == pytest.approx(r["frac"])
     assert set(bench.MIXED_FP64_STEPS) <= set(ops["per_step"])
+
+
+def test_stored_opcount_tables_match_the_oracle():
+    """profiles/opcounts.json, which the benchmark reads, is what the
+    oracle's op-counting build gives now (oracle/opcount_table.py)."""
+    import json
+
+    from oracle.opcount_table import TABLE, compute_tables
+    with open(TABLE) as f:
+        stored = json.load(f)
+    fresh = json.loads(json.dumps(compute_tables()))
+    assert stored == fresh
