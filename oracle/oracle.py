@@ -1,8 +1,9 @@
 """ctypes binding of the plain FP64 C++ oracle (oracle/wcns_oracle.cpp).
 
 TEST INFRASTRUCTURE: this module is the parity reference and the timed CPU
-baseline.  It is loaded only by tests, the smoke check and the benchmark's
-CPU-baseline leg; the CUDA library never imports it.
+baseline.  It is loaded only by tests, the smoke check, the benchmark's
+CPU-baseline legs and reference arm, and opcount_table.py; the CUDA library
+never imports it.
 
 The oracle follows Wong et al., arXiv 2102.05287: EOS and mixture rules
 (Section 2), HLLC (Section 3), HCS + WCNS-IS with characteristic projection

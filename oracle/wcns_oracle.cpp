@@ -4,9 +4,9 @@
 // scheme for compressible gas-liquid flows" (arXiv 2102.05287).
 //
 // TEST INFRASTRUCTURE.  This file is the parity reference for the CUDA
-// library and the timed CPU baseline.  Only the test-suite, the smoke check
-// and the benchmark's CPU-baseline leg load it.  It shares no code, header,
-// table or constant with the CUDA path.
+// library and the timed CPU baseline.  Only the test-suite, the smoke check,
+// the benchmark's CPU-baseline legs and reference arm, and opcount_table.py
+// load it.  It shares no code, header, table or constant with the CUDA path.
 //
 // Style: scalar loops, no fusion, one step of the paper per function, in the
 // paper's order and notation.  Build with -O2 -ffp-contract=off so every
