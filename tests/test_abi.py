@@ -67,3 +67,47 @@ def test_host_side_validation_needs_no_gpu(lib):
     assert L.wcns_create(ctypes.byref(g), ctypes.byref(b), 1.4, 4.4, 6e8, ctypes.byref(h)) == wcns.WCNS_E_INVALID_ARG
     assert L.wcns_rhs(None, None, None, 1.0) == wcns.WCNS_E_INVALID_ARG
     assert L.wcns_strerror(wcns.WCNS_E_INVALID_ARG).decode() == "invalid argument"
+
+
+def test_empty_and_oversized_inputs_are_rejected_without_a_gpu(lib):
+    """Empty grids and batches, a batch with an empty problem, and a step
+    beyond the allocation-free scratch are refused by the host checks,
+    before any CUDA call and before the state pointer is used."""
+    from paper_2102_05287_gb300 import wcns
+    L = wcns.load()
+    E = wcns.WCNS_E_INVALID_ARG
+    g = wcns.wcns_grid()
+    g.ndim = 2
+    g.n[0], g.n[1] = 16, 0  # no cells along y
+    g.lo[0], g.lo[1], g.hi[0], g.hi[1] = 0.0, 0.0, 1.0, 1.0
+    b = wcns.wcns_bcs()
+    h = ctypes.c_void_p()
+    assert L.wcns_create(ctypes.byref(g), ctypes.byref(b), 1.4, 4.4, 6e8, ctypes.byref(h)) == E
+    g.n[1] = 8
+    g.hi[1] = 0.0  # empty extent
+    assert L.wcns_create(ctypes.byref(g), ctypes.byref(b), 1.4, 4.4, 6e8, ctypes.byref(h)) == E
+    assert not h.value
+
+    bh = ctypes.c_void_p()
+    IA = ctypes.c_int * 3
+    DA = ctypes.c_double * 3
+    lo, hi = DA(0.0, 0.0, 0.0), DA(1.0, 1.0, 1.0)
+    T, Pd = wcns.WCNS_BC_TRANSMISSIVE, wcns.WCNS_BC_PERIODIC
+    assert L.wcns_batch_create(0, IA(4, 5, 6), lo, hi, T, T, 1.4, 4.4, 6e8, ctypes.byref(bh)) == E
+    assert L.wcns_batch_create(3, IA(4, 0, 6), lo, hi, T, T, 1.4, 4.4, 6e8, ctypes.byref(bh)) == E
+    assert L.wcns_batch_create(3, IA(4, 5, 6), lo, DA(1.0, 0.0, 1.0), T, T, 1.4, 4.4, 6e8,
+                               ctypes.byref(bh)) == E
+    assert L.wcns_batch_create(3, IA(4, 5, 6), lo, hi, Pd, T, 1.4, 4.4, 6e8, ctypes.byref(bh)) == E
+    assert not bh.value
+
+    # the allocation-free step: no scratch for a 2048 x 1024 grid
+    # ((3 * 6 + 3) doubles a cell > 8M doubles), nor for a non-positive dt;
+    # the state pointer is a placeholder the checks never dereference
+    g.n[0], g.n[1] = 2048, 1024
+    g.hi[1] = 1.0
+    W = ctypes.c_void_p(256)
+    assert L.wcns_rk3_step_noalloc(ctypes.byref(g), ctypes.byref(b), 1.4, 4.4, 6e8, None, W,
+                                   1e-7) == wcns.WCNS_E_TOO_LARGE
+    g.n[0], g.n[1] = 16, 8
+    assert L.wcns_rk3_step_noalloc(ctypes.byref(g), ctypes.byref(b), 1.4, 4.4, 6e8, None, W, 0.0) == E
+    assert L.wcns_rk3_step_noalloc(ctypes.byref(g), ctypes.byref(b), 1.4, 4.4, 6e8, None, None, 1e-7) == E
