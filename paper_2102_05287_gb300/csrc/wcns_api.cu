@@ -370,7 +370,8 @@ int run_steps(wcns_handle *h, double *W, int nsteps, double dt_fixed, double cfl
     h->launches = before;  // counted when replayed
     cudaError_t e = cudaStreamEndCapture(h->cap, &g);
     h->launch_stream = h->stream;
-    if (st || e != cudaSuccess) return WCNS_E_CUDA;
+    if (e == cudaSuccess && st) cudaGraphDestroy(g);  // a partial capture is never launched
+    if (st || e != cudaSuccess) return st ? st : WCNS_E_CUDA;
     e = cudaGraphInstantiate(&h->graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {

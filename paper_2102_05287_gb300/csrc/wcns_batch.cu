@@ -460,7 +460,8 @@ int wcns_batch_advance(wcns_batch *b, double *W, int nsteps, double cfl, double 
     if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return WCNS_E_CUDA;
     st = enqueue_batch_step(b, W, cfl, t_out, b->variant, b->grid, b->cap);
     cudaError_t e = cudaStreamEndCapture(b->cap, &g);
-    if (st || e != cudaSuccess) return WCNS_E_CUDA;
+    if (e == cudaSuccess && st) cudaGraphDestroy(g);  // a partial capture is never launched
+    if (st || e != cudaSuccess) return st ? st : WCNS_E_CUDA;
     e = cudaGraphInstantiate(&b->graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
