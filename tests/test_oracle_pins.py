@@ -791,3 +791,50 @@ def test_rhs_commutes_with_axis_permutations(ndim):
     L = o.rhs(W, dt)
     Lp = o.rhs(permute(W), dt)
     np.testing.assert_allclose(Lp, permute(L), rtol=1e-13, atol=1e-13 * np.abs(L).max())
+
+
+# ---------------------------------------------------------------------------
+# Dimension reduction: a field that is uniform along the extra axis, with no
+# velocity along it, is the lower-dimensional problem (Sec. 2 "similar
+# extension").  The sweep along that axis must add exactly nothing, the extra
+# momentum must stay at rest, and the flux limiter must see the same
+# lambda_d = dt / (dx_d sigma_d) (Sec. 3.3): with sigma_d = tau_d / sum(tau),
+# dt_low = dt_high * sum(tau_high) / sum(tau_low) gives equal lambdas.  On
+# these states the limiters act (a lambda without sigma_d misses by 5e-5).
+# ---------------------------------------------------------------------------
+def _lift(W, mom_axis, copies):
+    """Insert a zero momentum component for the new axis (after the existing
+    momenta) and repeat the state along that axis (the new slowest axis)."""
+    nd = W.shape[0] - 4
+    fields = [W[f] for f in range(2 + nd)] + [np.zeros_like(W[0])] + [W[2 + nd], W[3 + nd]]
+    assert mom_axis == nd
+    return np.ascontiguousarray(np.broadcast_to(np.stack(fields)[:, None], (nd + 5, copies) + W.shape[1:]))
+
+
+@pytest.mark.parametrize("case", ["2d_to_1d", "3d_to_2d"])
+def test_uniform_extra_axis_reduces_to_the_lower_dimension(case):
+    T = ("transmissive", "transmissive")
+    if case == "2d_to_1d":
+        n_lo, bcs_lo, copies, bc_new = (64,), (T,), 4, ("symmetry", "transmissive")
+    else:
+        n_lo, bcs_lo, copies, bc_new = (24, 16), (T, ("symmetry", "transmissive")), 6, ("periodic", "periodic")
+    nd = len(n_lo)
+    W = P.random_admissible(n_lo, seed=21 + nd)
+    Wh = _lift(W, nd, copies)
+    n_hi = n_lo + (copies,)
+    lo = Oracle(n_lo, (0.0,) * nd, (1.0,) * nd, bcs_lo, **EOS)
+    hi = Oracle(n_hi, (0.0,) * (nd + 1), (1.0,) * (nd + 1), bcs_lo + (bc_new,), **EOS)
+    tau = [s * n for s, n in zip(hi.max_wavespeed(Wh), n_hi)]
+    dt_hi = 0.4 / sum(tau)
+    dt_lo = dt_hi * sum(tau) / sum(tau[:nd])
+    L_hi = hi.rhs(Wh, dt_hi)
+    L_lo = lo.rhs(W, dt_lo)
+    assert np.all(L_hi[2 + nd] == 0.0)  # the new momentum stays at rest
+    ref = np.broadcast_to(_lift(L_lo, nd, copies), L_hi.shape)
+    X, R = L_hi.reshape(nd + 5, -1), ref.reshape(nd + 5, -1)
+    err = np.abs(X - R).max(axis=1) / np.maximum(np.abs(R).max(axis=1), 1e-300)
+    assert err.max() < 1e-13, err
+    s_lo, s_hi = lo.stats.as_dict(), hi.stats.as_dict()
+    assert s_lo["flux_limited"] > 0 and s_lo["interp_limited"] > 0
+    for k in ("interp_limited", "flux_limited", "interp_hard", "flux_hard"):
+        assert s_hi[k] == copies * s_lo[k], (k, s_hi[k], s_lo[k])
