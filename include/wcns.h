@@ -147,7 +147,9 @@ int wcns_set_dirichlet_face(wcns_handle *h, int axis, int side, const double *W_
  * summed over the ndim directions.  dt is the Euler step the flux limiter
  * protects (Sec. 5.2): lambda_d = dt / (dx_d sigma_d), sigma_d = tau_d /
  * sum(tau) with tau_d = max(|u_d| + c)/dx_d of W and the Dirichlet ghost
- * states (Sec. 3.3).
+ * states (Sec. 3.3).  dt must be finite and >= 0 (else WCNS_E_INVALID_ARG);
+ * dt = 0 is taken as a vanishing step (1e-300), for which the flux limiter's
+ * half states are the cell states themselves.
  * W and dWdt are device arrays of nf * ncells doubles; they must not
  * overlap.  Asynchronous on the handle's stream. */
 int wcns_rhs(wcns_handle *h, const double *W, double *dWdt, double dt);
