@@ -22,3 +22,21 @@ def load_golden(name):
                 continue
             rows.append([float(x) for x in line.split()])
     return rows
+
+
+def build_abi_consumer(libpath, outdir):
+    """Compile tests/abi_consumer.c as strict C99 against include/wcns.h and
+    the built libwcns.so; returns the executable's path."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    libdir = os.path.dirname(os.path.abspath(libpath))
+    exe = os.path.join(str(outdir), "abi_consumer")
+    cmd = [cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-O2",
+           "-I", os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "abi_consumer.c"),
+           "-L", libdir, "-lwcns", "-Wl,-rpath," + libdir, "-o", exe]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    return exe

@@ -111,3 +111,14 @@ def test_empty_and_oversized_inputs_are_rejected_without_a_gpu(lib):
     g.n[0], g.n[1] = 16, 8
     assert L.wcns_rk3_step_noalloc(ctypes.byref(g), ctypes.byref(b), 1.4, 4.4, 6e8, None, W, 0.0) == E
     assert L.wcns_rk3_step_noalloc(ctypes.byref(g), ctypes.byref(b), 1.4, 4.4, 6e8, None, None, 1e-7) == E
+
+
+def test_plain_c_program_uses_the_boundary(lib, tmp_path):
+    """The header is self-contained C99, and a C program linked against the
+    library gets the documented answers from its host-side checks."""
+    import subprocess
+    from paper_2102_05287_gb300 import build
+    from tests.conftest import build_abi_consumer
+    exe = build_abi_consumer(build.LIB, tmp_path)
+    r = subprocess.run([exe, "--checks"], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, r.stdout + r.stderr

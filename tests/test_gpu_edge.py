@@ -8,7 +8,8 @@
   same, so the flux differences and the alpha1 div(u) term vanish exactly
   (Sec. 4 semi-discrete form);
 - zero steps leave the state and the time untouched;
-- a batch of one- to fifteen-cell Riemann problems.
+- a batch of one- to fifteen-cell Riemann problems;
+- a plain C99 program (tests/abi_consumer.c) driving the C ABI directly.
 
 FP64 bar: 1e-12 relative per field (with the oracle's 1-ulp spread as the
 fallback where a limiter theta solve amplifies round-off); mixed bar: the
@@ -205,3 +206,37 @@ def test_batch_of_tiny_problems(precision):
         assert abs(tt[k] - t_single) <= 1e-14 * t_single
         s.close()
     b.close()
+
+
+def test_plain_c_program_advances_the_shock_tube(tmp_path):
+    """tests/abi_consumer.c, a C99 program that sees only include/wcns.h,
+    advances the Sec. 6 water-air shock tube (200 cells) 20 steps through
+    wcns_advance_steps_host; its result is the Python binding's, bit for bit,
+    and its first step is the oracle's."""
+    import subprocess
+    from paper_2102_05287_gb300 import build
+    from tests.conftest import build_abi_consumer
+    exe = build_abi_consumer(build.LIB, tmp_path)
+    pr = P.water_air_shock_tube(200)
+    assert pr.eos == {"gamma_g": 1.4, "gamma_l": 4.4, "pinf_l": 6e8}  # the program's fluids
+    W0 = np.ascontiguousarray(pr.W)
+    src, dst = tmp_path / "w0.bin", tmp_path / "w1.bin"
+    W0.tofile(src)
+    for nsteps in (1, 20):
+        r = subprocess.run([exe, str(src), str(dst), str(nsteps), "0.5"], capture_output=True, text=True,
+                           timeout=120)
+        assert r.returncode == 0, r.stdout + r.stderr
+        words = r.stdout.split()
+        t_c = float(words[1])
+        assert int(words[5]) == 0 and int(words[7]) == 0, r.stdout  # nonfinite, inadmissible
+        got = np.fromfile(dst).reshape(W0.shape)
+        s = Solver((200,), (0.0,), (1.0,), ((T, T),), **pr.eos)
+        Wh = torch.from_numpy(W0.copy())
+        t_py = s.advance_steps_host(Wh, nsteps, cfl=0.5)
+        s.close()
+        assert np.array_equal(got, Wh.numpy()) and t_c == t_py
+        if nsteps == 1:
+            o = Oracle((200,), (0.0,), (1.0,), ((T, T),), **pr.eos)
+            dt = 0.5 / (o.max_wavespeed(W0)[0] * 200)
+            assert abs(t_c - dt) <= 1e-14 * dt
+            assert_parity(got, o.rk3_step(W0, dt), lambda X: o.rk3_step(X, dt), W0)
