@@ -65,9 +65,10 @@ struct BatchGeo {
 // MIXED selects the mixed-precision body (wcns_mixed_body.cuh).  Mixed
 // tiles target BATCH_MIXED_WARPS resident warps per SM (a register cap of
 // 65536 / (32 BATCH_MIXED_WARPS) per thread); the FP64 body keeps its
-// registers.
+// registers.  On the 4096-problem batch 32 warps (64 registers, more
+// spills) beat 28, 24, 20 and 16: the single-pass body is latency bound.
 #ifndef BATCH_MIXED_WARPS
-#define BATCH_MIXED_WARPS 24
+#define BATCH_MIXED_WARPS 32
 #endif
 template <bool MIXED, class T>
 __global__ void __launch_bounds__(T::THREADS, MIXED ? BATCH_MIXED_WARPS * 32 / T::THREADS : 1)
