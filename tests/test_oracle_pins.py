@@ -838,3 +838,85 @@ def test_uniform_extra_axis_reduces_to_the_lower_dimension(case):
     assert s_lo["flux_limited"] > 0 and s_lo["interp_limited"] > 0
     for k in ("interp_limited", "flux_limited", "interp_hard", "flux_hard"):
         assert s_hi[k] == copies * s_lo[k], (k, s_hi[k], s_lo[k])
+
+
+# ---------------------------------------------------------------------------
+# The positivity property of Sec. 5 on random violent states, and the
+# pressure-velocity equilibrium of Sec. 6.2 in 2D with the limiters acting.
+# ---------------------------------------------------------------------------
+def _violent_state(rng, n):
+    """Piecewise-constant random states in G: segments (1D) or painted
+    rectangles (2D) of volume fraction at a 1e-8 floor or 1/2, liquid
+    density 500-1500, gas density 1e-2-30, velocities up to 800 m/s and
+    pressures 1e4-1e9, so the unlimited scheme leaves G almost always."""
+    ndim = len(n)
+    grid = tuple(reversed(n))
+
+    def draw():
+        return ([rng.choice([1e-8, 1 - 1e-8, 0.5]), rng.uniform(500, 1500), 10 ** rng.uniform(-2, 1.5)]
+                + list(rng.uniform(-800, 800, ndim)) + [10 ** rng.uniform(4, 9)])
+
+    F = np.empty((4 + ndim,) + grid)
+    F[:] = np.array(draw()).reshape((-1,) + (1,) * ndim)
+    for _ in range(5):
+        box = [slice(*sorted(rng.integers(0, k + 1, 2))) for k in grid]
+        F[(slice(None),) + tuple(box)] = np.array(draw()).reshape((-1,) + (1,) * ndim)
+    a1, rl, rg = F[0], F[1], F[2]
+    return P.conservative(EOS, a1 * rl, (1 - a1) * rg, list(F[3:3 + ndim]), F[3 + ndim], a1)
+
+
+@pytest.mark.parametrize("ndim,trials", [(1, 200), (2, 40)])
+def test_positivity_on_random_violent_states(ndim, trials):
+    """Sec. 5: at CFL 0.5 the forward-Euler stage W + dt L(W) of PP-WCNS-IS
+    and the SSPRK3 step stay in G (admissibility written out in this file,
+    not taken from the oracle); the same states take the unlimited
+    WCNS-IS out of G in at least 75 % of the trials."""
+    rng = np.random.default_rng(11 + ndim)
+    T = ("transmissive", "transmissive")
+    unlimited_out = limited = 0
+    for _ in range(trials):
+        n = tuple(int(rng.integers(12, 48 if ndim == 1 else 20)) for _ in range(ndim))
+        W = _violent_state(rng, n)
+        assert in_G(EOS, W, ndim)
+        for scheme in ("pp-wcns-is", "wcns-is"):
+            o = Oracle(n, (0.0,) * ndim, (1.0,) * ndim, (T,) * ndim, scheme=scheme, **EOS)
+            sm = o.max_wavespeed(W)
+            dt = 0.5 / sum(sm[d] * n[d] for d in range(ndim))
+            stage = W + dt * o.rhs(W, dt)
+            if scheme == "pp-wcns-is":
+                assert in_G(EOS, stage, ndim), n
+                assert in_G(EOS, o.rk3_step(W, dt), ndim), n
+                limited += o.stats.as_dict()["flux_limited"]
+            else:
+                unlimited_out += not in_G(EOS, stage, ndim)
+    assert unlimited_out >= 0.75 * trials and limited > 0, (unlimited_out, limited)
+
+
+def test_pressure_velocity_equilibrium_2d_with_limiters_acting():
+    """Sec. 6.2 in 2D: uniform p and velocity with volume fractions at their
+    floors and phasic densities random from cell to cell; after 20 CFL-0.5
+    steps p, u and v are still uniform (to 1e-11), although both limiters
+    act thousands of times (the alpha1 split of the HCS flux and the
+    limiter blends keep the equilibrium)."""
+    n = (32, 24)
+    grid = (24, 32)
+    rng = np.random.default_rng(5)
+    a1 = np.clip(rng.uniform(0, 1, grid), 1e-6, 1 - 1e-6)
+    a1[:, :10], a1[:, 20:] = 1 - 1e-6, 1e-6
+    W = P.conservative(EOS, a1 * rng.uniform(900, 1100, grid), (1 - a1) * rng.uniform(1, 50, grid),
+                       [np.full(grid, 80.0), np.full(grid, -50.0)], np.full(grid, 2e6), a1)
+    o = make(n)
+    sm = o.max_wavespeed(W)
+    dt = 0.5 / (sm[0] * n[0] + sm[1] * n[1])
+    for _ in range(20):
+        W = o.rk3_step(W, dt)
+    st = o.stats.as_dict()
+    assert st["interp_limited"] > 1000 and st["flux_limited"] > 1000, st
+    rho = W[0] + W[1]
+    a = W[5]
+    ke = 0.5 * (W[2] ** 2 + W[3] ** 2) / rho
+    G = a / (EOS["gamma_l"] - 1) + (1 - a) / (EOS["gamma_g"] - 1)
+    p = (W[4] - ke - a * EOS["gamma_l"] * EOS["pinf_l"] / (EOS["gamma_l"] - 1)) / G
+    assert np.abs(W[2] / rho - 80.0).max() / 80.0 < 1e-11
+    assert np.abs(W[3] / rho + 50.0).max() / 50.0 < 1e-11
+    assert np.abs(p - 2e6).max() / 2e6 < 1e-11
