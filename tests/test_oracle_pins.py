@@ -378,6 +378,64 @@ def test_interp_limiter_restores_bounds(case):
     _collinear(Wn, Wt, out)
 
 
+@pytest.mark.parametrize("case", ["neg_a2r2", "alpha_above_one", "neg_rho_ct2"])
+def test_interp_limiter_theta_is_the_largest_admissible(case):
+    """Algorithms 1-3 solve (1 - theta) f(W_i) + theta f(W~) = eps for the
+    violated quantity: theta is the closed form computed here from f written
+    out in this file (a linear f then sits exactly at its tolerance; for
+    rho ctilde^2, concave, at or above it), not just any admissible blend."""
+    o = make((8,))
+    # (alpha near 1 with a high pressure, so that the volume-fraction blend
+    # alone restores G and Algorithm 3 does not act after it)
+    a1, p = (0.99, 1e8) if case == "alpha_above_one" else (0.3, 1e6)
+    Wn = rand_state(np.random.default_rng(14), 1, a1=a1, p=p)
+    Wt = Wn.copy()
+    if case == "neg_a2r2":
+        Wt[1] = -0.5 * Wn[1]
+        f, eps, tol = (lambda W: W[1]), 1e-10, 1e-13 * Wn[1]
+    elif case == "alpha_above_one":
+        Wt[-1] = 1.003
+        f, eps, tol = (lambda W: 1.0 - W[-1]), 1e-10, 1e-15
+    else:
+        Wt[3] = Wn[3] - 3.0 * o.thermo(Wn)["rho_ct2"]
+        f, eps = (lambda W: float(rho_ct2(EOS, W.reshape(-1, 1), 1)[0])), 1e-8
+    out, lim, hard = o.interp_limit(Wn, Wt)
+    assert lim and not hard
+    th_expected = (f(Wn) - eps) / (f(Wn) - f(Wt))
+    d1 = Wt - Wn
+    th = np.dot(d1, out - Wn) / np.dot(d1, d1)
+    assert abs(th - th_expected) <= 1e-12, (th, th_expected)
+    if case != "neg_rho_ct2":
+        assert abs(f(out) - eps) <= tol, (f(out), eps)
+    else:
+        assert f(out) >= eps * (1 - 1e-6)
+
+
+def test_flux_hard_switch_checks_both_half_states():
+    """Sec. 5.2 hard switch: it inspects W_i^{***,+} and W_{i+1}^{***,-};
+    when the first-order half state on either side already leaves G (a flux
+    that drains more phase-2 mass than the cell holds in the half step), the
+    switch fires and both split fluxes are the first-order ones."""
+    o = make((8,))
+    rng = np.random.default_rng(16)
+    Wi = rand_state(rng, 1, a1=0.5, p=1e6)
+    Wi1 = rand_state(rng, 1, a1=0.5, p=1e6)
+    GH, uH = o.hllc(0, Wi, Wi1)
+    lam = 0.2 / 1500.0
+    for side in ("plus", "minus"):
+        GHm, GHp = GH.copy(), GH.copy()
+        GHm[-1] -= Wi[-1] * uH
+        GHp[-1] -= Wi1[-1] * uH
+        if side == "plus":  # W_i^+ = W_i - 2 lam (G^- - F_i)
+            GHm[1] += 5.0 * Wi[1] / (2 * lam)
+        else:  # W_{i+1}^- = W_{i+1} + 2 lam (G^+ - F_{i+1})
+            GHp[1] -= 5.0 * Wi1[1] / (2 * lam)
+        gm, gp, lim, hard = o.flux_limit(0, Wi, Wi1, GHm, GHp, lam, GHm, GHp)
+        assert hard, side
+        np.testing.assert_array_equal(gm, GHm)
+        np.testing.assert_array_equal(gp, GHp)
+
+
 def test_flux_limiter_blends_toward_hllc_until_half_states_are_admissible():
     o = make((8,))
     rng = np.random.default_rng(15)
