@@ -1017,3 +1017,43 @@ def test_rhs_converges_to_the_model_operator_at_fifth_order():
             assert order.min() >= 4.4, (N, order)
         prev = err
     assert err.max() < 1e-8, err
+
+
+def _spectral_d(f, axis):
+    k = np.fft.fftfreq(f.shape[axis], 1.0 / f.shape[axis]) * 2 * np.pi
+    shape = [1] * f.ndim
+    shape[axis] = f.shape[axis]
+    return np.real(np.fft.ifft(1j * k.reshape(shape) * np.fft.fft(f, axis=axis), axis=axis))
+
+
+def test_rhs_converges_to_the_model_operator_2d():
+    """2D counterpart of the fifth-order pin, in the L2 norm (in 2D some
+    line always has a smooth extremum near a midpoint, where the order drops
+    locally, as the paper's convergence proof excludes critical points):
+    -div of every flux and -u.grad(alpha1); mean observed order >= 4.4 for
+    every component from N = 64 to 256, and L2 errors below 2e-8."""
+    errs = []
+    for N in (64, 256):
+        c = (np.arange(N) + 0.5) / N
+        Y, X = np.meshgrid(c, c, indexing="ij")
+        tx, ty = 2 * np.pi * X, 2 * np.pi * Y
+        a1 = 0.5 + 0.2 * np.sin(tx + 0.3) * np.cos(ty + 0.9)
+        r1 = 1000 * (1 + 0.01 * np.cos(tx + 1.1 + ty))
+        r2 = 1 + 0.1 * np.cos(tx + 2.0) * np.sin(ty + 0.2)
+        u = 10 + 5 * np.sin(tx + 0.7)
+        v = -6 + 4 * np.cos(ty + 0.5 + tx)
+        p = 1e5 * (1 + 0.01 * np.cos(tx + 0.4) * np.cos(ty + 1.3))
+        W = P.conservative(EOS, a1 * r1, (1 - a1) * r2, [u, v], p, a1)
+        o = make((N, N))
+        sm = o.max_wavespeed(W)
+        L = o.rhs(W, 0.4 / (sm[0] * N + sm[1] * N))
+        E = W[4]
+        dx, dy = (lambda f: _spectral_d(f, 1)), (lambda f: _spectral_d(f, 0))
+        exact = [-dx(W[0] * u) - dy(W[0] * v), -dx(W[1] * u) - dy(W[1] * v),
+                 -dx(W[2] * u + p) - dy(W[2] * v), -dx(W[3] * u) - dy(W[3] * v + p),
+                 -dx((E + p) * u) - dy((E + p) * v), -u * dx(a1) - v * dy(a1)]
+        errs.append(np.array([np.sqrt(np.mean((L[q] - exact[q]) ** 2) / np.mean(exact[q] ** 2))
+                              for q in range(6)]))
+    order = np.log2(errs[0] / errs[1]) / 2
+    assert order.min() >= 4.4, order
+    assert errs[1].max() < 2e-8, errs[1]
