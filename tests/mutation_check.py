@@ -90,6 +90,15 @@ MUTANTS = [
      "if (flip) dst[2 + d] = dst[2 + d];", False),
     ("symmetry ghost mirrored about the wrong cell", "src = i < 0 ? -1 - i : 2 * n - 1 - i;",
      "src = i < 0 ? -i : 2 * n - 2 - i;", False),
+    ("pressure added to the x momentum flux in every direction", "F[2 + d] = F[2 + d] + t.p;",
+     "F[2] = F[2] + t.p;", False),
+    ("node normal velocity always u_x", "nd.un = nd.t.vel[d];", "nd.un = nd.t.vel[0];", False),
+    ("left star normal momentum always in x", "WsL[2 + d] = chi * (tL.rho * ss);",
+     "WsL[2] = chi * (tL.rho * ss);", False),
+    ("R^-1 tangential rows pick the normal velocity", "Rinv[row * nf + 2 + j] = 1.0;",
+     "Rinv[row * nf + 2 + d] = 1.0;", False),
+    ("tau_d from the x wave speed", "tau[d] = smax[d] / spacing(c, d);", "tau[d] = smax[0] / spacing(c, d);",
+     False),
     ("sign(0) = +1 in the HLLC flux (at s* = 0 both sides give the same flux)", "  if (x > 0.0) return 1.0;",
      "  if (x >= 0.0) return 1.0;", True),
 ]
