@@ -1,6 +1,7 @@
 """Mutation check of the oracle pins (test infrastructure, run by hand).
 
-Each mutant is one plausible mistake in oracle/wcns_oracle.cpp: a dropped
+Each mutant is one plausible mistake in oracle/wcns_oracle.cpp (or in the
+exact Riemann solver oracle/exact_riemann.py): a dropped
 term, a wrong sign, constant, index or operand order.  For every mutant the
 repository is copied to a scratch directory, the mistake is planted in the
 copy's oracle (the first occurrence of the pattern: the scheme's own code,
@@ -23,6 +24,7 @@ import tempfile
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join("oracle", "wcns_oracle.cpp")
+RIEMANN_SRC = os.path.join("oracle", "exact_riemann.py")
 SKIP = {".git", "_work", "gpurun_out", "_build", "__pycache__", "profiles", "baseline", ".pytest_cache"}
 
 # (what the mistake is, pattern, replacement, harmless)
@@ -103,6 +105,25 @@ MUTANTS = [
      "  if (x >= 0.0) return 1.0;", True),
 ]
 
+# mistakes in the exact two-stiffened-gas Riemann solver (the reference of
+# the shock-tube convergence pins)
+RIEMANN_MUTANTS = [
+    ("shock relation B without pinf", "B = (g - 1.0) / (g + 1.0) * (self.p + pi)",
+     "B = (g - 1.0) / (g + 1.0) * self.p", False),
+    ("rarefaction exponent (g-1)/g", "e = (g - 1.0) / (2.0 * g)", "e = (g - 1.0) / g", False),
+    ("star velocity with the wave functions swapped", "u = 0.5 * (L.u + R.u) + 0.5 * (fr - fl)",
+     "u = 0.5 * (L.u + R.u) + 0.5 * (fl - fr)", False),
+    ("shock speed with the minus term", "(g + 1.0) / (2.0 * g) * ratio + (g - 1.0) / (2.0 * g))",
+     "(g + 1.0) / (2.0 * g) * ratio - (g - 1.0) / (2.0 * g))", False),
+    ("post-shock density ratio with -gm", "rho = s.rho * (ratio + gm) / (gm * ratio + 1.0)",
+     "rho = s.rho * (ratio - gm) / (gm * ratio + 1.0)", False),
+    ("fan pressure without the -pinf", "p = (s.p + pi) * (c / s.c) ** (2.0 * g / (g - 1.0)) - pi",
+     "p = (s.p + pi) * (c / s.c) ** (2.0 * g / (g - 1.0))", False),
+    ("mixture pinf = Pi / gbar", "return gb, Pi * (gb - 1.0) / gb", "return gb, Pi / gb", False),
+]
+
+ALL = [(SRC,) + m for m in MUTANTS] + [(RIEMANN_SRC,) + m for m in RIEMANN_MUTANTS]
+
 
 def _copy_repo(dst):
     def ignore(_dir, names):
@@ -111,11 +132,11 @@ def _copy_repo(dst):
 
 
 def run_mutant(k):
-    what, pattern, replacement, harmless = MUTANTS[k]
+    src_file, what, pattern, replacement, harmless = ALL[k]
     work = tempfile.mkdtemp(prefix="oracle_mutant%02d_" % k)
     try:
         _copy_repo(work)
-        path = os.path.join(work, SRC)
+        path = os.path.join(work, src_file)
         with open(path) as f:
             src = f.read()
         if pattern not in src:
@@ -141,8 +162,8 @@ def main():
     args = ap.parse_args()
     survivors = []
     with cf.ProcessPoolExecutor(max_workers=args.jobs) as ex:
-        for k, failed, summary in ex.map(run_mutant, range(len(MUTANTS))):
-            what, _, _, harmless = MUTANTS[k]
+        for k, failed, summary in ex.map(run_mutant, range(len(ALL))):
+            _, what, _, _, harmless = ALL[k]
             caught = bool(failed)
             tag = "killed" if caught else ("harmless" if harmless else "SURVIVED")
             if failed is None:
@@ -150,7 +171,7 @@ def main():
             print("%-8s %-62s %s" % (tag, what, ", ".join(failed or []) or summary), flush=True)
             if not caught and not harmless:
                 survivors.append(what)
-    print("%d mutants, %d survived" % (len(MUTANTS), len(survivors)))
+    print("%d mutants, %d survived" % (len(ALL), len(survivors)))
     return 1 if survivors else 0
 
 

@@ -655,10 +655,19 @@ def test_exact_riemann_satisfies_jump_conditions():
     R = ER.Side(right[0] + right[1], 0.0, 1e5, gr, pr_)
     ps, us = ER.star_state(L, R)
     assert 1e5 < ps < 1e9 and us > 0
-    # right shock: Rankine-Hugoniot in the shock frame
+    # right shock: Rankine-Hugoniot in the shock frame, with the shock speed
+    # located in the sampled solution (the last xi that still returns the
+    # post-shock state), not taken from a formula
     rho_s = ER.sample(L, R, ps, us, us + 1e-9)[0]
-    ratio = (ps + pr_) / (1e5 + pr_)
-    S = R.u + R.c * math.sqrt((gr + 1) / (2 * gr) * ratio + (gr - 1) / (2 * gr))
+    lo, hi = us + 1e-9, us + 100.0 * R.c
+    assert ER.sample(L, R, ps, us, hi)[0] == R.rho
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if ER.sample(L, R, ps, us, mid)[0] == rho_s:
+            lo = mid
+        else:
+            hi = mid
+    S = 0.5 * (lo + hi)
     m0, m1 = R.rho * (R.u - S), rho_s * (us - S)
     assert m1 == pytest.approx(m0, rel=1e-10)
     assert 1e5 + m0 * (R.u - S) == pytest.approx(ps + m1 * (us - S), rel=1e-10)
