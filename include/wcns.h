@@ -18,7 +18,9 @@
  *  - Pointers named W / dWdt are DEVICE pointers owned by the caller (for
  *    example torch CUDA tensors), 8-byte aligned.  The handle owns all
  *    scratch it needs, allocated once in wcns_create; rhs / step / advance
- *    calls allocate nothing.
+ *    calls allocate nothing (the one exception: the first
+ *    wcns_advance_steps_host call allocates the device copy of a host
+ *    state, which the handle then keeps).
  *  - Work is ordered on the stream set with wcns_set_options (default: the
  *    legacy default stream).  Calls returning host values synchronise that
  *    stream.
@@ -193,8 +195,10 @@ int wcns_advance_to(wcns_handle *h, double *W, double t0, double t_end, double c
                     double *t_out, long *steps_out);
 
 /* As wcns_advance_steps, but W_host is a HOST array (pageable or pinned):
- * it is copied to the handle's device state, advanced, and copied back,
- * all on the handle's stream.  Synchronises. */
+ * it is copied to a device state owned by the handle (allocated by the
+ * first call, 8 nf bytes a cell, freed by wcns_destroy), advanced, and
+ * copied back, all on the handle's stream.  Synchronises.  Returns
+ * WCNS_E_CUDA if that allocation fails. */
 int wcns_advance_steps_host(wcns_handle *h, double *W_host, int nsteps, double cfl,
                             double dt_fixed, double *t_io);
 
