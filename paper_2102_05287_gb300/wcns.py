@@ -330,6 +330,8 @@ class Batch:
     def advance(self, W, nsteps, cfl=0.5, t=None):
         if tuple(W.shape) != (5, self.total):
             raise ValueError("packed state must have shape (5, %d)" % self.total)
+        if t is not None and tuple(t.shape) != (self.nprob,):
+            raise ValueError("t must have shape (%d,): one time per problem" % self.nprob)
         tp = _ptr(t) if t is not None else None
         _check(self.lib.wcns_batch_advance(self.h, _ptr(W), int(nsteps), float(cfl), tp), "wcns_batch_advance")
         return W
