@@ -101,6 +101,12 @@ MUTANTS = [
      "Rinv[row * nf + 2 + d] = 1.0;", False),
     ("tau_d from the x wave speed", "tau[d] = smax[d] / spacing(c, d);", "tau[d] = smax[0] / spacing(c, d);",
      False),
+    ("cell index with the x extent as every stride", "idx = idx * c.n[d] + ijk[d];",
+     "idx = idx * c.n[0] + ijk[d];", False),
+    ("R tangential rows write the normal velocity", "R[(2 + j) * nf + row] = 1.0;",
+     "R[(2 + d) * nf + row] = 1.0;", False),
+    ("momentum fluxes all carry the normal momentum", "for (int j = 0; j < ndim; ++j) F[2 + j] = W[2 + j] * u;",
+     "for (int j = 0; j < ndim; ++j) F[2 + j] = W[2 + d] * u;", False),
     ("sign(0) = +1 in the HLLC flux (at s* = 0 both sides give the same flux)", "  if (x > 0.0) return 1.0;",
      "  if (x >= 0.0) return 1.0;", True),
 ]
@@ -150,6 +156,8 @@ def run_mutant(k):
         except subprocess.TimeoutExpired:
             return k, None, "timed out"
         failed = sorted(set(re.findall(r"FAILED \S*test_oracle_pins.py::(\w+)", r.stdout)))
+        if r.returncode != 0 and not failed:  # the oracle crashed the test process
+            failed = ["(pytest exited with status %d)" % r.returncode]
         lines = r.stdout.strip().splitlines()
         return k, failed, lines[-1] if lines else r.stderr[-200:]
     finally:
