@@ -122,3 +122,35 @@ def test_plain_c_program_uses_the_boundary(lib, tmp_path):
     exe = build_abi_consumer(build.LIB, tmp_path)
     r = subprocess.run([exe, "--checks"], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0, r.stdout + r.stderr
+
+
+def test_launch_grid_limits_are_refused_on_the_host(lib):
+    """The documented launch-grid limits of wcns_create (gridDim.y and
+    gridDim.z <= 65535: in 2D/3D n[0] <= 524,280 and n[1] <= 131,070, in 3D
+    also n[1], n[2] <= 65,535) and the cell-count cap are refused before any
+    allocation; sizes just inside pass the checks (and then fail only for
+    want of a GPU here)."""
+    from paper_2102_05287_gb300 import wcns
+    L = wcns.load()
+    E = wcns.WCNS_E_INVALID_ARG
+
+    def create(*n):
+        g = wcns.wcns_grid()
+        g.ndim = len(n)
+        for d, k in enumerate(n):
+            g.n[d] = k
+            g.lo[d], g.hi[d] = 0.0, 1.0
+        h = ctypes.c_void_p()
+        st = L.wcns_create(ctypes.byref(g), ctypes.byref(wcns.wcns_bcs()), 1.4, 4.4, 6e8, ctypes.byref(h))
+        if h.value:  # created (a machine with a GPU)
+            L.wcns_destroy(h)
+        return st
+
+    assert create(524281, 1) == E
+    assert create(16, 131071) == E
+    assert create(16, 65536, 2) == E
+    assert create(16, 2, 65536) == E
+    assert create(1 << 30 | 1) == E
+    assert create(65535, 65535, 300) == E  # beyond 2^40 cells
+    for ok in ((524280, 1), (16, 131070), (16, 65535, 65535)):
+        assert create(*ok) != E, ok
