@@ -1,13 +1,18 @@
 """Benchmark: cell-stage updates/s of the PP-WCNS-IS solver on one GB300.
 
-Workload: the 2D shock / air-bubble interaction in water on a 1024 x 512
-grid ([0,2] x [0,1], symmetry at y = 0, transmissive elsewhere), FP64, with
-SSPRK3 steps at CFL 0.5.  One bench step is one SSPRK3 step (three RHS
-evaluations, i.e. 3 x 524,288 cell-stage updates, all directions fused per
-stage).  Inputs are synthetic and seeded (paper_2102_05287_gb300.problems).
+Workload (the precision study): the 2D shock / air-bubble interaction in
+water on a 2048 x 1024 grid ([0,2] x [0,1], symmetry at y = 0, transmissive
+elsewhere, seed 2), SSPRK3 steps at CFL 0.5.  One bench step is one SSPRK3
+step (three RHS evaluations, i.e. 3 x 2,097,152 cell-stage updates, all
+directions fused per stage).  The headline value is the FP64 solver; the
+mixed FP32/FP64 solver is the variant.  Both precisions' first step from
+the initial state is compared with the FP64 oracle's step on the full grid
+(L1 / Linf in rho, p, alpha1); that oracle step is also the timed CPU
+baseline.  Inputs are synthetic and seeded (paper_2102_05287_gb300.problems).
 
 Arms:
-  default           this library (FP64 headline, mixed FP32/FP64 variant)
+  default           this library (FP64 headline, mixed FP32/FP64 variant,
+                    and both on the 1024 x 512 shock/bubble grid)
   --impl reference  the FP64 C++ oracle on the host cores (a deliberately
                     slow, plain reference; bounded sample of the same
                     workload)
@@ -15,16 +20,19 @@ Arms:
 Rooflines (the path has no dense contraction; it is ALU bound):
   roofline                  FP64 sweep: the oracle's op mix per cell and
                             direction (op-counting build, IS weights in their
-                            one-division form) over the live CUDA-event time
-                            of the dominant sweep, against the FP64 FMA peak
-                            measured live by csrc/peaks.cu
+                            one-division form; add, mul, min/max, division and
+                            square root one flop each) over the live
+                            CUDA-event time of the dominant sweep, against the
+                            FP64 FMA peak measured live by csrc/peaks.cu
   variants.mixed.roofline   mixed sweep: the FP64 steps (node EOS, node
                             fluxes, update) at the FP64 peak plus all other
                             steps at the FP32 peak
   --workload riemann_batch  step-level fractions of the batched mode
+  --workload bubble_3d      per-sweep fractions of the 3D solvers
 
-Other workloads (--workload): precision_2048, convergence, riemann_batch,
-bubble_3d, stress, full_runs; each prints its own JSON line.
+Other workloads (--workload): convergence, riemann_batch, bubble_3d, stress,
+full_runs, precision_2048 (the headline's workload with more error
+statistics); each prints its own JSON line.
 
 Multi-GPU (torchrun, one rank per GPU): independent replicas of the
 workload, one per rank (weak scaling; no data-path collective).  Rank 0
@@ -48,7 +56,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cell-stage updates/s per GB300 (FP64 vs mixed) at stated error; % of stencil roofline"
 UNIT = "cell-stage updates/s"
-WORKLOAD = "shock_bubble_2d_1024x512"
+WORKLOAD = "shock_bubble_2d_2048x1024"
+SEED = 2
 
 
 def parse():
@@ -57,8 +66,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--nx", type=int, default=1024)
-    ap.add_argument("--ny", type=int, default=512)
+    ap.add_argument("--nx", type=int, default=2048)
+    ap.add_argument("--ny", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--nprob", type=int, default=4096,
@@ -202,8 +211,9 @@ def _opcount_table(name):
 
 def algorithmic_ops(nx, ny):
     """Per-cell, per-direction operation mix of one RHS evaluation of the 2D
-    shock/bubble workload (measured on a 128 x 64 copy; the mix is per cell,
-    and the limiters idle on the initial state either way)."""
+    shock/bubble workload (measured on a 128 x 64 copy, the stored table;
+    the mix is per cell, and the limiters idle on the initial state of
+    every grid size)."""
     return _opcount_table("shock_bubble_2d")
 
 
@@ -242,21 +252,56 @@ def mixed_roofline(ops, peaks, avg_ms, ncell, fallbacks):
             "roofline_us": (t64 + t32) * 1e6, "roofline_us_overlapped": max(t64, t32) * 1e6,
             "avg_launch_ms": avg_ms, "fp64_fallbacks": fallbacks, "traffic": None,
             "note": "mixed sweep: FP64 steps %s at the measured FP64 FMA peak plus the other steps at the "
-                    "measured FP32 FMA peak, divisions and square roots as one flop, op mix per step from "
+                    "measured FP32 FMA peak, divisions and square roots as one flop (FP32 divisions and "
+                    "square roots run on the multi-function unit, whose measured rates are in the line's "
+                    "peaks: fp32_fdividef_gops, fp32_sqrt_gops), op mix per step from "
                     "the oracle's op-counting build (IS weights in one-division form); frac = roofline "
                     "time / CUDA-event time of one launch (of measured), from %d steps timed per kernel "
                     "right after the graph-replayed timed steps" % (MIXED_FP64_STEPS, PROFILE_STEPS_MIXED)}
 
 
+def fp64_roofline(ops, peaks, avg_ms, ncell, kernel):
+    """Roofline of one launch of an FP64 sweep (one direction over ncell
+    cells): the oracle's op mix per cell and direction, every add, mul,
+    min/max, division and square root one flop, over the launch time,
+    against the measured FP64 FMA peak.  frac_div_sqrt_weighted counts each
+    division and square root at its measured cost in FMA-flops instead."""
+    p64 = peaks.get("fp64_fma_tflops", 1.25)
+    div_eq = (p64 * 1e12) / (peaks.get("fp64_div_gops", 67.0) * 1e9)
+    sqrt_eq = (p64 * 1e12) / (peaks.get("fp64_sqrt_gops", 58.5) * 1e9)
+    plain = ops["add"] + ops["mul"] + ops["minmax"] + ops["div"] + ops["sqrt"]
+    weighted = ops["add"] + ops["mul"] + ops["minmax"] + div_eq * ops["div"] + sqrt_eq * ops["sqrt"]
+    t = avg_ms * 1e-3
+    achieved = plain * ncell / t / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": p64, "unit": "TFLOP/s", "frac": achieved / p64,
+            "traffic": None, "kernel": kernel, "avg_launch_ms": avg_ms,
+            "flops_per_cell_dir": plain,
+            "frac_div_sqrt_weighted": weighted * ncell / t / 1e12 / p64,
+            "flop_eq_per_cell_dir_div_sqrt_weighted": weighted,
+            "ops_per_cell_dir": {k: v for k, v in ops.items() if k != "per_step"},
+            "peak_source": peaks.get("source", "nominal FP64 1.25 TFLOP/s (fallback)"),
+            "note": "FP64-pipe roofline of the dominant sweep: algorithmic flops = the oracle's op mix per cell "
+                    "and direction (op-counting build, IS weights in their one-division form), add, mul, "
+                    "min/max, division and square root one flop each, x cells of one launch, over the launch's "
+                    "live CUDA-event time; peak = the FP64 FMA rate of this GPU measured live (of measured). "
+                    "frac_div_sqrt_weighted counts each division / square root at its measured cost in "
+                    "FMA-flops (%.1f / %.1f)" % (div_eq, sqrt_eq)}
+
+
 # ---------------------------------------------------------------------------
 # reference arm: the oracle on the host cores
 # ---------------------------------------------------------------------------
+def _cfl_dt(sm, pr):
+    """dt = CFL / sum_d (max(|u_d| + c) / dx_d), CFL 0.5 (Sec. 3.3)."""
+    return 0.5 / sum(sm[d] * pr.n[d] / (pr.hi[d] - pr.lo[d]) for d in range(pr.ndim))
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
     from oracle import Oracle
     from paper_2102_05287_gb300 import problems as P
-    pr = P.shock_bubble_2d(args.nx, args.ny)
+    pr = P.shock_bubble_2d(args.nx, args.ny, seed=SEED)
     o = Oracle(pr.n, pr.lo, pr.hi, pr.bcs, **pr.eos)
     W = pr.W
     for _ in range(min(args.warmup, 1)):
@@ -265,9 +310,7 @@ def run_reference(args, world, rank):
     steps = max(1, min(args.steps, 3))
     t0 = time.perf_counter()
     for _ in range(steps):
-        sm = o.max_wavespeed(W)
-        dt = 0.5 / (sm[0] * pr.n[0] / 2.0 + sm[1] * pr.n[1])
-        W = o.rk3_step(W, dt)
+        W = o.rk3_step(W, _cfl_dt(o.max_wavespeed(W), pr))
     el = time.perf_counter() - t0
     value = 3 * pr.ncells * steps / el
     line = {
@@ -275,9 +318,12 @@ def run_reference(args, world, rank):
         "steps": steps, "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * el / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": [pr.n[0], pr.n[1]], "precision": "fp64",
+        "config": {"workload": WORKLOAD if (args.nx, args.ny) == (2048, 1024) else
+                   "shock_bubble_2d_%dx%d" % (args.nx, args.ny),
+                   "grid": [pr.n[0], pr.n[1]], "precision": "fp64",
                    "step": "one SSPRK3 step (3 RHS evaluations)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(),
+                         "kind": "oracle",
                          "sample": "%d SSPRK3 steps of the full %dx%d workload, single thread" %
                                    (steps, pr.n[0], pr.n[1])},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -285,25 +331,19 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(nx, ny):
+def oracle_step(pr, dt):
+    """CPU baseline leg: one SSPRK3 step of the FP64 oracle on the full grid
+    from the initial state, single thread, timed.  Its result is also the
+    reference of the GPU's first-step errors."""
     from oracle import Oracle
-    from paper_2102_05287_gb300 import problems as P
-    pr = P.shock_bubble_2d(nx, ny)
     o = Oracle(pr.n, pr.lo, pr.hi, pr.bcs, **pr.eos)
-    W = pr.W
-    steps = 0
     t0 = time.perf_counter()
-    while True:
-        sm = o.max_wavespeed(W)
-        dt = 0.5 / (sm[0] * pr.n[0] / 2.0 + sm[1] * pr.n[1])
-        W = o.rk3_step(W, dt)
-        steps += 1
-        el = time.perf_counter() - t0
-        if el > 10.0 or steps >= 5:
-            break
-    return {"value": 3 * pr.ncells * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d SSPRK3 steps of the full %dx%d workload, single thread, %.1f s" %
-                      (steps, pr.n[0], pr.n[1], el)}
+    W1 = o.rk3_step(pr.W, dt)
+    el = time.perf_counter() - t0
+    cpu = {"value": 3 * pr.ncells / el, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
+           "sample": "one SSPRK3 step of the full %dx%d workload from its initial state, single thread "
+                     "(the oracle is not threaded), %.1f s" % (pr.n[0], pr.n[1], el)}
+    return cpu, W1
 
 
 # ---------------------------------------------------------------------------
@@ -327,6 +367,23 @@ def timed_steps(torch, solver, W, steps, flush):
     return times, solver.launches() - launches0
 
 
+def kernel_time(torch, solver, W, flush, steps):
+    """Per-direction launch count and summed CUDA-event time of the sweeps
+    over `steps` steps, taken right after the graph-replayed timed steps
+    (per-kernel events make every launch direct)."""
+    solver.profile_enable(16 * steps + 16)
+    solver.profile_read()
+    timed_steps(torch, solver, W, steps, flush)
+    prof = solver.profile_read()
+    solver.profile_enable(0)
+    return prof
+
+
+def dominant(prof, ndim):
+    d = max((d for d in range(ndim) if prof["launches"][d] > 0), key=lambda d: prof["ms"][d])
+    return d, prof["ms"][d] / prof["launches"][d]
+
+
 def run_gb300(args, world, rank, local):
     import numpy as np
     import torch
@@ -335,19 +392,21 @@ def run_gb300(args, world, rank, local):
     from paper_2102_05287_gb300.wcns import Solver
 
     torch.cuda.set_device(local)
-    pr = P.shock_bubble_2d(args.nx, args.ny, seed=1 + rank)
+    pr = P.shock_bubble_2d(args.nx, args.ny, seed=SEED + rank)
     ncell = pr.ncells
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    # ---------------- FP64 (the workload's precision) -----------------------
+    # ---------------- FP64 (the headline) ----------------------------------
     s64 = Solver(pr.n, pr.lo, pr.hi, pr.bcs, precision="fp64", stream=stream, **pr.eos)
     W64 = torch.from_numpy(pr.W).cuda()
+    # the first step from the initial state, at the dt both precisions and
+    # the oracle take, for the error report
+    dt1 = _cfl_dt(s64.max_wavespeed(W64), pr)
+    first = {"fp64": s64.rk3_step(W64.clone(), dt1)}
     for _ in range(args.warmup):
         s64.advance_steps(W64, 1, cfl=0.5)
     torch.cuda.synchronize()
-    s64.profile_enable(16 * args.steps + 16)
-    s64.profile_read()
     barrier(world)
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
@@ -356,10 +415,10 @@ def run_gb300(args, world, rank, local):
     torch.cuda.synchronize()
     barrier(world)
     wall = time.perf_counter() - wall0
-    prof = s64.profile_read()
     clocks = clk.summary()
     ms64 = barrier_and_max(world, sum(times64)) / args.steps
     value = world * 3 * ncell / (ms64 * 1e-3)
+    prof64 = kernel_time(torch, s64, W64, flush, 3)
     stats64 = s64.stats()
 
     # ---------------- mixed FP32/FP64 variant -------------------------------
@@ -367,30 +426,17 @@ def run_gb300(args, world, rank, local):
     if not args.no_mixed:
         sm_ = Solver(pr.n, pr.lo, pr.hi, pr.bcs, precision="mixed", stream=stream, **pr.eos)
         Wm = torch.from_numpy(pr.W).cuda()
+        first["mixed"] = sm_.rk3_step(Wm.clone(), dt1)
         for _ in range(args.warmup):
             sm_.advance_steps(Wm, 1, cfl=0.5)
         torch.cuda.synchronize()
         tm, _ = timed_steps(torch, sm_, Wm, args.steps, flush)
         msm = barrier_and_max(world, sum(tm)) / args.steps
-        # error of the mixed run against the FP64 run after the same steps
-        a, b = Wm.double(), W64
-        rho_m, rho_d = a[0] + a[1], b[0] + b[1]
-        l1 = lambda x, y: float((x - y).abs().sum() / y.abs().sum())
-        linf = lambda x, y: float((x - y).abs().max() / y.abs().max())
-        mixed = {"value": world * 3 * ncell / (msm * 1e-3), "ms_per_step": msm,
-                 "speedup_vs_fp64": ms64 / msm,
-                 "error_vs_fp64_after_steps": {
-                     "steps": args.warmup + args.steps,
-                     "l1_rel": {"rho": l1(rho_m, rho_d), "E": l1(a[4], b[4]), "alpha1": l1(a[5], b[5])},
-                     "linf_rel": {"rho": linf(rho_m, rho_d), "E": linf(a[4], b[4]), "alpha1": linf(a[5], b[5])}},
+        mixed = {"value": world * 3 * ncell / (msm * 1e-3), "ms_per_step": msm, "speedup_vs_fp64": ms64 / msm,
+                 "error_vs_fp64_gpu_after_steps": dict(steps=args.warmup + args.steps,
+                                                       **_errors(Wm.cpu(), W64.cpu(), pr.eos, 2)),
                  "stats": sm_.stats()}
-        # per-kernel durations from a separate pass right after the timed
-        # steps: per-kernel events make every launch direct (no graph
-        # replay), which would slow the timed mixed steps by a few percent
-        sm_.profile_enable(16 * PROFILE_STEPS_MIXED + 16)
-        sm_.profile_read()
-        timed_steps(torch, sm_, Wm, PROFILE_STEPS_MIXED, flush)
-        mixed["profile"] = sm_.profile_read()
+        mixed["profile"] = kernel_time(torch, sm_, Wm, flush, PROFILE_STEPS_MIXED)
         sm_.close()
 
     # ---------------- end to end through the host-buffer entry point --------
@@ -407,61 +453,68 @@ def run_gb300(args, world, rank, local):
            "d2h_bytes_per_step": nbytes, "steps": e2e_steps,
            "note": "wcns_advance_steps_host: pinned host state copied in, one SSPRK3 step, copied out"}
 
+    # ---------------- the 1024 x 512 shock/bubble grid ------------------------
+    small = {}
+    if rank == 0 and (args.nx, args.ny) != (1024, 512):
+        pc = P.shock_bubble_2d(1024, 512, seed=1)
+        for prec in ("fp64", "mixed"):
+            sc = Solver(pc.n, pc.lo, pc.hi, pc.bcs, precision=prec, stream=stream, **pc.eos)
+            Wc = torch.from_numpy(pc.W).cuda()
+            for _ in range(args.warmup):
+                sc.advance_steps(Wc, 1, cfl=0.5)
+            tc, _ = timed_steps(torch, sc, Wc, max(3, min(args.steps, 10)), flush)
+            msc = sum(tc) / len(tc)
+            small[prec] = {"value": 3 * pc.ncells / (msc * 1e-3), "ms_per_step": msc, "steps": len(tc)}
+            sc.close()
+
     if rank != 0:
         s64.close()
         return
 
-    # ---------------- roofline of the dominant kernel -----------------------
+    # ---------------- CPU baseline and first-step errors vs the oracle -------
+    cpu, W_or = (None, None) if args.no_cpu_baseline else oracle_step(pr, dt1)
+    if W_or is not None:
+        ref = torch.from_numpy(W_or)
+        errs = {prec: _errors(first[prec].cpu(), ref, pr.eos, 2) for prec in first}
+    else:
+        errs = None
+
+    # ---------------- rooflines of the dominant kernels ----------------------
     peaks = load_peaks()
     ops = algorithmic_ops(args.nx, args.ny)
-    dirs = [d for d in range(2) if prof["launches"][d] > 0]
-    dom = max(dirs, key=lambda d: prof["ms"][d])
-    avg_ms = prof["ms"][dom] / prof["launches"][dom]
-    p64 = peaks.get("fp64_fma_tflops", 1.25)
-    div_eq = (p64 * 1e12) / (peaks.get("fp64_div_gops", 67.0) * 1e9)
-    sqrt_eq = (p64 * 1e12) / (peaks.get("fp64_sqrt_gops", 58.5) * 1e9)
-    flop_eq = ops["add"] + ops["mul"] + ops["minmax"] + div_eq * ops["div"] + sqrt_eq * ops["sqrt"]
+    dom, avg_ms = dominant(prof64, 2)
+    roofline = fp64_roofline(ops, peaks, avg_ms, ncell, "sweep_kernel<2,%d,double> (%s sweep)" % (dom, "xy"[dom]))
     src_hash = hashlib.sha256(open(os.path.join(ROOT, "paper_2102_05287_gb300", "csrc", "wcns_sweep.cuh"),
                                    "rb").read()).hexdigest()[:16]
-    achieved = flop_eq * ncell / (avg_ms * 1e-3) / 1e12
-    plain = ops["add"] + ops["mul"] + ops["minmax"] + ops["div"] + ops["sqrt"]
-    roofline = {"bound": "alu", "achieved": achieved, "peak": p64, "unit": "TFLOP/s", "frac": achieved / p64,
-                "traffic": None,
-                "frac_div_sqrt_as_one_flop": plain * ncell / (avg_ms * 1e-3) / 1e12 / p64,
-                "kernel": "sweep_kernel<2,%d,double> (%s sweep)" % (dom, "xy"[dom]),
-                "avg_launch_ms": avg_ms,
-                "flop_eq_per_cell_dir": flop_eq,
-                "ops_per_cell_dir": {k: v for k, v in ops.items() if k != "per_step"},
-                "peak_source": peaks.get("source", "nominal FP64 1.25 TFLOP/s (fallback)"),
-                "note": "FP64-pipe roofline: add/mul/minmax count 1 flop, div/sqrt count their measured "
-                        "cost in FMA-flop equivalents; op mix from the oracle's op-counting build with the "
-                        "IS weights counted in their one-division form; peak = measured FP64 FMA rate of "
-                        "this GPU (of measured). frac_div_sqrt_as_one_flop counts every division and square "
-                        "root as a single flop instead (a lower bound on the fraction)."}
     traffic_file = os.path.join(ROOT, "profiles", "sweep_traffic.json")
     if os.path.exists(traffic_file):
         try:
             tr = json.load(open(traffic_file))
             k = "fp64_dir%d" % dom
-            # only counters taken on the current kernel source count
-            if (tr.get("kernel_source_sha256_16") == src_hash and k in tr
-                    and tr[k].get("grid") == [args.nx, args.ny]):
-                roofline["traffic"] = tr[k]["bytes_per_launch"]
+            # only counters taken on the current kernel source count; a
+            # capture on a smaller grid is scaled by the cells of one launch
+            if tr.get("kernel_source_sha256_16") == src_hash and k in tr:
+                g = tr[k]["grid"]
+                roofline["traffic"] = tr[k]["bytes_per_launch"] * ncell / float(g[0] * g[1])
+                roofline["traffic_source"] = "ncu dram bytes of a %dx%d capture, scaled to %d cells" % (
+                    g[0], g[1], ncell)
         except Exception:
             pass
     roofline["ops_per_step_per_cell_dir"] = ops["per_step"]
     if mixed:
         pm = mixed.pop("profile")
-        dm = max((d for d in range(2) if pm["launches"][d] > 0), key=lambda d: pm["ms"][d])
-        mixed["roofline"] = mixed_roofline(ops, peaks, pm["ms"][dm] / pm["launches"][dm], ncell,
-                                           mixed["stats"]["fp64_fallbacks"])
+        dm, avg_m = dominant(pm, 2)
+        mixed["roofline"] = mixed_roofline(ops, peaks, avg_m, ncell, mixed["stats"]["fp64_fallbacks"])
         mixed["roofline"]["kernel"] = "sweep_kernel_mixed<2,%d> (%s sweep)" % (dm, "xy"[dm])
-    cpu = None if args.no_cpu_baseline else cpu_baseline(args.nx, args.ny)
+        if errs:
+            mixed["first_step_error_vs_fp64_oracle"] = errs["mixed"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": [args.nx, args.ny], "cells": ncell, "precision": "fp64",
+        "config": {"workload": WORKLOAD if (args.nx, args.ny) == (2048, 1024) else
+                   "shock_bubble_2d_%dx%d" % (args.nx, args.ny),
+                   "grid": [args.nx, args.ny], "cells": ncell, "precision": "fp64", "seed": SEED,
                    "scheme": "PP-WCNS-IS + SSPRK3, CFL 0.5",
                    "step": "one SSPRK3 step = 3 RHS evaluations (x and y sweeps fused with the stage combine)",
                    "l2": "flushed between timed steps (256 MiB write outside the timed events)",
@@ -472,10 +525,14 @@ def run_gb300(args, world, rank, local):
         "gpu_launches": launches,
         "clocks": clocks,
         "wall_s_timed_region": wall,
-        "variants": {"mixed": mixed} if mixed else {},
+        "first_step_error_vs_fp64_oracle": errs["fp64"] if errs else None,
+        "variants": dict({"mixed": mixed} if mixed else {},
+                         **({"shock_bubble_2d_1024x512": small} if small else {})),
         "stats_fp64": stats64,
         "peaks": {k: peaks.get(k) for k in ("fp64_fma_tflops", "fp32_fma_tflops", "fp64_div_gops",
-                                           "fp64_sqrt_gops", "fp64_copy_gbs", "device")},
+                                           "fp64_sqrt_gops", "fp32_div_gops", "fp32_fdividef_gops",
+                                           "fp32_sqrt_gops",
+                                           "fp64_copy_gbs", "device")},
     }
     print(json.dumps(line), flush=True)
     s64.close()
@@ -547,7 +604,7 @@ def workload_precision(args):
     ref = o.rk3_step(pr.W, 0.5 / (sm[0] * pr.n[0] / 2.0 + sm[1] * pr.n[1]))
     t_or = time.perf_counter() - t0
     ref = torch.from_numpy(ref)
-    cpu = {"value": 3 * pr.ncells / t_or, "unit": UNIT, "cores": 1, "kind": "oracle",
+    cpu = {"value": 3 * pr.ncells / t_or, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
            "sample": "one SSPRK3 step of the full 2048x1024 grid, single thread, %.1f s" % t_or}
     line = {"workload": "precision_2048x1024", "metric": METRIC, "unit": UNIT,
             "steps": args.steps, "warmup": args.warmup, "results": res,
@@ -613,28 +670,17 @@ def algorithmic_ops_1d(rb=None):
 
 def batch_roofline(ops, peaks, prec, ms_per_step, cells):
     """Step-level roofline fraction of the batched mode: the algorithmic
-    work of three RHS evaluations over all cells at the FP64 pipe's measured
-    rate (FP64: divisions and square roots at their measured cost) or at the
-    two pipes' rates (mixed, as mixed_roofline), over the whole step's time
-    (the per-problem dt kernel included)."""
+    work of three RHS evaluations over all cells (every add, mul, min/max,
+    division and square root one flop) at the FP64 pipe's measured rate
+    (FP64) or at the two pipes' rates (mixed, as mixed_roofline), over the
+    whole step's time (the per-problem dt kernel included)."""
     if prec == "mixed":
         r = mixed_roofline(ops, peaks, ms_per_step / 3.0, cells, fallbacks=None)
         r["note"] = "batched mixed step: " + r["note"] + "; time = one third of the step"
         return r
-    p64 = peaks.get("fp64_fma_tflops", 1.25)
-    div_eq = (p64 * 1e12) / (peaks.get("fp64_div_gops", 67.0) * 1e9)
-    sqrt_eq = (p64 * 1e12) / (peaks.get("fp64_sqrt_gops", 58.5) * 1e9)
-    flop_eq = ops["add"] + ops["mul"] + ops["minmax"] + div_eq * ops["div"] + sqrt_eq * ops["sqrt"]
-    achieved = flop_eq * 3 * cells / (ms_per_step * 1e-3) / 1e12
-    plain = ops["add"] + ops["mul"] + ops["minmax"] + ops["div"] + ops["sqrt"]
-    return {"bound": "alu", "achieved": achieved, "peak": p64, "unit": "TFLOP/s", "frac": achieved / p64,
-            "frac_div_sqrt_as_one_flop": plain * 3 * cells / (ms_per_step * 1e-3) / 1e12 / p64,
-            "flop_eq_per_cell_stage": flop_eq,
-            "note": "batched FP64 step: the oracle's 1D op mix (IS weights in one-division form, divisions "
-                    "and square roots at their measured cost) over three stages of all cells, over the whole "
-                    "step time (of measured); frac_div_sqrt_as_one_flop counts each division and square "
-                    "root as one flop (a lower bound). The kernel computes fewer divisions than the "
-                    "oracle's printed formulas (shared reciprocals), so the weighted count can reach 1"}
+    r = fp64_roofline(ops, peaks, ms_per_step / 3.0, cells, "batch_sweep_kernel<false, ...> (one stage)")
+    r["note"] = "batched FP64 step, time = one third of the step (dt kernel included): " + r["note"]
+    return r
 
 
 def workload_batch(args):
@@ -685,7 +731,7 @@ def workload_batch(args):
         o.rk3_step(W0, 0.5 / (o.max_wavespeed(W0)[0] * n))
         cells += n
     el = time.perf_counter() - t0
-    cpu = {"value": 3 * cells / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+    cpu = {"value": 3 * cells / el, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
            "sample": "one SSPRK3 step of 32 seeded problems of the batch (%d cells), single thread, %.1f s"
                      % (cells, el)}
     print(json.dumps({"workload": "riemann_batch_%d" % len(rb.sizes), "problems": len(rb.sizes), "cells": total,
@@ -696,11 +742,17 @@ def workload_batch(args):
 
 def workload_3d(args):
     """3D air-bubble collapse in water, 384^3, 7 fields SoA: mixed (the
-    workload's precision) and FP64, a few SSPRK3 steps each."""
+    workload's precision) and FP64, a few SSPRK3 steps each, then two more
+    with per-sweep CUDA events for the rooflines of the x, y and z sweeps
+    (FP64: the oracle's 3D op mix at the FP64 peak; mixed: the two-pipe
+    roofline)."""
     import torch
     from paper_2102_05287_gb300 import problems as P
     from paper_2102_05287_gb300.wcns import Solver
     pr = P.bubble_collapse_3d(384)
+    ops = _opcount_table("bubble_collapse_3d")
+    peaks = load_peaks()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     res, states = {}, {}
     for prec in ("mixed", "fp64"):
         s = Solver(pr.n, pr.lo, pr.hi, pr.bcs, precision=prec, **pr.eos)
@@ -714,8 +766,25 @@ def workload_3d(args):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / k
+        prof = kernel_time(torch, s, W, flush, 2)
+        sweeps = {}
+        for d in range(3):
+            avg = prof["ms"][d] / max(prof["launches"][d], 1)
+            if prec == "fp64":
+                r = fp64_roofline(ops, peaks, avg, pr.ncells, "sweep_kernel<3,%d,double>" % d)
+            else:
+                r = mixed_roofline(ops, peaks, avg, pr.ncells, fallbacks=None)
+                r["kernel"] = "sweep_kernel_mixed<3,%d>" % d
+            sweeps["xyz"[d]] = {"avg_launch_ms": avg, "frac": r["frac"]}
+        dom, avg_dom = dominant(prof, 3)
+        if prec == "fp64":
+            roof = fp64_roofline(ops, peaks, avg_dom, pr.ncells, "sweep_kernel<3,%d,double>" % dom)
+        else:
+            roof = mixed_roofline(ops, peaks, avg_dom, pr.ncells, fallbacks=None)
+            roof["kernel"] = "sweep_kernel_mixed<3,%d>" % dom
+        roof.pop("ops_per_cell_dir", None)
         res[prec] = {"ms_per_step": ms, "steps": k, "cell_stage_updates_per_s": 3 * pr.ncells / (ms * 1e-3),
-                     "stats": s.stats()}
+                     "stats": s.stats(), "roofline": roof, "sweeps": sweeps}
         states[prec] = W.cpu()
         del W
         s.close()
@@ -731,7 +800,8 @@ def workload_3d(args):
     sm = o.max_wavespeed(small.W)
     o.rk3_step(small.W, 0.5 / (sum(sm) * 48))
     el = time.perf_counter() - t0
-    cpu = {"value": 3 * small.ncells / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+    cpu = {"value": 3 * small.ncells / el, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(),
+           "kind": "oracle",
            "sample": "one SSPRK3 step of the same problem at 48^3 (single thread, %.1f s), "
                      "rate extrapolated to 384^3" % el}
     print(json.dumps({"workload": "bubble_collapse_3d_384", "cells": pr.ncells, "results": res,
@@ -799,13 +869,16 @@ def workload_stress(args):
         s = Solver(pr.n, pr.lo, pr.hi, pr.bcs, scheme="wcns-is", **pr.eos, **kw)
         W = torch.from_numpy(pr.W).cuda()
         failed_at = None
+        from paper_2102_05287_gb300.wcns import WcnsError
         for k in range(nsteps):
-            s.advance_steps(W, 1, cfl=0.5)
-            st = s.stats()
-            if st["inadmissible"] or st["nonfinite"]:
-                failed_at = k  # the state after step k was flagged when step k + 1 read it
+            try:
+                s.advance_steps(W, 1, cfl=0.5)
+            except WcnsError as e:  # WCNS_E_INADMISSIBLE or WCNS_E_NONFINITE
+                failed_at = k  # steps completed before the one whose call reported it
+                failed_status = e.status
                 break
-        row["unlimited_wcns_is"] = {"flagged_after_steps": failed_at, "stats": s.stats()}
+        row["unlimited_wcns_is"] = {"flagged_after_steps": failed_at,
+                                    "status": failed_status if failed_at is not None else 0, "stats": s.stats()}
         s.close()
         out.append(row)
     print(json.dumps({"workload": "stress_section6", "results": out}), flush=True)

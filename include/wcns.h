@@ -28,6 +28,15 @@
  *    nothing throws or aborts.  wcns_strerror gives a message.  Device-side
  *    problems (non-finite values, inadmissible input, limiter hard switches)
  *    are counted in the handle's statistics (wcns_get_stats), never trapped.
+ *    The calls that synchronise at their end (wcns_advance_steps,
+ *    wcns_advance_to, wcns_advance_steps_host, wcns_batch_advance) also read
+ *    those counters back and return WCNS_E_NONFINITE when an update of
+ *    theirs was not finite, else WCNS_E_INADMISSIBLE when a stage input
+ *    state (the initial state included) had a cell outside G: a negative
+ *    partial density, alpha1 outside [0, 1], rho ctilde^2 <= 0 or a
+ *    non-finite value (Sec. 2).  The state is left as the device computed
+ *    it; the kernels always run to completion.  Asynchronous calls
+ *    (wcns_rhs, wcns_rk3_step, wcns_rk3_step_noalloc) only count.
  */
 #ifndef WCNS_H
 #define WCNS_H
@@ -45,9 +54,9 @@ enum {
   WCNS_OK = 0,
   WCNS_E_INVALID_ARG = 1,   /* bad argument (null pointer, size, parameter) */
   WCNS_E_CUDA = 2,          /* a CUDA runtime call failed */
-  WCNS_E_INADMISSIBLE = 3,  /* input state outside the admissible set G (Sec. 2) */
+  WCNS_E_INADMISSIBLE = 3,  /* a stage input state outside the admissible set G (Sec. 2) */
   WCNS_E_NONFINITE = 4,     /* a non-finite value appeared */
-  WCNS_E_TIMEOUT = 5,       /* a bounded device wait gave up */
+                            /* 5 is not used: no call waits on the device with a time limit */
   WCNS_E_UNSUPPORTED = 6,   /* option combination not provided */
   WCNS_E_TOO_LARGE = 7      /* problem exceeds the fixed no-allocation scratch */
 };
@@ -177,20 +186,24 @@ int wcns_set_stage_trace(wcns_handle *h, double *W1_out, double *W2_out);
 /* Advance W in place by nsteps SSPRK3 steps.  With dt_fixed > 0 every step
  * uses dt_fixed; otherwise dt = cfl / sum_d tau_d from the state at the
  * start of each step (Sec. 3.3), computed and kept on the device.
- * *t_io (host) holds the start time on entry and the final time on exit.
- * One step (dt kernel and all sweeps) is captured once into a CUDA graph
- * per (W, dt_fixed, cfl) and replayed on the handle's private stream,
- * ordered after the caller's pending work; per-kernel timing disables the
- * graph.  Synchronises once at the end. */
+ * *t_io (host, may be NULL) holds the start time on entry and the final
+ * time on exit.  One step (dt kernel and all sweeps) is captured once into
+ * a CUDA graph per (W, dt_fixed, cfl) and replayed on the handle's private
+ * stream, ordered after the caller's pending work; per-kernel timing
+ * disables the graph.  Synchronises once at the end and returns
+ * WCNS_E_NONFINITE / WCNS_E_INADMISSIBLE as described at the top (all
+ * nsteps steps are taken either way). */
 int wcns_advance_steps(wcns_handle *h, double *W, int nsteps, double cfl, double dt_fixed,
                        double *t_io);
 
 /* Advance W in place from t0 to t_end with CFL-limited steps (dt as above,
  * the last step clipped to land on t_end).  Returns the end time and the
  * number of steps taken in the host outputs (either may be NULL).  The host
- * checks the device step control every 8-256 steps: a non-finite time step
- * (a state whose wave speed is not finite) ends the call with
- * WCNS_E_NONFINITE, W holding the state of that moment. */
+ * checks the device step control and counters every 8-256 steps: a
+ * non-finite time step (a state whose wave speed is not finite) or a
+ * non-finite update ends the call with WCNS_E_NONFINITE, an inadmissible
+ * stage input with WCNS_E_INADMISSIBLE, W holding the state of that moment
+ * and the outputs the time and steps reached. */
 int wcns_advance_to(wcns_handle *h, double *W, double t0, double t_end, double cfl,
                     double *t_out, long *steps_out);
 
@@ -198,7 +211,8 @@ int wcns_advance_to(wcns_handle *h, double *W, double t0, double t_end, double c
  * it is copied to a device state owned by the handle (allocated by the
  * first call, 8 nf bytes a cell, freed by wcns_destroy), advanced, and
  * copied back, all on the handle's stream.  Synchronises.  Returns
- * WCNS_E_CUDA if that allocation fails. */
+ * WCNS_E_CUDA if that allocation fails; the state is copied back also when
+ * the steps return WCNS_E_NONFINITE or WCNS_E_INADMISSIBLE. */
 int wcns_advance_steps_host(wcns_handle *h, double *W_host, int nsteps, double cfl,
                             double dt_fixed, double *t_io);
 
@@ -215,13 +229,14 @@ long long wcns_ncells(const wcns_handle *h);
 long long wcns_launch_count(const wcns_handle *h);
 
 /* One SSPRK3 step that allocates nothing (the paper has no counterpart:
- * this is a deployment aid).  Some callers cannot call cudaMalloc: code
- * that runs while a CUDA graph is being captured, real-time loops where an
- * allocation would synchronise the device, and hosts that hand a plugin a
- * fixed device-memory budget and forbid it to allocate more.  This entry
- * point takes the grid, boundary set, fluids and options directly (no
- * handle) and advances the caller's device array W in place by one step
- * of size dt, exactly like wcns_rk3_step.  Its scratch (two stage states,
+ * this is a deployment aid).  Some callers cannot call cudaMalloc:
+ * real-time loops, where an allocation can synchronise the whole device and
+ * break the loop's deadline; host applications that hand a plugin a fixed
+ * device-memory budget and forbid it to allocate more; and code that must
+ * not create per-solver state at all (no handle to keep, no scratch to
+ * free).  This entry point takes the grid, boundary set, fluids and
+ * options directly (no handle) and advances the caller's device array W in
+ * place by one step of size dt, exactly like wcns_rk3_step.  Its scratch (two stage states,
  * the RHS accumulator, the node cache in 2D/3D, step control and counters)
  * lives in one file-scope device array of WCNS_NOALLOC_MAX_DOUBLES doubles
  * (64 MiB) that every GPU loading the library holds until the process
@@ -236,7 +251,8 @@ long long wcns_launch_count(const wcns_handle *h);
  * the rest is overwritten before it is read.  Calls whose work overlaps on
  * the GPU (other streams, other host threads) race on the array and must
  * be serialised by the caller.  opt may be NULL (defaults).  Asynchronous
- * on opt->stream. */
+ * on opt->stream: no host memory is read by the device and nothing is
+ * waited for (uniform Dirichlet states travel as kernel arguments). */
 #define WCNS_NOALLOC_MAX_DOUBLES (8ll * 1024 * 1024)
 int wcns_rk3_step_noalloc(const wcns_grid *grid, const wcns_bcs *bcs, double gamma_g, double gamma_l,
                           double pinf_l, const wcns_options *opt, double *W, double dt);
@@ -286,8 +302,10 @@ int wcns_batch_set_options(wcns_batch *b, const wcns_options *opt);
  * and the persistent grid (1, 2, 4 or 8 blocks per SM) by timing trial
  * steps on the tuning copy; make it before any stream capture of the
  * caller's.  t_out: optional DEVICE array of nprob doubles; each problem's
- * step sizes are added to it.  Asynchronous: ordered after the caller's
- * pending work on the options' stream, and that stream waits for it. */
+ * step sizes are added to it.  Ordered after the caller's pending work on
+ * the options' stream, and that stream waits for it; synchronises once at
+ * the end and returns WCNS_E_NONFINITE / WCNS_E_INADMISSIBLE as described
+ * at the top (every problem takes all nsteps steps either way). */
 int wcns_batch_advance(wcns_batch *b, double *W_packed, int nsteps, double cfl, double *t_out);
 /* The autotuner's choice: cells per tile and persistent grid size;
  * WCNS_E_UNSUPPORTED before the first advance. */

@@ -8,11 +8,14 @@ requires the stored one to match.  Run from the repository root:
 
     python -m oracle.opcount_table
 
-Two tables:
-  shock_bubble_2d   the 2D shock / air-bubble workload on a 128 x 64 copy
-                    (1/8 of the benchmark grid), one RHS at its CFL-0.5 dt;
-  riemann_batch     16 seeded problems of the 4096-problem Riemann batch,
-                    one RHS each at its CFL-0.5 dt, summed over their cells.
+Three tables:
+  shock_bubble_2d     the 2D shock / air-bubble workload on a 128 x 64 copy
+                      (the benchmark grids are 1024 x 512 and 2048 x 1024;
+                      the mix is per cell), one RHS at its CFL-0.5 dt;
+  riemann_batch       16 seeded problems of the 4096-problem Riemann batch,
+                      one RHS each at its CFL-0.5 dt, summed over their cells;
+  bubble_collapse_3d  the 3D bubble collapse on a 24^3 copy (the workload is
+                      384^3), one RHS at its CFL-0.5 dt.
 The IS weights are counted in their one-division form (Sec. 4.3): the
 oracle forms them with five ratio divisions and four normalising divisions
 as printed; scaling every eta_k by the product of the five (beta + eps)
@@ -58,6 +61,20 @@ def shock_bubble_2d(nx=128, ny=64):
     return _table(per_step, is_calls, "shock_bubble_2d %dx%d, one RHS at CFL 0.5" % (nx, ny))
 
 
+def bubble_collapse_3d(n=24):
+    pr = P.bubble_collapse_3d(n)
+    o = Oracle(pr.n, pr.lo, pr.hi, pr.bcs, counting=True, **pr.eos)
+    sm = o.max_wavespeed(pr.W)
+    dt = 0.5 / sum(sm[d] * pr.n[d] / (pr.hi[d] - pr.lo[d]) for d in range(3))
+    o.opcount_reset()
+    o.rhs(pr.W, dt)
+    units = pr.ncells * pr.ndim
+    per_step = {r: {k: v / units for k, v in c.items()} for r, c in o.opcount_rows().items()}
+    is_calls = 2 * (pr.ndim + 4) * o.stats.midpoints / units
+    _one_division_form(per_step, is_calls)
+    return _table(per_step, is_calls, "bubble_collapse_3d %d^3, one RHS at CFL 0.5" % n)
+
+
 def riemann_batch(nsample=16):
     rb = P.riemann_batch()
     picks = np.random.default_rng(1).choice(len(rb.sizes), nsample, replace=False)
@@ -83,7 +100,8 @@ def riemann_batch(nsample=16):
 
 
 def compute_tables():
-    return {"shock_bubble_2d": shock_bubble_2d(), "riemann_batch": riemann_batch()}
+    return {"shock_bubble_2d": shock_bubble_2d(), "riemann_batch": riemann_batch(),
+            "bubble_collapse_3d": bubble_collapse_3d()}
 
 
 def main():

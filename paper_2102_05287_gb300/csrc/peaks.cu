@@ -7,6 +7,8 @@
 //   * FP32 FMA throughput
 //   * FP64 division and square-root throughput (operations/s; these are
 //     multi-instruction sequences, reported as ops, not flops)
+//   * FP32 division (IEEE a / b and the approximate __fdividef) and sqrtf
+//     throughput, the forms the mixed-precision sweeps use
 //   * a STREAM-style FP64 copy bandwidth
 // and prints one JSON object.  Timing uses CUDA events after warm-up.
 //
@@ -64,6 +66,37 @@ __global__ void sqrt_chain(double *out, int iters) {
   if (s == -12345.678) out[blockIdx.x] = s;
 }
 
+// FP32 division chains: IEEE-rounded a / b (FAST = false) or __fdividef.
+template <int NCHAIN, bool FAST>
+__global__ void div32_chain(float *out, int iters, float b) {
+  float acc[NCHAIN];
+#pragma unroll
+  for (int c = 0; c < NCHAIN; ++c) acc[c] = 1.0f + (threadIdx.x + c) * 1e-3f;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < NCHAIN; ++c) acc[c] = FAST ? __fdividef(b, acc[c]) : b / acc[c];
+  }
+  float s = 0;
+#pragma unroll
+  for (int c = 0; c < NCHAIN; ++c) s += acc[c];
+  if (s == -12345.678f) out[blockIdx.x] = s;
+}
+
+template <int NCHAIN>
+__global__ void sqrt32_chain(float *out, int iters) {
+  float acc[NCHAIN];
+#pragma unroll
+  for (int c = 0; c < NCHAIN; ++c) acc[c] = 2.0f + (threadIdx.x + c) * 1e-3f;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < NCHAIN; ++c) acc[c] = sqrtf(acc[c]) + 1.0f;
+  }
+  float s = 0;
+#pragma unroll
+  for (int c = 0; c < NCHAIN; ++c) s += acc[c];
+  if (s == -12345.678f) out[blockIdx.x] = s;
+}
+
 __global__ void copy_kernel(const double2 *__restrict__ src, double2 *__restrict__ dst, size_t n) {
   size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = src[i];
@@ -113,6 +146,14 @@ int main() {
   float mss = time_ms([&] { sqrt_chain<4><<<blocks, threads>>>(out, its); }, 3);
   double sqrt_gops = nthreads * its * 4 / (mss * 1e-3) / 1e9;
 
+  const int it32d = 4096;
+  float msd32 = time_ms([&] { div32_chain<8, false><<<blocks, threads>>>((float *)out, it32d, 1.5f); }, 3);
+  double div32_gops = nthreads * it32d * 8 / (msd32 * 1e-3) / 1e9;
+  float msf32 = time_ms([&] { div32_chain<8, true><<<blocks, threads>>>((float *)out, it32d, 1.5f); }, 3);
+  double fdiv32_gops = nthreads * it32d * 8 / (msf32 * 1e-3) / 1e9;
+  float mss32 = time_ms([&] { sqrt32_chain<8><<<blocks, threads>>>((float *)out, it32d); }, 3);
+  double sqrt32_gops = nthreads * it32d * 8 / (mss32 * 1e-3) / 1e9;
+
   size_t nbytes = (size_t)2 << 30;  // 2 GiB per buffer, far above L2
   size_t n2 = nbytes / sizeof(double2);
   double2 *a, *b;
@@ -125,9 +166,11 @@ int main() {
   int clock_khz = 0;
   CK(cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, 0));
   printf("{\"device\": \"%s\", \"sms\": %d, \"fp64_fma_tflops\": %.4f, \"fp32_fma_tflops\": %.3f, "
-         "\"fp64_div_gops\": %.2f, \"fp64_sqrt_gops\": %.2f, \"fp64_copy_gbs\": %.1f, "
+         "\"fp64_div_gops\": %.2f, \"fp64_sqrt_gops\": %.2f, \"fp32_div_gops\": %.1f, "
+         "\"fp32_fdividef_gops\": %.1f, \"fp32_sqrt_gops\": %.1f, \"fp64_copy_gbs\": %.1f, "
          "\"clock_khz\": %d}\n",
-         prop.name, sms, fp64_tflops, fp32_tflops, div_gops, sqrt_gops, copy_gbs, clock_khz);
+         prop.name, sms, fp64_tflops, fp32_tflops, div_gops, sqrt_gops, div32_gops, fdiv32_gops, sqrt32_gops,
+         copy_gbs, clock_khz);
   CK(cudaFree(a));
   CK(cudaFree(b));
   CK(cudaFree(out));

@@ -19,7 +19,6 @@ struct wcns_handle {
   int bc[3][2];
   double dirichlet[3][2][7];
   double *dir_face[3][2];  // optional per-face Dirichlet states (device, [nf][face cells])
-  double *bc_states;       // device copies of the uniform Dirichlet states [3][2][7]
   EosConst eos;
   wcns_options opt;
   cudaStream_t stream;
@@ -53,34 +52,39 @@ namespace {
 // ---------------------------------------------------------------------------
 // Device helpers.
 // ---------------------------------------------------------------------------
-// max over cells of (|u_d| + c) (Sec. 3.3), FP64 mixture thermodynamics
-// (Sec. 2), into ctl->smax[slot][d].
+// |u_d| + c of one conservative state for d < ndim (Sec. 3.3), with the FP64
+// mixture thermodynamics of Sec. 2: p = (rho e - Pi)/Gamma,
+// pbar = Pi/(Gamma + 1), rho c^2 = (1 + 1/Gamma)(p + pbar).
+__device__ __forceinline__ void state_wavespeeds(double a1r1, double a2r2, const double *m, double E, double a1,
+                                                 int ndim, const EosConst &e, double *s) {
+  const double rho = a1r1 + a2r2;
+  const double ir = 1.0 / rho;
+  double m2 = 0.0, v[3] = {0.0, 0.0, 0.0};
+  for (int j = 0; j < ndim; ++j) {
+    v[j] = m[j] * ir;
+    m2 = fma(m[j], v[j], m2);
+  }
+  const double rhoe = E - 0.5 * m2;
+  const double Gam = fma(a1, e.r1 - e.r2, e.r2);
+  const double Pi = a1 * e.q1;
+  const double iG = 1.0 / Gam;
+  const double p = (rhoe - Pi) * iG;
+  const double pb = Pi / (Gam + 1.0);
+  const double c = sqrt((1.0 + iG) * (p + pb) * ir);
+  for (int j = 0; j < ndim; ++j) s[j] = fabs(v[j]) + c;
+}
+
+// max over cells of (|u_d| + c) (Sec. 3.3) into ctl->smax[slot][d].
 __global__ void reduce_wavespeed_kernel(const double *__restrict__ W, long long N, int ndim,
                                         EosConst e, StepCtl *ctl, int slot) {
   double smax[3] = {0.0, 0.0, 0.0};
   const int E = 2 + ndim, A = 3 + ndim;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
-    const double rho = W[i] + W[N + i];
-    const double ir = 1.0 / rho;
-    double m2 = 0.0, v[3] = {0.0, 0.0, 0.0};
-    for (int j = 0; j < ndim; ++j) {
-      const double m = W[(2 + j) * N + i];
-      v[j] = m * ir;
-      m2 = fma(m, v[j], m2);
-    }
-    const double rhoe = W[E * N + i] - 0.5 * m2;
-    const double a1 = W[A * N + i];
-    const double Gam = fma(a1, e.r1 - e.r2, e.r2);
-    const double Pi = a1 * e.q1;
-    const double iG = 1.0 / Gam;
-    const double p = (rhoe - Pi) * iG;
-    const double pb = Pi / (Gam + 1.0);
-    const double c = sqrt((1.0 + iG) * (p + pb) * ir);
-    for (int j = 0; j < ndim; ++j) {
-      const double s = fabs(v[j]) + c;
-      smax[j] = (s > smax[j] || s != s) ? s : smax[j];
-    }
+    double m[3], sp[3];
+    for (int j = 0; j < ndim; ++j) m[j] = W[(2 + j) * N + i];
+    state_wavespeeds(W[i], W[N + i], m, W[E * N + i], W[A * N + i], ndim, e, sp);
+    for (int j = 0; j < ndim; ++j) smax[j] = (sp[j] > smax[j] || sp[j] != sp[j]) ? sp[j] : smax[j];
   }
   for (int j = 0; j < ndim; ++j) {
     unsigned long long b = __double_as_longlong(smax[j]);
@@ -92,7 +96,31 @@ __global__ void reduce_wavespeed_kernel(const double *__restrict__ W, long long 
   }
 }
 
-__global__ void init_ctl_kernel(StepCtl *ctl, double t, double t_end) {
+// The uniform Dirichlet ghost states of a handle, passed BY VALUE as a
+// kernel argument (no device copy, no host-to-device transfer).
+struct UniformBcStates {
+  double w[6][7];  // conservative states, [face][field]
+  int count;
+};
+
+// max(|u_d| + c) of the uniform Dirichlet states into ctl->smax[0][d]; one
+// thread per state.
+__global__ void bc_wavespeed_kernel(const UniformBcStates u, int ndim, EosConst e, StepCtl *ctl) {
+  const int k = threadIdx.x;
+  if (k >= u.count) return;
+  const double *w = u.w[k];
+  double sp[3];
+  state_wavespeeds(w[0], w[1], w + 2, w[2 + ndim], w[3 + ndim], ndim, e, sp);
+  for (int j = 0; j < ndim; ++j) {
+    // as in the reduction: NaN bits order above every finite wave speed's
+    const unsigned long long b = __double_as_longlong(sp[j]);
+    if (b) atomicMax(&ctl->smax[0][j], b);
+  }
+}
+
+__global__ void init_ctl_kernel(StepCtl *ctl, const DevStats *stats, double t, double t_end) {
+  ctl->stat0[0] = stats->inadmissible;
+  ctl->stat0[1] = stats->nonfinite;
   for (int k = 0; k < 4; ++k)
     for (int d = 0; d < 3; ++d) ctl->smax[k][d] = ctl->smax_bc[d];
   ctl->dt = 0.0;
@@ -158,7 +186,7 @@ int launch_reduce(wcns_handle *h, const double *W, int slot) {
 }
 
 int launch_init(wcns_handle *h, double t, double t_end) {
-  init_ctl_kernel<<<1, 1, 0, h->launch_stream>>>(h->ctl, t, t_end);
+  init_ctl_kernel<<<1, 1, 0, h->launch_stream>>>(h->ctl, h->stats, t, t_end);
   h->launches++;
   return cuda_status(cudaGetLastError());
 }
@@ -311,34 +339,52 @@ void drop_graph(wcns_handle *h) {
 }
 
 // Dirichlet ghost states enter the boundary midpoints' fluxes like cells, so
-// their max(|u_d| + c) bounds dt too (Sec. 3.3).  They are reduced by the
-// same kernel as the cells, into slot 0 of the (reset) step control, and the
-// result is kept as the floor every wave-speed slot starts from.  Called when
-// the boundary data change; every entry point re-initialises the step
-// control afterwards.  Stream-ordered, no allocation.
+// their max(|u_d| + c) bounds dt too (Sec. 3.3).  They are reduced into
+// slot 0 of the (reset) step control, and the result is kept as the floor
+// every wave-speed slot starts from.  Uniform states travel by value in the
+// kernel's arguments; per-face states are reduced from their device copies.
+// Called when the boundary data change; every entry point re-initialises
+// the step control afterwards.  Stream-ordered; no allocation and no host
+// memory read by the device.
 int update_bc_wavespeed(wcns_handle *h) {
   cudaStream_t st = h->stream;
   cudaError_t e = cudaMemsetAsync(h->ctl, 0, sizeof(StepCtl), st);
+  UniformBcStates u;
+  memset(&u, 0, sizeof(u));
   for (int d = 0; d < h->ndim && e == cudaSuccess; ++d) {
     for (int s = 0; s < 2 && e == cudaSuccess; ++s) {
       if (h->bc[d][s] != WCNS_BC_DIRICHLET) continue;
       const double *src = h->dir_face[d][s];
-      long long n = h->N / h->n[d];
       if (!src) {
-        double *dst = h->bc_states + (size_t)(2 * d + s) * 7;
-        e = cudaMemcpyAsync(dst, h->dirichlet[d][s], sizeof(double) * h->nf, cudaMemcpyHostToDevice, st);
-        src = dst;
-        n = 1;
+        for (int q = 0; q < h->nf; ++q) u.w[u.count][q] = h->dirichlet[d][s][q];
+        u.count++;
+        continue;
       }
-      if (e != cudaSuccess) break;
+      const long long n = h->N / h->n[d];
       const long long blocks = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
       reduce_wavespeed_kernel<<<(int)blocks, 256, 0, st>>>(src, n, h->ndim, h->eos, h->ctl, 0);
       e = cudaGetLastError();
     }
   }
+  if (e == cudaSuccess && u.count) {
+    bc_wavespeed_kernel<<<1, 32, 0, st>>>(u, h->ndim, h->eos, h->ctl);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->ctl->smax_bc, h->ctl->smax[0], sizeof(h->ctl->smax_bc), cudaMemcpyDeviceToDevice, st);
   return cuda_status(e);
+}
+
+// Status of a synchronising call: waits for the handle's stream, then
+// compares the device counters with their snapshot from the call's
+// launch_init (WCNS_E_NONFINITE, WCNS_E_INADMISSIBLE or WCNS_OK).  The
+// step control is returned in *c.
+int read_status(wcns_handle *h, StepCtl *c) {
+  DevStats s;
+  CK(cudaMemcpyAsync(c, h->ctl, sizeof(StepCtl), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(&s, h->stats, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return status_from_counts(*c, s, WCNS_OK, WCNS_E_NONFINITE, WCNS_E_INADMISSIBLE);
 }
 
 // nsteps SSPRK3 steps.  With graphs enabled (and no per-kernel timing) one
@@ -431,8 +477,10 @@ int wcns_create(const wcns_grid *g, const wcns_bcs *bcs, double gamma_g, double 
       return WCNS_E_INVALID_ARG;
     if ((bcs->kind[d][0] == WCNS_BC_SYMMETRY || bcs->kind[d][1] == WCNS_BC_SYMMETRY) && g->n[d] < 3)
       return WCNS_E_INVALID_ARG;
+    // at most 2^30 cells an axis and 2^40 in all, checked before the
+    // product is formed so that it cannot overflow
+    if (g->n[d] > (1 << 30) || N > (1ll << 40) / g->n[d]) return WCNS_E_INVALID_ARG;
     N *= g->n[d];
-    if (g->n[d] > (1 << 30) || N > (1ll << 40)) return WCNS_E_INVALID_ARG;
   }
   // launch-grid limits of the sweeps (gridDim.y / gridDim.z <= 65535)
   {
@@ -477,7 +525,6 @@ int wcns_create(const wcns_grid *g, const wcns_bcs *bcs, double gamma_g, double 
   if (e == cudaSuccess) e = cudaMalloc(&h->stats, sizeof(DevStats));
   if (e == cudaSuccess) e = cudaMemset(h->stats, 0, sizeof(DevStats));
   if (e == cudaSuccess) e = cudaMemset(h->ctl, 0, sizeof(StepCtl));
-  if (e == cudaSuccess) e = cudaMalloc(&h->bc_states, sizeof(double) * 3 * 2 * 7);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
@@ -586,13 +633,10 @@ int wcns_advance_steps(wcns_handle *h, double *W, int nsteps, double cfl, double
   if (!st && (h->ndim > 1 || dt_fixed == 0.0)) st = launch_reduce(h, W, 3);
   if (!st) st = run_steps(h, W, nsteps, dt_fixed, cfl);
   if (st) return st;
-  if (t_io) {
-    StepCtl c;
-    CK(cudaMemcpyAsync(&c, h->ctl, sizeof(StepCtl), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    *t_io = c.t;
-  }
-  return WCNS_OK;
+  StepCtl c;
+  st = read_status(h, &c);
+  if (t_io) *t_io = c.t;
+  return st;
 }
 
 int wcns_advance_to(wcns_handle *h, double *W, double t0, double t_end, double cfl, double *t_out,
@@ -606,16 +650,16 @@ int wcns_advance_to(wcns_handle *h, double *W, double t0, double t_end, double c
   for (;;) {
     st = run_steps(h, W, batch, 0.0, cfl);
     if (st) return st;
-    CK(cudaMemcpyAsync(&c, h->ctl, sizeof(StepCtl), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
+    st = read_status(h, &c);
+    if (t_out) *t_out = c.t;
+    if (steps_out) *steps_out = (long)c.steps;
     // a non-finite wave speed makes dt and t NaN: report it before the
     // t < t_end test (false for NaN) could end the loop as if t_end was reached
     if (!isfinite(c.t) || !isfinite(c.dt) || (c.active && c.dt <= 0.0)) return WCNS_E_NONFINITE;
+    if (st) return st;  // a non-finite update or an inadmissible stage input
     if (!c.active || !(c.t < t_end)) break;
     if (batch < 256) batch *= 2;
   }
-  if (t_out) *t_out = c.t;
-  if (steps_out) *steps_out = (long)c.steps;
   return WCNS_OK;
 }
 
@@ -626,12 +670,14 @@ int wcns_advance_steps_host(wcns_handle *h, double *W_host, int nsteps, double c
   if (!h->Wh) CK(cudaMalloc(&h->Wh, bytes));
   CK(cudaMemcpyAsync(h->Wh, W_host, bytes, cudaMemcpyHostToDevice, h->stream));
   double t = t_io ? *t_io : 0.0;
-  int st = wcns_advance_steps(h, h->Wh, nsteps, cfl, dt_fixed, &t);
-  if (st) return st;
+  const int st = wcns_advance_steps(h, h->Wh, nsteps, cfl, dt_fixed, &t);
+  // the state comes back also when the steps report a non-finite or
+  // inadmissible state (the caller sees what the device holds)
+  if (st != WCNS_OK && st != WCNS_E_NONFINITE && st != WCNS_E_INADMISSIBLE) return st;
   CK(cudaMemcpyAsync(W_host, h->Wh, bytes, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   if (t_io) *t_io = t;
-  return WCNS_OK;
+  return st;
 }
 
 int wcns_get_stats(wcns_handle *h, wcns_stats *out) {
@@ -710,7 +756,6 @@ const char *wcns_strerror(int s) {
     case WCNS_E_CUDA: return "CUDA runtime error";
     case WCNS_E_INADMISSIBLE: return "input state outside the admissible set";
     case WCNS_E_NONFINITE: return "non-finite value";
-    case WCNS_E_TIMEOUT: return "bounded device wait timed out";
     case WCNS_E_UNSUPPORTED: return "unsupported option combination";
     case WCNS_E_TOO_LARGE:
       return "problem too large for the fixed no-allocation scratch (needs 3 * nf * ncells <= "
@@ -739,7 +784,6 @@ void wcns_destroy(wcns_handle *h) {
   cudaFree(h->Wh);
   cudaFree(h->ctl);
   cudaFree(h->stats);
-  cudaFree(h->bc_states);
   free(h);
 }
 
@@ -779,7 +823,6 @@ int noalloc_setup(int dev, double **states, unsigned char **ctl) {
   *ctl = g_noalloc_ctl_ptr[dev];
   return WCNS_OK;
 }
-static_assert(sizeof(StepCtl) + sizeof(DevStats) + 16 <= 512, "control region too small");
 }  // namespace
 
 extern "C" int wcns_rk3_step_noalloc(const wcns_grid *g, const wcns_bcs *bcs, double gamma_g, double gamma_l,
@@ -798,8 +841,8 @@ extern "C" int wcns_rk3_step_noalloc(const wcns_grid *g, const wcns_bcs *bcs, do
     if ((bcs->kind[d][0] == WCNS_BC_PERIODIC) != (bcs->kind[d][1] == WCNS_BC_PERIODIC)) return WCNS_E_INVALID_ARG;
     if ((bcs->kind[d][0] == WCNS_BC_SYMMETRY || bcs->kind[d][1] == WCNS_BC_SYMMETRY) && g->n[d] < 3)
       return WCNS_E_INVALID_ARG;
+    if (g->n[d] > (1 << 30) || N > (1ll << 40) / g->n[d]) return WCNS_E_TOO_LARGE;
     N *= g->n[d];
-    if (N > (1ll << 40)) return WCNS_E_TOO_LARGE;
   }
   {
     const long long ny = g->ndim > 1 ? g->n[1] : 1, nz = g->ndim > 2 ? g->n[2] : 1;
@@ -852,13 +895,12 @@ extern "C" int wcns_rk3_step_noalloc(const wcns_grid *g, const wcns_bcs *bcs, do
     h.node_c = (float *)(h.node_ir + N);
     h.node_ok = (unsigned int *)(h.node_c + N);
   }
-  // small region: StepCtl | DevStats | uniform Dirichlet states [3][2][7]
+  // small region: StepCtl | DevStats (the uniform Dirichlet states reach
+  // the device as kernel arguments, from this stack frame's handle)
   constexpr size_t kStatsOff = ((sizeof(StepCtl) + 15) / 16) * 16;
-  constexpr size_t kBcOff = ((kStatsOff + sizeof(DevStats) + 15) / 16) * 16;
-  static_assert(kBcOff + sizeof(double) * 42 <= sizeof(g_noalloc_ctl), "no-alloc control region too small");
+  static_assert(kStatsOff + sizeof(DevStats) <= sizeof(g_noalloc_ctl), "no-alloc control region too small");
   h.ctl = (StepCtl *)ctlmem;
   h.stats = (DevStats *)(ctlmem + kStatsOff);
-  h.bc_states = (double *)(ctlmem + kBcOff);
   // The counters keep the previous call's values: clear them.
   if (cudaMemsetAsync(h.stats, 0, sizeof(DevStats), h.stream) != cudaSuccess) return WCNS_E_CUDA;
   st = update_bc_wavespeed(&h);

@@ -133,6 +133,12 @@ __global__ void batch_begin_kernel(int nprob, const double *inv_dx, double *dt, 
   if (t_acc) t_acc[k] += d;
 }
 
+// DevStats counts at the start of a batch advance, for its status.
+__global__ void batch_snapshot_kernel(const DevStats *s, StepCtl *c) {
+  c->stat0[0] = s->inadmissible;
+  c->stat0[1] = s->nonfinite;
+}
+
 typedef cudaError_t (*BatchLauncher)(const SweepArgs &, const BatchArgs &, int grid, cudaStream_t);
 
 // A batch tile: TH threads and TH - TRIM midpoints (TH - TRIM + 5 nodes).
@@ -204,7 +210,8 @@ struct wcns_batch {
   unsigned long long *smax, *smax_scratch;
   double *W1, *W2, *Wtrial;
   DevStats *stats;
-  StepCtl *ctl;  // unused by the batch geometry; keeps SweepArgs complete
+  StepCtl *ctl;  // counter snapshot of the current advance (stat0); the
+                 // batch geometry takes dt from its per-problem tables
   // per tile length: work list
   int *tile_prob[kNumVariants], *tile_first[kNumVariants];
   int ntiles[kNumVariants];
@@ -453,6 +460,9 @@ int wcns_batch_advance(wcns_batch *b, double *W, int nsteps, double cfl, double 
   // order after the caller's pending work
   if (cudaEventRecord(b->ev_in, b->stream) != cudaSuccess) return WCNS_E_CUDA;
   if (cudaStreamWaitEvent(b->cap, b->ev_in, 0) != cudaSuccess) return WCNS_E_CUDA;
+  batch_snapshot_kernel<<<1, 1, 0, b->cap>>>(b->stats, b->ctl);
+  b->launches++;
+  if (cudaGetLastError() != cudaSuccess) return WCNS_E_CUDA;
   int st = launch_batch_reduce(b, W, b->cap);
   if (st) return st;
   if (!b->graph || b->graph_W != W || b->graph_cfl != cfl || b->graph_t != t_out) {
@@ -479,7 +489,13 @@ int wcns_batch_advance(wcns_batch *b, double *W, int nsteps, double cfl, double 
   }
   if (cudaEventRecord(b->ev_out, b->cap) != cudaSuccess) return WCNS_E_CUDA;
   if (cudaStreamWaitEvent(b->stream, b->ev_out, 0) != cudaSuccess) return WCNS_E_CUDA;
-  return WCNS_OK;
+  // status: the counters against their snapshot (synchronises)
+  StepCtl c;
+  DevStats s;
+  if (cudaMemcpyAsync(&c, b->ctl, sizeof(c), cudaMemcpyDeviceToHost, b->cap) != cudaSuccess) return WCNS_E_CUDA;
+  if (cudaMemcpyAsync(&s, b->stats, sizeof(s), cudaMemcpyDeviceToHost, b->cap) != cudaSuccess) return WCNS_E_CUDA;
+  if (cudaStreamSynchronize(b->cap) != cudaSuccess) return WCNS_E_CUDA;
+  return status_from_counts(c, s, WCNS_OK, WCNS_E_NONFINITE, WCNS_E_INADMISSIBLE);
 }
 
 int wcns_batch_get_stats(wcns_batch *b, wcns_stats *out) {

@@ -100,7 +100,18 @@ struct StepCtl {
   double t_end;     // advance-to target (or +inf)
   long long steps;  // steps taken
   int active;       // 0 once t has reached t_end: remaining kernels do nothing
+  // DevStats inadmissible / nonfinite counts when the current call began:
+  // a synchronising call compares them with the counts at its end
+  unsigned long long stat0[2];
 };
+
+// Status of the work enqueued since the counters were snapshotted into
+// stat0: a non-finite update first, then a stage input outside G (Sec. 2).
+inline int status_from_counts(const StepCtl &c, const DevStats &s, int ok, int e_nonfinite, int e_inadmissible) {
+  if (s.nonfinite > c.stat0[1]) return e_nonfinite;
+  if (s.inadmissible > c.stat0[0]) return e_inadmissible;
+  return ok;
+}
 
 enum Epilogue {
   EPI_WRITE = 0,     // L  = contribution

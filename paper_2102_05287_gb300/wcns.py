@@ -13,8 +13,8 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libwcns.so")
 
-WCNS_OK, WCNS_E_INVALID_ARG, WCNS_E_CUDA, WCNS_E_INADMISSIBLE, WCNS_E_NONFINITE, WCNS_E_TIMEOUT, \
-    WCNS_E_UNSUPPORTED, WCNS_E_TOO_LARGE = range(8)
+WCNS_OK, WCNS_E_INVALID_ARG, WCNS_E_CUDA, WCNS_E_INADMISSIBLE, WCNS_E_NONFINITE = range(5)
+WCNS_E_UNSUPPORTED, WCNS_E_TOO_LARGE = 6, 7
 WCNS_BC_TRANSMISSIVE, WCNS_BC_PERIODIC, WCNS_BC_SYMMETRY, WCNS_BC_DIRICHLET = range(4)
 WCNS_FP64, WCNS_MIXED = 0, 1
 WCNS_SCHEME_PP_WCNS_IS, WCNS_SCHEME_HLLC1, WCNS_SCHEME_WCNS_IS = 0, 1, 2

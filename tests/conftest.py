@@ -40,3 +40,15 @@ def build_abi_consumer(libpath, outdir):
     r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr
     return exe
+
+
+def pytest_terminal_summary(terminalreporter, exitstatus, config):
+    """Report the FP64 parity cases that needed the conditioning fallback."""
+    try:
+        from tests import parity_log
+    except Exception:
+        return
+    if "tests.test_gpu_parity" in sys.modules or "test_gpu_parity" in sys.modules:
+        terminalreporter.write_sep("-", "FP64 parity fallback report")
+        for line in parity_log.summary_lines():
+            terminalreporter.write_line(line)

@@ -1,15 +1,26 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
 
-Tolerances: FP64 path 1e-12 relative per field per RHS / step (relative to
-the field's max magnitude), 1e-8 after a full 1D water-air shock-tube run;
-the mixed path is checked for its error level and exact invariants.
+Tolerances, FP64 path: 1e-12 relative per field per RHS / step (relative to
+the field's max magnitude); where a limiter or the IS weights make a case
+ill-conditioned, 4x the oracle's own spread under 1-ulp input
+perturbations (each such case is recorded in tests/parity_log.py and
+reported).  After the full 1D water-air shock-tube run (255 steps), the
+GPU's end state must differ from the oracle's by no more than
+max(1e-8, the largest difference between the oracle and 32 oracle runs
+under 1-ulp noise) and 3x their median: once the flux limiter has put a
+cell exactly at its tolerance, Algorithm 1's first branch decides on a
+1-ulp difference, so no FP64 implementation can promise 1e-8 there.  The mixed path is
+checked for its error level and exact invariants.
 """
+import os
+
 import numpy as np
 import pytest
 
 from oracle import Oracle
 from oracle import exact_riemann as ER
 from paper_2102_05287_gb300 import problems as P
+from tests import parity_log
 
 pytestmark = pytest.mark.gpu
 
@@ -69,6 +80,7 @@ def assert_parity(got, ref, fn, W, tol=TOL_FP64):
     if np.all(err < tol):
         return err
     floor = noise_floor(fn, W, ref)
+    parity_log.record(os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0], err, floor, tol)
     bound = np.maximum(tol, 4.0 * floor)
     assert np.all(err <= bound) and err.max() < 1e-9, (err, floor)
     return err
@@ -227,24 +239,60 @@ def shadow_step_errors(o, s, W, dt):
         e = relerr(got, ref)
         bar = np.full(len(e), TOL_FP64)
         if np.any(e >= TOL_FP64):
-            bar = np.maximum(bar, 4.0 * noise_floor(stage, inp, ref))
+            floor = noise_floor(stage, inp, ref)
+            parity_log.record("test_water_air_shock_tube_full_run (a shadowed stage)", e, floor, TOL_FP64)
+            bar = np.maximum(bar, 4.0 * floor)
         errs.append(e)
         bars.append(bar)
     return errs, bars, W3
 
 
+def oracle_trajectory_ensemble(o, pr, runs=32, seed=0):
+    """The oracle's own run-to-run spread on a CFL-0.5 run to pr.t_end:
+    `runs` oracle runs whose state is perturbed by a seeded relative 1 ulp
+    (2.3e-16) at the start and again after every step, each taking the
+    oracle's own dt (cfl / sum_d max(|u_d| + c)/dx_d, Sec. 3.3).  Such a run
+    stands for an FP64 implementation that rounds differently at every
+    step.  Returns the unperturbed run's end state (oracle advance_to) and
+    the (runs, fields) array of each member's relerr against it."""
+    rng = np.random.default_rng(seed)
+    ref = o.advance_to(pr.W, 0.0, pr.t_end, cfl=0.5)[0]
+    dx = [(pr.hi[d] - pr.lo[d]) / pr.n[d] for d in range(pr.ndim)]
+    devs = []
+    for _ in range(runs):
+        W = pr.W * (1.0 + rng.uniform(-1.0, 1.0, pr.W.shape) * 2.3e-16)
+        t = 0.0
+        while t < pr.t_end:
+            sm = o.max_wavespeed(W)
+            dt = 0.5 / sum(sm[d] / dx[d] for d in range(pr.ndim))
+            last = t + dt >= pr.t_end
+            if last:
+                dt = pr.t_end - t
+            W = o.rk3_step(W, dt)
+            W = W * (1.0 + rng.uniform(-1.0, 1.0, W.shape) * 2.3e-16)
+            t = pr.t_end if last else t + dt
+        devs.append(relerr(W, ref))
+    return ref, np.array(devs)
+
+
 def test_water_air_shock_tube_full_run():
     """1D water-air shock tube, 200 cells, CFL 0.5 to t = 2.4e-4, FP64.
 
-    Every stage of every fused GPU step is shadowed by the oracle: its RHS
-    is evaluated on the GPU's own stage input and the stage state compared
-    (1e-12, or the oracle's 1-ulp spread at that input).  Whole trajectories
-    are not compared point by point: once the flux limiter has driven a
-    cell's partial density to exactly the tolerance eps, the first branch of
-    Algorithm 1 (node below eps: theta = 0, else theta = 1) switches between
-    first-order and high-order fluxes on a 1-ulp difference in that cell, so
-    two correct runs may part there.  Both runs are compared with the exact
-    two-stiffened-gas Riemann solution instead."""
+    (1) Stage shadowing: every stage of every fused GPU step is compared
+    with the oracle's RHS evaluated on the GPU's own stage input (1e-12, or
+    the oracle's 1-ulp spread at that input).
+    (2) Whole trajectory: the GPU's end state, from those host-timed steps
+    and from wcns_advance_to (device-side dt), against the oracle's end
+    state.  Once the flux limiter has put a cell's partial density exactly
+    at its tolerance, the first branch of Algorithm 1 switches between
+    first-order and high-order fluxes on a 1-ulp difference in that cell,
+    so correct runs part there: 32 oracle runs under 1-ulp noise (on the
+    initial state and after every step) differ from the unperturbed one by
+    a heavy-tailed amount (median ~5e-5 in a2r2, the largest ~4e-4).  The
+    GPU must be within max(1e-8, the largest of those differences) and
+    within 3x their median, per field.
+    (3) GPU and oracle agree to 1e-3 (relative) in their L1 density error
+    against the exact two-stiffened-gas Riemann solution."""
     pr = P.water_air_shock_tube(200)
     o, s = pair(pr.n, pr.bcs, lo=pr.lo, hi=pr.hi)
     W = pr.W.copy()
@@ -262,13 +310,33 @@ def test_water_air_shock_tube_full_run():
     assert steps > 200
     st = s.stats()
     assert st["nonfinite"] == 0 and st["inadmissible"] == 0
-    Wref, _, _ = o.advance_to(pr.W, 0.0, pr.t_end, cfl=0.5)
+    # (2) whole trajectories against the oracle's own run-to-run spread
+    Wref, devs = oracle_trajectory_ensemble(o, pr)
+    Wg = torch.from_numpy(pr.W).cuda()
+    s2 = Solver(pr.n, pr.lo, pr.hi, pr.bcs, **pr.eos)
+    s2.advance_to(Wg, 0.0, pr.t_end, cfl=0.5)
+    W_adv = Wg.cpu().numpy()
+    s2.close()
+    e_shadow = relerr(W, Wref)
+    e_adv = relerr(W_adv, Wref)
+    med, top = np.median(devs, axis=0), devs.max(axis=0)
+    fmt = lambda a: np.array2string(np.asarray(a), precision=2)  # noqa: E731
+    print("config-0 full run, per field (a1r1, a2r2, m, E, alpha1) vs the oracle: GPU with host dt %s, "
+          "GPU wcns_advance_to %s; 32 oracle runs under 1-ulp noise: median %s, max %s; rank of the "
+          "wcns_advance_to run among them %s" %
+          (fmt(e_shadow), fmt(e_adv), fmt(med), fmt(top), (devs < e_adv).sum(axis=0)))
+    for e in (e_shadow, e_adv):
+        assert np.all(e <= np.maximum(1e-8, top)), (e, top)
+        assert np.all(e <= np.maximum(1e-8, 3.0 * med)), (e, med)
+    # (3) against the exact solution
     x = (np.arange(200) + 0.5) / 200
     ex, _ = ER.solve_five_equation(pr.eos, (999.999, 0.00005, 0.0, 1e9, 1 - 1e-6),
                                    (0.001, 49.99995, 0.0, 1e5, 1e-6), 0.7, pr.t_end, x)
     l1_gpu = np.mean(np.abs(W[0] + W[1] - ex[0] - ex[1]))
+    l1_adv = np.mean(np.abs(W_adv[0] + W_adv[1] - ex[0] - ex[1]))
     l1_ref = np.mean(np.abs(Wref[0] + Wref[1] - ex[0] - ex[1]))
-    assert abs(l1_gpu - l1_ref) <= 0.02 * l1_ref, (l1_gpu, l1_ref)
+    assert abs(l1_gpu - l1_ref) <= 1e-3 * l1_ref, (l1_gpu, l1_ref)
+    assert abs(l1_adv - l1_ref) <= 1e-3 * l1_ref, (l1_adv, l1_ref)
 
 
 def test_advance_to_matches_stepping():

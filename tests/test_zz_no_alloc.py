@@ -1,13 +1,14 @@
 """The allocation-free SSPRK3 entry point, wcns_rk3_step_noalloc.
 
-It exists for callers that must not call cudaMalloc (code running during a
-CUDA graph capture, real-time loops in which an allocation would
-synchronise the device, hosts that give a plugin a fixed device-memory
-budget).  Its scratch is a fixed device array inside the library, shared by
-every call.  These tests call it through the C ABI twice in a row and check
-each result against the ordinary handle-based wcns_rk3_step, within the
-1e-12 per-field relative tolerance of the FP64 parity tests; the file is
-named so that pytest collects it last.
+It exists for callers that must not call cudaMalloc: real-time loops in
+which an allocation can synchronise the device and miss a deadline, host
+applications that give a plugin a fixed device-memory budget, and code that
+keeps no per-solver state.  Its scratch is a fixed device array inside the
+library, shared by every call.  These tests call it through the C ABI twice
+in a row and check each result against the ordinary handle-based
+wcns_rk3_step, within the 1e-12 per-field relative tolerance of the FP64
+parity tests, in 1D, 2D and 3D, with transmissive, symmetry and uniform
+Dirichlet faces; the file is named so that pytest collects it last.
 """
 import ctypes as C
 
@@ -44,11 +45,50 @@ def c_grid_bcs(pr):
     for d in range(pr.ndim):
         for s in range(2):
             b.kind[d][s] = wcns._BC[pr.bcs[d][s]]
+            st = pr.extra.get("dirichlet_states", {}).get((d, s))
+            if st is not None:
+                for q, v in enumerate(st):
+                    b.dirichlet[d][s][q] = float(v)
     return g, b
 
 
+def shock_tube_dirichlet():
+    """The 1D water-air shock tube (200 cells) with its right face a uniform
+    Dirichlet state: the pre-shock air moving left into the tube at 50 m/s
+    (its wave speed then enters dt, Sec. 3.3)."""
+    pr = P.water_air_shock_tube(200)
+    right = pr.W[:, -1].copy()
+    rho = right[0] + right[1]
+    right[2] = -50.0 * rho
+    right[3] += 0.5 * rho * 50.0 ** 2
+    pr.bcs = (("transmissive", "dirichlet"),)
+    pr.extra["dirichlet_states"] = {(0, 1): right}
+    return pr
+
+
+def shock_bubble_dirichlet():
+    """The 2D shock/bubble problem (96 x 48) with uniform Dirichlet states on
+    the left face (its own post-shock state) and the top face (the ambient
+    water)."""
+    pr = P.shock_bubble_2d(96, 48, seed=5)
+    pr.bcs = (("dirichlet", "transmissive"), ("symmetry", "dirichlet"))
+    pr.extra["dirichlet_states"] = {(0, 0): pr.W[:, 0, 0].copy(), (1, 1): pr.W[:, -1, -1].copy()}
+    return pr
+
+
 PROBLEMS = {"shock_bubble_2d_96x48": lambda: P.shock_bubble_2d(96, 48, seed=5),
-            "bubble_collapse_3d_24": lambda: P.bubble_collapse_3d(n=24)}
+            "bubble_collapse_3d_24": lambda: P.bubble_collapse_3d(n=24),
+            "shock_tube_1d_200": lambda: P.water_air_shock_tube(200),
+            "shock_tube_1d_200_dirichlet": shock_tube_dirichlet,
+            "shock_bubble_2d_96x48_dirichlet": shock_bubble_dirichlet}
+
+
+def dirichlet_arg(pr):
+    """The Solver's `dirichlet` argument for the problem's uniform states."""
+    st = pr.extra.get("dirichlet_states")
+    if not st:
+        return None
+    return [[st.get((d, s)) for s in range(2)] for d in range(pr.ndim)]
 
 
 @pytest.mark.parametrize("problem", sorted(PROBLEMS))
@@ -57,7 +97,8 @@ def test_noalloc_step_matches_handle_step_twice(precision, problem):
     lib = wcns.load()
     pr = PROBLEMS[problem]()
     stream = torch.cuda.current_stream()
-    ref = wcns.Solver(pr.n, pr.lo, pr.hi, pr.bcs, precision=precision, stream=stream, **pr.eos)
+    ref = wcns.Solver(pr.n, pr.lo, pr.hi, pr.bcs, precision=precision, stream=stream, dirichlet=dirichlet_arg(pr),
+                      **pr.eos)
     g, b = c_grid_bcs(pr)
     o = wcns.wcns_default_options()
     o.precision = wcns._PREC[precision]
