@@ -219,10 +219,10 @@ def algorithmic_ops(nx, ny):
 
 # Steps the mixed-precision sweeps compute in FP64 on every cell (node
 # pressure and sound speed from the conservative state, the stored node
-# fluxes, the flux difference and state accumulation); all other steps run
+# fluxes, the flux difference and the SSPRK3 state combination); all other steps run
 # in FP32 (the limiters' FP32-certified path; their FP64 theta solves only
 # run where certification fails, none on the bench workload).
-MIXED_FP64_STEPS = ("node_eos", "node_flux", "update")
+MIXED_FP64_STEPS = ("node_eos", "node_flux", "update", "ssprk3_combine")
 PROFILE_STEPS_MIXED = 5
 
 
@@ -384,6 +384,20 @@ def dominant(prof, ndim):
     return d, prof["ms"][d] / prof["launches"][d]
 
 
+def all_sweeps(roof, prof, ndim):
+    """Adds the fraction over every sweep launch of the profiled steps (the
+    sum of their roofline times over the sum of their CUDA-event times),
+    which does not depend on how the work splits between the directions,
+    and each direction's own fraction."""
+    per_launch_roofline_ms = roof["frac"] * roof["avg_launch_ms"]
+    n = sum(prof["launches"][:ndim])
+    ms = sum(prof["ms"][:ndim])
+    roof["frac_all_sweeps"] = per_launch_roofline_ms * n / ms if ms > 0 else None
+    roof["per_direction_avg_launch_ms"] = {"xyz"[d]: prof["ms"][d] / prof["launches"][d]
+                                           for d in range(ndim) if prof["launches"][d] > 0}
+    return roof
+
+
 def run_gb300(args, world, rank, local):
     import numpy as np
     import torch
@@ -483,7 +497,8 @@ def run_gb300(args, world, rank, local):
     peaks = load_peaks()
     ops = algorithmic_ops(args.nx, args.ny)
     dom, avg_ms = dominant(prof64, 2)
-    roofline = fp64_roofline(ops, peaks, avg_ms, ncell, "sweep_kernel<2,%d,double> (%s sweep)" % (dom, "xy"[dom]))
+    roofline = all_sweeps(fp64_roofline(ops, peaks, avg_ms, ncell,
+                                        "sweep_kernel<2,%d,double> (%s sweep)" % (dom, "xy"[dom])), prof64, 2)
     src_hash = hashlib.sha256(open(os.path.join(ROOT, "paper_2102_05287_gb300", "csrc", "wcns_sweep.cuh"),
                                    "rb").read()).hexdigest()[:16]
     traffic_file = os.path.join(ROOT, "profiles", "sweep_traffic.json")
@@ -506,6 +521,7 @@ def run_gb300(args, world, rank, local):
         dm, avg_m = dominant(pm, 2)
         mixed["roofline"] = mixed_roofline(ops, peaks, avg_m, ncell, mixed["stats"]["fp64_fallbacks"])
         mixed["roofline"]["kernel"] = "sweep_kernel_mixed<2,%d> (%s sweep)" % (dm, "xy"[dm])
+        all_sweeps(mixed["roofline"], pm, 2)
         if errs:
             mixed["first_step_error_vs_fp64_oracle"] = errs["mixed"]
     line = {
@@ -782,6 +798,7 @@ def workload_3d(args):
         else:
             roof = mixed_roofline(ops, peaks, avg_dom, pr.ncells, fallbacks=None)
             roof["kernel"] = "sweep_kernel_mixed<3,%d>" % dom
+        all_sweeps(roof, prof, 3)
         roof.pop("ops_per_cell_dir", None)
         res[prec] = {"ms_per_step": ms, "steps": k, "cell_stage_updates_per_s": 3 * pr.ncells / (ms * 1e-3),
                      "stats": s.stats(), "roofline": roof, "sweeps": sweeps}

@@ -16,7 +16,9 @@ Three tables:
                       one RHS each at its CFL-0.5 dt, summed over their cells;
   bubble_collapse_3d  the 3D bubble collapse on a 24^3 copy (the workload is
                       384^3), one RHS at its CFL-0.5 dt.
-The IS weights are counted in their one-division form (Sec. 4.3): the
+Each table also holds the SSPRK3 stage combinations (Sec. 5.3), counted on
+one step and given per stage (the sweeps fuse them into their last
+direction).  The IS weights are counted in their one-division form (Sec. 4.3): the
 oracle forms them with five ratio divisions and four normalising divisions
 as printed; scaling every eta_k by the product of the five (beta + eps)
 needs one division and 14 multiplications instead.
@@ -32,6 +34,16 @@ from paper_2102_05287_gb300 import problems as P
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 TABLE = os.path.join(ROOT, "profiles", "opcounts.json")
 KEYS = ("add", "mul", "div", "sqrt", "minmax")
+
+
+def _combine_row(o, W, dt, stages_units):
+    """The SSPRK3 stage combinations (Sec. 5.3) of one counted step, per
+    cell-stage and direction: the combine row of rk3_step over 3 x
+    cells x directions."""
+    o.opcount_reset()
+    o.rk3_step(W, dt)
+    c = o.opcount_rows()["ssprk3_combine"]
+    return {k: c[k] / stages_units for k in KEYS}
 
 
 def _one_division_form(per_step, is_calls):
@@ -58,7 +70,9 @@ def shock_bubble_2d(nx=128, ny=64):
     per_step = {r: {k: v / units for k, v in c.items()} for r, c in o.opcount_rows().items()}
     is_calls = 2 * (pr.ndim + 4) * o.stats.midpoints / units
     _one_division_form(per_step, is_calls)
-    return _table(per_step, is_calls, "shock_bubble_2d %dx%d, one RHS at CFL 0.5" % (nx, ny))
+    per_step["ssprk3_combine"] = _combine_row(o, pr.W, dt, 3 * units)
+    return _table(per_step, is_calls, "shock_bubble_2d %dx%d, one RHS at CFL 0.5 (and the SSPRK3 stage "
+                                      "combinations of one step, per stage)" % (nx, ny))
 
 
 def bubble_collapse_3d(n=24):
@@ -72,13 +86,16 @@ def bubble_collapse_3d(n=24):
     per_step = {r: {k: v / units for k, v in c.items()} for r, c in o.opcount_rows().items()}
     is_calls = 2 * (pr.ndim + 4) * o.stats.midpoints / units
     _one_division_form(per_step, is_calls)
-    return _table(per_step, is_calls, "bubble_collapse_3d %d^3, one RHS at CFL 0.5" % n)
+    per_step["ssprk3_combine"] = _combine_row(o, pr.W, dt, 3 * units)
+    return _table(per_step, is_calls, "bubble_collapse_3d %d^3, one RHS at CFL 0.5 (and the SSPRK3 stage "
+                                      "combinations of one step, per stage)" % n)
 
 
 def riemann_batch(nsample=16):
     rb = P.riemann_batch()
     picks = np.random.default_rng(1).choice(len(rb.sizes), nsample, replace=False)
     rows, cells, mids = {}, 0, 0
+    comb = dict.fromkeys(KEYS, 0.0)
     for k in picks:
         n = int(rb.sizes[k])
         W0 = np.ascontiguousarray(rb.W[:, int(rb.offsets[k]):int(rb.offsets[k + 1])])
@@ -92,9 +109,12 @@ def riemann_batch(nsample=16):
                 acc[key] += v
         cells += n
         mids += o.stats.midpoints
+        for key, v in _combine_row(o, W0, dt, 3.0).items():
+            comb[key] += v
     per_step = {r: {k: v / cells for k, v in c.items()} for r, c in rows.items()}
     is_calls = 2 * 5 * mids / cells
     _one_division_form(per_step, is_calls)
+    per_step["ssprk3_combine"] = {k: v / cells for k, v in comb.items()}
     return _table(per_step, is_calls, "%d problems of the 4096-problem Riemann batch (%d cells), one RHS each "
                                       "at CFL 0.5" % (nsample, cells))
 

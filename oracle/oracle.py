@@ -307,7 +307,8 @@ class Oracle:
     # step number -> name of the step of the method the operations belong to
     OPCOUNT_ROWS = {0: "other", 2: "node_eos", 3: "projection", 4: "wcns_is", 5: "back_projection",
                     6: "interp_limiter", 7: "midpoint_hllc", 8: "node_flux", 9: "hcs_split",
-                    10: "first_order_hllc", 11: "flux_limiter", 12: "update", 13: "max_wavespeed"}
+                    10: "first_order_hllc", 11: "flux_limiter", 12: "update", 13: "max_wavespeed",
+                    14: "ssprk3_combine"}
 
     def opcount_rows(self):
         """Operation counts since the last reset, per step of the method:

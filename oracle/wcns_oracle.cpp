@@ -57,6 +57,7 @@ enum OcRow {
   ROW_FLUX_LIMIT = 11,   // flux limiter (Section 5.2)
   ROW_UPDATE = 12,       // flux difference + alpha1 div u (Section 4)
   ROW_WAVESPEED = 13,    // maximum wave speed (Section 3.3)
+  ROW_COMBINE = 14,      // SSPRK3 stage combination (Section 5.3)
 };
 
 #ifdef ORACLE_COUNT_OPS
@@ -873,12 +874,21 @@ static void rk3_impl(const oc_config &c, double *W, double dt, oc_stats *st) {
   const long N = ncells(c);
   const size_t M = (size_t)nf * N;
   std::vector<double> W0(W, W + M), W1(M), W2(M), L(M);
+  // the stage combinations in `real` arithmetic (the op-counting build
+  // books them to their own step; the values are the same doubles)
+  const real h = dt;
   rhs_impl(c, W0.data(), L.data(), dt, st);
-  for (size_t q = 0; q < M; ++q) W1[q] = W0[q] + dt * L[q];
+  OC_ROW(ROW_COMBINE);
+  for (size_t q = 0; q < M; ++q) W1[q] = o_val(real(W0[q]) + h * real(L[q]));
   rhs_impl(c, W1.data(), L.data(), dt, st);
-  for (size_t q = 0; q < M; ++q) W2[q] = 0.75 * W0[q] + 0.25 * (W1[q] + dt * L[q]);
+  OC_ROW(ROW_COMBINE);
+  for (size_t q = 0; q < M; ++q)
+    W2[q] = o_val(real(0.75) * real(W0[q]) + real(0.25) * (real(W1[q]) + h * real(L[q])));
   rhs_impl(c, W2.data(), L.data(), dt, st);
-  for (size_t q = 0; q < M; ++q) W[q] = (1.0 / 3.0) * W0[q] + (2.0 / 3.0) * (W2[q] + dt * L[q]);
+  OC_ROW(ROW_COMBINE);
+  for (size_t q = 0; q < M; ++q)
+    W[q] = o_val(real(1.0 / 3.0) * real(W0[q]) + real(2.0 / 3.0) * (real(W2[q]) + h * real(L[q])));
+  OC_ROW(ROW_OTHER);
 }
 
 }  // namespace

@@ -52,28 +52,6 @@ namespace {
 // ---------------------------------------------------------------------------
 // Device helpers.
 // ---------------------------------------------------------------------------
-// |u_d| + c of one conservative state for d < ndim (Sec. 3.3), with the FP64
-// mixture thermodynamics of Sec. 2: p = (rho e - Pi)/Gamma,
-// pbar = Pi/(Gamma + 1), rho c^2 = (1 + 1/Gamma)(p + pbar).
-__device__ __forceinline__ void state_wavespeeds(double a1r1, double a2r2, const double *m, double E, double a1,
-                                                 int ndim, const EosConst &e, double *s) {
-  const double rho = a1r1 + a2r2;
-  const double ir = 1.0 / rho;
-  double m2 = 0.0, v[3] = {0.0, 0.0, 0.0};
-  for (int j = 0; j < ndim; ++j) {
-    v[j] = m[j] * ir;
-    m2 = fma(m[j], v[j], m2);
-  }
-  const double rhoe = E - 0.5 * m2;
-  const double Gam = fma(a1, e.r1 - e.r2, e.r2);
-  const double Pi = a1 * e.q1;
-  const double iG = 1.0 / Gam;
-  const double p = (rhoe - Pi) * iG;
-  const double pb = Pi / (Gam + 1.0);
-  const double c = sqrt((1.0 + iG) * (p + pb) * ir);
-  for (int j = 0; j < ndim; ++j) s[j] = fabs(v[j]) + c;
-}
-
 // max over cells of (|u_d| + c) (Sec. 3.3) into ctl->smax[slot][d].
 __global__ void reduce_wavespeed_kernel(const double *__restrict__ W, long long N, int ndim,
                                         EosConst e, StepCtl *ctl, int slot) {
@@ -198,6 +176,13 @@ int launch_begin(wcns_handle *h, double dt_fixed, double cfl, int advance_time) 
   return cuda_status(cudaGetLastError());
 }
 
+// The k-th sweep direction of an RHS evaluation: x, y, z in FP64; in the
+// mixed path the order of mixed_first_dir (z, y, x by default).
+int sweep_dir(const wcns_handle *h, int k) {
+  const bool rev = h->opt.precision == WCNS_MIXED && mixed_first_dir(h->ndim) != 0;
+  return rev ? h->ndim - 1 - k : k;
+}
+
 SweepArgs base_args(wcns_handle *h, int d) {
   SweepArgs a;
   memset(&a, 0, sizeof(a));
@@ -238,8 +223,8 @@ SweepArgs base_args(wcns_handle *h, int d) {
     a.node_ir = h->node_ir;
     a.node_c = h->node_c;
     a.node_ok = h->node_ok;
-    a.node_write = d == 0;
-    a.node_read = d > 0;
+    a.node_write = d == sweep_dir(h, 0);
+    a.node_read = !a.node_write;
   }
   return a;
 }
@@ -276,9 +261,10 @@ void profile_free(wcns_handle *h) {
 
 // dW/dt of W into L for every direction (stage 0 lambda).
 int enqueue_rhs(wcns_handle *h, const double *W, double *L) {
-  for (int d = 0; d < h->ndim; ++d) {
+  for (int k = 0; k < h->ndim; ++k) {
+    const int d = sweep_dir(h, k);
     SweepArgs a = base_args(h, d);
-    a.epilogue = d == 0 ? EPI_WRITE : EPI_ACCUM;
+    a.epilogue = k == 0 ? EPI_WRITE : EPI_ACCUM;
     a.stage = 0;
     a.W_in = W;
     a.L = L;
@@ -299,24 +285,26 @@ int enqueue_step(wcns_handle *h, double *W, double dt_fixed, double cfl) {
   for (int s = 0; s < 3; ++s) {
     const double *Win = s == 0 ? W : (s == 1 ? h->W1 : h->W2);
     double *Wout = s == 0 ? h->W1 : (s == 1 ? h->W2 : W);
-    for (int d = 0; d < h->ndim; ++d) {
+    const int d0 = sweep_dir(h, 0);
+    for (int k = 0; k < h->ndim; ++k) {
+      const int d = sweep_dir(h, k);
       SweepArgs a = base_args(h, d);
       a.stage = s;
       a.W_in = Win;
       a.Wn = W;
       a.L = h->L;
-      // mixed path: L holds the raw x flux difference plus the other
-      // directions' differences scaled by dx_x/dx_d; the combine applies
-      // 1/dx_x (one FP64 multiply per field less in the x sweep)
+      // mixed path: L holds the first sweep's raw flux difference plus the
+      // other directions' differences scaled by dx_d0/dx_d; the combine
+      // applies 1/dx_d0 (one FP64 multiply per field less in the first sweep)
       const bool raw = h->opt.precision == WCNS_MIXED && h->ndim > 1;
-      if (d < h->ndim - 1) {
-        a.epilogue = d == 0 ? EPI_WRITE : EPI_ACCUM;
-        a.l_raw = raw && d == 0;
-        if (raw && d > 0) a.accum_scale = h->inv_dx[d] / h->inv_dx[0];
+      if (k < h->ndim - 1) {
+        a.epilogue = k == 0 ? EPI_WRITE : EPI_ACCUM;
+        a.l_raw = raw && k == 0;
+        if (raw && k > 0) a.accum_scale = h->inv_dx[d] / h->inv_dx[d0];
       } else {
         a.epilogue = EPI_COMBINE;
         a.read_L = h->ndim > 1;
-        a.l_unit = raw ? h->inv_dx[0] : 1.0;
+        a.l_unit = raw ? h->inv_dx[d0] : 1.0;
         a.rk_a = ra[s];
         a.rk_b = rb[s];
         a.W_out = Wout;

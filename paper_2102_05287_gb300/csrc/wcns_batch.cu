@@ -88,7 +88,8 @@ constexpr size_t batch_smem() {
   return MIXED ? SmemMixed<1, T>::BYTES : Smem<1, 0, T>::BYTES;
 }
 
-// max(|u| + c) per problem (FP64 EOS, Sec. 2), one block per tile.
+// max(|u| + c) per problem (FP64 EOS, Sec. 2, with the single-grid
+// reduction's formula), one block per tile.
 __global__ void batch_reduce_kernel(const double *__restrict__ W, long long total, EosConst e, BatchArgs b,
                                     int tile_cells) {
   for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
@@ -98,17 +99,9 @@ __global__ void batch_reduce_kernel(const double *__restrict__ W, long long tota
     double smax = 0.0;
     for (int i = first + threadIdx.x; i < min(first + tile_cells, n); i += blockDim.x) {
       const long long idx = b.offsets[prob] + i;
-      const double rho = W[idx] + W[total + idx];
-      const double ir = 1.0 / rho;
-      const double u = W[2 * total + idx] * ir;
-      const double rhoe = W[3 * total + idx] - 0.5 * W[2 * total + idx] * u;
-      const double a1 = W[4 * total + idx];
-      const double Gam = fma(a1, e.r1 - e.r2, e.r2);
-      const double Pi = a1 * e.q1;
-      const double iG = 1.0 / Gam;
-      const double p = (rhoe - Pi) * iG;
-      const double pb = Pi / (Gam + 1.0);
-      const double s = fabs(u) + sqrt((1.0 + iG) * (p + pb) * ir);
+      const double m = W[2 * total + idx];
+      double s;
+      state_wavespeeds(W[idx], W[total + idx], &m, W[3 * total + idx], W[4 * total + idx], 1, e, &s);
       smax = (s > smax || s != s) ? s : smax;
     }
     unsigned long long bits = __double_as_longlong(smax);

@@ -113,6 +113,43 @@ inline int status_from_counts(const StepCtl &c, const DevStats &s, int ok, int e
   return ok;
 }
 
+#ifdef __CUDACC__
+// |u_d| + c of one conservative state for d < ndim (Sec. 3.3), with the FP64
+// mixture thermodynamics of Sec. 2: p = (rho e - Pi)/Gamma,
+// pbar = Pi/(Gamma + 1), rho c^2 = (1 + 1/Gamma)(p + pbar).  Every FP64
+// reduction of max(|u_d| + c) (single grids, Dirichlet states, batched
+// problems) uses this one function, so that they agree bit for bit.
+__device__ __forceinline__ void state_wavespeeds(double a1r1, double a2r2, const double *m, double E, double a1,
+                                                 int ndim, const EosConst &e, double *s) {
+  const double rho = a1r1 + a2r2;
+  const double ir = 1.0 / rho;
+  double m2 = 0.0, v[3] = {0.0, 0.0, 0.0};
+  for (int j = 0; j < ndim; ++j) {
+    v[j] = m[j] * ir;
+    m2 = fma(m[j], v[j], m2);
+  }
+  const double rhoe = E - 0.5 * m2;
+  const double Gam = fma(a1, e.r1 - e.r2, e.r2);
+  const double Pi = a1 * e.q1;
+  const double iG = 1.0 / Gam;
+  const double p = (rhoe - Pi) * iG;
+  const double pb = Pi / (Gam + 1.0);
+  const double c = sqrt((1.0 + iG) * (p + pb) * ir);
+  for (int j = 0; j < ndim; ++j) s[j] = fabs(v[j]) + c;
+}
+#endif
+
+// Order of the directional sweeps of one mixed-precision RHS evaluation:
+// with MIXED_REVERSE_SWEEPS the last axis goes first and x last, so that
+// the sweep that carries the SSPRK3 combine (its extra W^n and L reads and
+// the state write) is the x sweep, whose tiles read and write whole rows.
+// The first sweep of an RHS fills the node cache and counts inadmissible
+// inputs; the FP64 path keeps the order x, y, z.
+#ifndef MIXED_REVERSE_SWEEPS
+#define MIXED_REVERSE_SWEEPS 1
+#endif
+__host__ __device__ constexpr int mixed_first_dir(int ndim) { return MIXED_REVERSE_SWEEPS ? ndim - 1 : 0; }
+
 enum Epilogue {
   EPI_WRITE = 0,     // L  = contribution
   EPI_ACCUM = 1,     // L += contribution

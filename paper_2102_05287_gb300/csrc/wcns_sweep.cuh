@@ -1036,6 +1036,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
   for (int j = 0; j < NDIM; ++j) smax_local[j] = 0.0;
   int midpoints_done = 0;
   const double idx_ = geo.inv_dx();
+  const bool has_a = (__double_as_longlong(a.rk_a) << 1) != 0;  // a != 0, an integer test
   for (int q = tid; q < T::TL * (T::TM - 1); q += T::THREADS) {
     const int l = DIR == 0 ? q / (T::TM - 1) : q % T::TL;
     const int m = DIR == 0 ? q % (T::TM - 1) : q / T::TL;
@@ -1062,7 +1063,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         const double tot = a.read_L ? a.L[(long long)f * N + idx] + upd[f] : upd[f];
-        const double wn = a.rk_a != 0.0 ? a.Wn[(long long)f * N + idx] : 0.0;
+        const double wn = has_a ? a.Wn[(long long)f * N + idx] : 0.0;
         w[f] = a.rk_a * wn + a.rk_b * (sm.W[f * T::NN + ns] + dt * tot);
         finite = finite && finite64(w[f]);
         a.W_out[(long long)f * N + idx] = w[f];
