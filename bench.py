@@ -30,9 +30,9 @@ Rooflines (the path has no dense contraction; it is ALU bound):
   --workload riemann_batch  step-level fractions of the batched mode
   --workload bubble_3d      per-sweep fractions of the 3D solvers
 
-Other workloads (--workload): convergence, riemann_batch, bubble_3d, stress,
-full_runs, precision_2048 (the headline's workload with more error
-statistics); each prints its own JSON line.
+Other workloads (--workload): convergence, riemann_batch, bubble_batch_2d,
+bubble_3d, stress, full_runs, precision_2048 (the headline's workload with
+more error statistics); each prints its own JSON line.
 
 Multi-GPU (torchrun, one rank per GPU): independent replicas of the
 workload, one per rank (weak scaling; no data-path collective).  Rank 0
@@ -73,8 +73,8 @@ def parse():
     ap.add_argument("--nprob", type=int, default=4096,
                     help="riemann_batch: number of problems (4096 is the workload; fewer for profiling)")
     ap.add_argument("--workload", default="shock_bubble",
-                    choices=["shock_bubble", "precision_2048", "convergence", "riemann_batch", "bubble_3d", "stress",
-                             "full_runs"],
+                    choices=["shock_bubble", "precision_2048", "convergence", "riemann_batch", "bubble_batch_2d",
+                             "bubble_3d", "stress", "full_runs"],
                     help="shock_bubble (default): the headline line; the others measure the remaining "
                          "workloads and print their own JSON line")
     return ap.parse_args()
@@ -684,18 +684,20 @@ def algorithmic_ops_1d(rb=None):
     return _opcount_table("riemann_batch")
 
 
-def batch_roofline(ops, peaks, prec, ms_per_step, cells):
+def batch_roofline(ops, peaks, prec, ms_per_step, cells, ndim=1):
     """Step-level roofline fraction of the batched mode: the algorithmic
-    work of three RHS evaluations over all cells (every add, mul, min/max,
-    division and square root one flop) at the FP64 pipe's measured rate
-    (FP64) or at the two pipes' rates (mixed, as mixed_roofline), over the
-    whole step's time (the per-problem dt kernel included)."""
+    work of three RHS evaluations over all cells and directions (every add,
+    mul, min/max, division and square root one flop) at the FP64 pipe's
+    measured rate (FP64) or at the two pipes' rates (mixed, as
+    mixed_roofline), over the whole step's time (the per-problem dt kernel
+    included)."""
+    sweeps = 3 * ndim
     if prec == "mixed":
-        r = mixed_roofline(ops, peaks, ms_per_step / 3.0, cells, fallbacks=None)
-        r["note"] = "batched mixed step: " + r["note"] + "; time = one third of the step"
+        r = mixed_roofline(ops, peaks, ms_per_step / sweeps, cells, fallbacks=None)
+        r["note"] = "batched mixed step: " + r["note"] + "; time = the step over its %d sweeps" % sweeps
         return r
-    r = fp64_roofline(ops, peaks, ms_per_step / 3.0, cells, "batch_sweep_kernel<false, ...> (one stage)")
-    r["note"] = "batched FP64 step, time = one third of the step (dt kernel included): " + r["note"]
+    r = fp64_roofline(ops, peaks, ms_per_step / sweeps, cells, "batched FP64 sweeps (the whole step)")
+    r["note"] = ("batched FP64 step, time = the step over its %d sweeps (dt kernel included): " % sweeps) + r["note"]
     return r
 
 
@@ -751,6 +753,60 @@ def workload_batch(args):
            "sample": "one SSPRK3 step of 32 seeded problems of the batch (%d cells), single thread, %.1f s"
                      % (cells, el)}
     print(json.dumps({"workload": "riemann_batch_%d" % len(rb.sizes), "problems": len(rb.sizes), "cells": total,
+                      "steps": args.steps, "warmup": args.warmup, "results": res,
+                      "mixed_speedup_vs_fp64": res["fp64"]["ms_per_step"] / res["mixed"]["ms_per_step"],
+                      "mixed_vs_fp64_after_steps": err, "cpu_baseline": cpu}), flush=True)
+
+
+def workload_batch_2d(args):
+    """Independent 2D shock / air-bubble problems of uneven sizes (1024 by
+    default; 32..256 cells an axis, log-uniform, drawn separately, seed 5):
+    one persistent launch per direction and stage, CUDA-graph step,
+    autotuned persistent grid; FP64 and mixed."""
+    import numpy as np
+    import torch
+    from oracle import Oracle
+    from paper_2102_05287_gb300 import problems as P
+    from paper_2102_05287_gb300.wcns import Batch
+    nprob = args.nprob if args.nprob != 4096 else 1024
+    gb = P.bubble_batch_2d(nprob=nprob, seed=5, nmin=32, nmax=256)
+    total = int(gb.offsets[-1])
+    ops = algorithmic_ops(0, 0)
+    peaks = load_peaks()
+    res, states = {}, {}
+    for prec in ("fp64", "mixed"):
+        b = Batch.grids(gb.sizes, gb.lo, gb.hi, gb.bcs, precision=prec, **gb.eos)
+        W = torch.from_numpy(gb.W).cuda()
+        b.advance(W, args.warmup, cfl=0.5)  # includes the autotuning run
+        torch.cuda.synchronize()
+        e0, e1 = _events(torch)
+        l0 = b.launches()
+        e0.record()
+        b.advance(W, args.steps, cfl=0.5)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        res[prec] = {"ms_per_step": ms, "cell_stage_updates_per_s": 3 * total / (ms * 1e-3),
+                     "tuning": b.tuning(), "launches_per_step": (b.launches() - l0) / args.steps,
+                     "stats": b.stats(), "roofline": batch_roofline(ops, peaks, prec, ms, total, ndim=2)}
+        states[prec] = W.cpu()
+        b.close()
+    err = _errors(states["mixed"], states["fp64"], gb.eos, 2)
+    # the oracle on the host: one CFL step of 64 seeded problems of the batch
+    picks = np.random.default_rng(0).choice(nprob, min(64, nprob), replace=False)
+    cells, t0 = 0, time.perf_counter()
+    for k in picks:
+        nx, ny = (int(v) for v in gb.sizes[k])
+        W0 = np.ascontiguousarray(gb.problem(k))
+        o = Oracle((nx, ny), (0.0, 0.0), (1.0, 1.0), gb.bcs, **gb.eos)
+        sm = o.max_wavespeed(W0)
+        o.rk3_step(W0, 0.5 / (sm[0] * nx + sm[1] * ny))
+        cells += nx * ny
+    el = time.perf_counter() - t0
+    cpu = {"value": 3 * cells / el, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
+           "sample": "one SSPRK3 step of %d seeded problems of the batch (%d cells), single thread, %.1f s"
+                     % (len(picks), cells, el)}
+    print(json.dumps({"workload": "bubble_batch_2d_%d" % nprob, "problems": nprob, "cells": total,
                       "steps": args.steps, "warmup": args.warmup, "results": res,
                       "mixed_speedup_vs_fp64": res["fp64"]["ms_per_step"] / res["mixed"]["ms_per_step"],
                       "mixed_vs_fp64_after_steps": err, "cpu_baseline": cpu}), flush=True)
@@ -1013,7 +1069,8 @@ def main():
     args = parse()
     if args.workload != "shock_bubble":
         {"precision_2048": workload_precision, "convergence": workload_convergence,
-         "riemann_batch": workload_batch, "bubble_3d": workload_3d, "stress": workload_stress,
+         "riemann_batch": workload_batch, "bubble_batch_2d": workload_batch_2d, "bubble_3d": workload_3d,
+         "stress": workload_stress,
          "full_runs": workload_full_runs}[args.workload](args)
         return
     world, rank, local = dist_setup(args)

@@ -276,9 +276,9 @@ const char *wcns_strerror(int status);
 void wcns_destroy(wcns_handle *h);
 
 /* ------------------------------------------------------------------------
- * Batched mode: many independent 1D problems advanced together.
- * Each problem k has ncells[k] cells on [lo[k], hi[k]] with the boundary
- * kinds bc_lo / bc_hi (TRANSMISSIVE or PERIODIC), and shares the fluid
+ * Batched mode: many independent 1D or 2D problems advanced together.
+ * In 1D each problem k has ncells[k] cells on [lo[k], hi[k]] with the boundary
+ * kinds bc_lo / bc_hi (TRANSMISSIVE, PERIODIC or SYMMETRY), and shares the fluid
  * pair.  States are packed one after another: the packed device array has
  * 5 rows of total = sum(ncells) doubles (SoA [5][total]); problem k
  * occupies columns offsets[k] .. offsets[k] + ncells[k] - 1 with
@@ -288,27 +288,52 @@ void wcns_destroy(wcns_handle *h);
 typedef struct wcns_batch wcns_batch;
 
 /* ncells: host array of nprob sizes (each >= 1); lo/hi: host arrays of
- * nprob doubles; bc_lo/bc_hi: TRANSMISSIVE or PERIODIC (both periodic or
- * neither).  Copies the problem table and one (problem, tile) work list per
+ * nprob doubles; bc_lo/bc_hi: TRANSMISSIVE, PERIODIC (both periodic or
+ * neither) or SYMMETRY (then every problem needs >= 3 cells).  Copies the problem table and one (problem, tile) work list per
  * candidate tile length to the device and allocates the stage states and a
  * tuning copy (four packed states in all). */
 int wcns_batch_create(int nprob, const int *ncells, const double *lo, const double *hi, int bc_lo,
                       int bc_hi, double gamma_g, double gamma_l, double pinf_l, wcns_batch **out);
+/* Problems of one or two dimensions (Sec. 3.3: each problem takes its own
+ * CFL step dt_k = cfl / sum_d max(|u_d| + c)/dx_{k,d} and its own
+ * directional split lambda_d).  n, lo and hi are HOST arrays of
+ * nprob * ndim values, problem-major (n[k * ndim + d]; d = 0 is x), each
+ * n >= 1 (and <= 2^20 an axis in 2D), hi > lo.  bcs holds one boundary set
+ * for every problem: TRANSMISSIVE, PERIODIC (both faces of an axis) or
+ * SYMMETRY (n >= 3 on that axis); DIRICHLET is not provided in batches
+ * (WCNS_E_INVALID_ARG).  Packed state: nf = ndim + 4 rows of total =
+ * sum_k prod_d n[k][d] doubles; problem k occupies columns offsets[k] ..
+ * offsets[k] + prod_d n[k][d] - 1 (offsets[k] = the cells of the problems
+ * before it), stored x fastest like a single grid's state.  ndim = 1 is
+ * wcns_batch_create with the axis-0 kinds of bcs; ndim = 3 returns
+ * WCNS_E_UNSUPPORTED.  In 2D every stage is one persistent launch per
+ * direction over a work list of (problem, tile) (x tiles of 4 rows x 58
+ * cells, y tiles of 8 columns x 26 cells), and the device holds the
+ * problem tables, three packed states and the RHS accumulator besides the
+ * caller's, a tuning copy, and the mixed sweeps' node cache (24 bytes a
+ * cell).  A problem advanced in a batch equals the same problem advanced
+ * alone through wcns_create / wcns_advance_steps, step for step. */
+int wcns_batch_create_grids(int ndim, int nprob, const int *n, const double *lo, const double *hi,
+                            const wcns_bcs *bcs, double gamma_g, double gamma_l, double pinf_l,
+                            wcns_batch **out);
 int wcns_batch_set_options(wcns_batch *b, const wcns_options *opt);
 /* Advance every problem by nsteps SSPRK3 steps in place (device array
  * W_packed).  Each stage is one persistent launch over all problems; one
  * step (dt update + three stages) is captured once into a CUDA graph and
  * replayed.  The first call tunes the tile length (63, 127 or 255 cells)
- * and the persistent grid (1, 2, 4 or 8 blocks per SM) by timing trial
- * steps on the tuning copy; make it before any stream capture of the
+ * and the persistent grid (1, 2, 4 or 8 blocks per SM; 2D: 1 up to the
+ * occupancy limit) by timing trial steps on the tuning copy; make it
+ * before any stream capture of the
  * caller's.  t_out: optional DEVICE array of nprob doubles; each problem's
  * step sizes are added to it.  Ordered after the caller's pending work on
  * the options' stream, and that stream waits for it; synchronises once at
  * the end and returns WCNS_E_NONFINITE / WCNS_E_INADMISSIBLE as described
  * at the top (every problem takes all nsteps steps either way). */
 int wcns_batch_advance(wcns_batch *b, double *W_packed, int nsteps, double cfl, double *t_out);
-/* The autotuner's choice: cells per tile and persistent grid size;
- * WCNS_E_UNSUPPORTED before the first advance. */
+/* The autotuner's choice: cells per tile and persistent grid size (2D:
+ * the cells of an x tile and the blocks of the persistent sweeps before
+ * the cap by their work lists); WCNS_E_UNSUPPORTED before the first
+ * advance. */
 int wcns_batch_tuning(const wcns_batch *b, int *tile_cells, int *grid);
 int wcns_batch_get_stats(wcns_batch *b, wcns_stats *out);
 long long wcns_batch_total_cells(const wcns_batch *b);

@@ -532,7 +532,7 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
     const double dt0 = geo.dt(), lam0 = geo.lam(), bdt0 = a.rk_b * dt0;
     sm.scal[0] = dt0;
     sm.scal[1] = lam0;
-    sm.scal[2] = bdt0 * a.l_unit;  // multiplies the L array (see SweepArgs::l_raw)
+    sm.scal[2] = bdt0 * geo.l_unit();  // multiplies the L array (see SweepArgs::l_raw)
     sm.scal[3] = bdt0 * geo.inv_dx();
     reinterpret_cast<float *>(sm.scal + 4)[0] = (float)(2.0 * lam0);
     *sm.nslow = 0u;
@@ -918,7 +918,7 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
       } else {
 #pragma unroll
         for (int f = 0; f < NF; ++f)
-          a.L[(long long)f * N + idx] = fma(diff[f], a.accum_scale, a.L[(long long)f * N + idx]);
+          a.L[(long long)f * N + idx] = fma(diff[f], geo.accum_scale(), a.L[(long long)f * N + idx]);
       }
     } else {
       const int ns = nslot(l, m + 3);

@@ -724,6 +724,9 @@ struct GridGeo {
     return a.ctl->dt * tsum / __longlong_as_double(a.ctl->smax[a.stage][DIR]);
   }
   __device__ unsigned long long *smax_slot(int j) const { return &a.ctl->smax[a.stage + 1][j]; }
+  // mixed path: scaling of the L array (see SweepArgs::l_raw)
+  __device__ double l_unit() const { return a.l_unit; }
+  __device__ double accum_scale() const { return a.accum_scale; }
 };
 
 // ---------------------------------------------------------------------------

@@ -367,6 +367,74 @@ def riemann_batch(nprob=4096, seed=3, eos=WORKLOAD_EOS, nmin=128, nmax=8192, flo
                         dict(ratio=ratio, rho_l=rho_l, rho_g=rho_g, x0=x0))
 
 
+@dataclass
+class GridBatch:
+    sizes: np.ndarray       # (nprob, ndim) cells per axis, x first
+    offsets: np.ndarray     # first cell of each problem in the packed array
+    W: np.ndarray           # packed SoA (nf, total_cells), each problem x fastest
+    lo: np.ndarray          # (nprob, ndim)
+    hi: np.ndarray          # (nprob, ndim)
+    bcs: tuple
+    eos: dict
+    params: dict
+
+    def problem(self, k):
+        """Problem k's state as a (nf, ny, nx) array."""
+        nx, ny = (int(v) for v in self.sizes[k])
+        return self.W[:, int(self.offsets[k]):int(self.offsets[k + 1])].reshape(self.W.shape[0], ny, nx)
+
+
+def bubble_batch_2d(nprob=1024, seed=5, eos=WORKLOAD_EOS, nmin=32, nmax=256, floor=1e-6):
+    """Independent 2D shock / air-bubble problems of uneven sizes on [0,1]^2,
+    transmissive on every face (the 2D shock/bubble workload's physics in
+    problems of tens to hundreds of cells an axis): nx and ny log-uniform in
+    [nmin, nmax] (drawn separately); an air bubble (density U[1,100], p 1e5)
+    of radius U[0.1, 0.25] centred at U[0.4, 0.6]^2 with a tanh interface
+    about one cell wide, in water (density U[900,1100], p 1e5); a planar
+    shock at x = U[0.05, 0.12] with post-shock pressure 1e5 times a ratio
+    log-uniform in [10, 1e4] (Rankine-Hugoniot of the fixed-alpha mixture)."""
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(nmin), np.log(nmax), size=(nprob, 2))).astype(np.int64)
+    ratio = np.exp(rng.uniform(np.log(10.0), np.log(1e4), size=nprob))
+    rho_l = rng.uniform(900.0, 1100.0, size=nprob)
+    rho_g = rng.uniform(1.0, 100.0, size=nprob)
+    R = rng.uniform(0.1, 0.25, size=nprob)
+    ctr = rng.uniform(0.4, 0.6, size=(nprob, 2))
+    xs = rng.uniform(0.05, 0.12, size=nprob)
+    ncell = sizes[:, 0] * sizes[:, 1]
+    offsets = np.zeros(nprob + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum(ncell)
+    total = int(offsets[-1])
+    a1 = np.empty(total)
+    a1r1 = np.empty(total)
+    a2r2 = np.empty(total)
+    u = np.empty(total)
+    p = np.empty(total)
+    gb, pb = mixture_params(eos, 1 - floor)
+    for k in range(nprob):
+        nx, ny = int(sizes[k, 0]), int(sizes[k, 1])
+        X, Y = np.meshgrid(_centers(nx, 0.0, 1.0), _centers(ny, 0.0, 1.0), indexing="xy")
+        r = np.hypot(X - ctr[k, 0], Y - ctr[k, 1])
+        h = min(1.0 / nx, 1.0 / ny)
+        a_gas = floor + (1 - 2 * floor) * 0.5 * (1 - np.tanh((r - R[k]) / h))
+        a = 1.0 - a_gas
+        rho_pre = (1 - floor) * rho_l[k] + floor * rho_g[k]
+        rho_post, u_post, _ = stiffened_shock(rho_pre, 1e5, 1e5 * ratio[k], gb, pb)
+        comp = rho_post / rho_pre
+        post = X < xs[k]
+        sl = slice(int(offsets[k]), int(offsets[k + 1]))
+        a1[sl] = a.ravel()
+        a1r1[sl] = (a * np.where(post, rho_l[k] * comp, rho_l[k])).ravel()
+        a2r2[sl] = ((1 - a) * np.where(post, rho_g[k] * comp, rho_g[k])).ravel()
+        u[sl] = np.where(post, u_post, 0.0).ravel()
+        p[sl] = np.where(post, 1e5 * ratio[k], 1e5).ravel()
+    W = conservative(eos, a1r1, a2r2, [u, np.zeros(total)], p, a1)
+    lo = np.zeros((nprob, 2))
+    hi = np.ones((nprob, 2))
+    return GridBatch(sizes, offsets, W, lo, hi, (("transmissive", "transmissive"),) * 2, dict(eos),
+                     dict(ratio=ratio, rho_l=rho_l, rho_g=rho_g, R=R, centre=ctr, x_shock=xs))
+
+
 def random_admissible(shape_n, eos=WORKLOAD_EOS, seed=0, jumps=True):
     """Random admissible states on a grid of shape n (x first): smooth random
     fields plus, if ``jumps``, a few material/pressure discontinuities.

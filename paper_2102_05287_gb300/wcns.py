@@ -29,7 +29,7 @@ EXPORTS = [
     "wcns_advance_steps_host", "wcns_get_stats", "wcns_reset_stats", "wcns_nfields", "wcns_ncells",
     "wcns_launch_count", "wcns_rk3_step_noalloc", "wcns_profile_enable", "wcns_profile_read", "wcns_strerror", "wcns_destroy", "wcns_batch_create", "wcns_batch_set_options",
     "wcns_batch_advance", "wcns_batch_tuning", "wcns_batch_get_stats", "wcns_batch_total_cells", "wcns_batch_launch_count",
-    "wcns_batch_destroy",
+    "wcns_batch_destroy", "wcns_batch_create_grids",
 ]
 
 
@@ -110,6 +110,7 @@ def load(path=LIB_PATH):
         "wcns_batch_total_cells": ([vp], ll),
         "wcns_batch_launch_count": ([vp], ll),
         "wcns_batch_destroy": ([vp], None),
+        "wcns_batch_create_grids": ([i, i, P(i), P(d), P(d), P(wcns_bcs), d, d, d, P(vp)], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -300,23 +301,57 @@ class Solver:
 
 
 class Batch:
-    """Many independent 1D problems advanced together (packed SoA [5][total])."""
+    """Many independent problems advanced together.  1D (the default form):
+    Batch(ncells, lo, hi, bc_lo, bc_hi, ...), packed SoA (5, total).  Any
+    dimension: Batch.grids(n, lo, hi, bcs, ...) with n, lo, hi of shape
+    (nprob, ndim) (x first) and one boundary set for all problems, packed SoA
+    (ndim + 4, total), each problem x fastest."""
 
     def __init__(self, ncells, lo, hi, bc_lo, bc_hi, gamma_g, gamma_l, pinf_l, precision="fp64",
-                 scheme="pp-wcns-is", stream=None):
-        import torch
+                 scheme="pp-wcns-is", stream=None, _handle=None, _nf=5):
         lib = load()
         self.lib = lib
         nprob = len(ncells)
         self.nprob = nprob
-        nc = (C.c_int * nprob)(*[int(x) for x in ncells])
-        lo_ = (C.c_double * nprob)(*[float(x) for x in lo])
-        hi_ = (C.c_double * nprob)(*[float(x) for x in hi])
-        h = C.c_void_p()
-        _check(lib.wcns_batch_create(nprob, nc, lo_, hi_, _BC[bc_lo] if isinstance(bc_lo, str) else bc_lo,
-                                     _BC[bc_hi] if isinstance(bc_hi, str) else bc_hi, gamma_g, gamma_l, pinf_l,
-                                     C.byref(h)), "wcns_batch_create")
+        self.nf = _nf
+        if _handle is None:
+            nc = (C.c_int * nprob)(*[int(x) for x in ncells])
+            lo_ = (C.c_double * nprob)(*[float(x) for x in lo])
+            hi_ = (C.c_double * nprob)(*[float(x) for x in hi])
+            h = C.c_void_p()
+            _check(lib.wcns_batch_create(nprob, nc, lo_, hi_, _BC[bc_lo] if isinstance(bc_lo, str) else bc_lo,
+                                         _BC[bc_hi] if isinstance(bc_hi, str) else bc_hi, gamma_g, gamma_l,
+                                         pinf_l, C.byref(h)), "wcns_batch_create")
+        else:
+            h = _handle
         self.h = h
+        self._configure(precision, scheme, stream)
+
+    @classmethod
+    def grids(cls, n, lo, hi, bcs, gamma_g, gamma_l, pinf_l, precision="fp64", scheme="pp-wcns-is",
+              stream=None):
+        import numpy as np
+        n = np.asarray(n, dtype=np.int64)
+        nprob, ndim = n.shape
+        lo = np.asarray(lo, dtype=np.float64).reshape(nprob, ndim)
+        hi = np.asarray(hi, dtype=np.float64).reshape(nprob, ndim)
+        b = wcns_bcs()
+        for d in range(ndim):
+            for s in range(2):
+                k = bcs[d][s]
+                b.kind[d][s] = _BC[k] if isinstance(k, str) else int(k)
+        n_ = (C.c_int * (nprob * ndim))(*[int(x) for x in n.ravel()])
+        lo_ = (C.c_double * (nprob * ndim))(*[float(x) for x in lo.ravel()])
+        hi_ = (C.c_double * (nprob * ndim))(*[float(x) for x in hi.ravel()])
+        h = C.c_void_p()
+        _check(load().wcns_batch_create_grids(int(ndim), int(nprob), n_, lo_, hi_, C.byref(b), gamma_g, gamma_l,
+                                              pinf_l, C.byref(h)), "wcns_batch_create_grids")
+        return cls([0] * nprob, None, None, None, None, gamma_g, gamma_l, pinf_l, precision=precision,
+                   scheme=scheme, stream=stream, _handle=h, _nf=ndim + 4)
+
+    def _configure(self, precision, scheme, stream):
+        import torch
+        lib, h = self.lib, self.h
         o = wcns_default_options()
         o.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
         o.scheme = _SCHEME[scheme] if isinstance(scheme, str) else int(scheme)
@@ -328,8 +363,8 @@ class Batch:
         self.total = int(lib.wcns_batch_total_cells(h))
 
     def advance(self, W, nsteps, cfl=0.5, t=None):
-        if tuple(W.shape) != (5, self.total):
-            raise ValueError("packed state must have shape (5, %d)" % self.total)
+        if tuple(W.shape) != (self.nf, self.total):
+            raise ValueError("packed state must have shape (%d, %d)" % (self.nf, self.total))
         if t is not None and tuple(t.shape) != (self.nprob,):
             raise ValueError("t must have shape (%d,): one time per problem" % self.nprob)
         tp = _ptr(t) if t is not None else None
