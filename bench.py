@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--ny", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--n3d", type=int, default=384,
+                    help="bubble_3d: cells an axis (384 is the workload; smaller grids for profiling)")
     ap.add_argument("--nprob", type=int, default=4096,
                     help="riemann_batch: number of problems (4096 is the workload; fewer for profiling)")
     ap.add_argument("--workload", default="shock_bubble",
@@ -821,7 +823,7 @@ def workload_3d(args):
     import torch
     from paper_2102_05287_gb300 import problems as P
     from paper_2102_05287_gb300.wcns import Solver
-    pr = P.bubble_collapse_3d(384)
+    pr = P.bubble_collapse_3d(args.n3d)
     ops = _opcount_table("bubble_collapse_3d")
     peaks = load_peaks()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -877,7 +879,7 @@ def workload_3d(args):
            "kind": "oracle",
            "sample": "one SSPRK3 step of the same problem at 48^3 (single thread, %.1f s), "
                      "rate extrapolated to 384^3" % el}
-    print(json.dumps({"workload": "bubble_collapse_3d_384", "cells": pr.ncells, "results": res,
+    print(json.dumps({"workload": "bubble_collapse_3d_%d" % args.n3d, "cells": pr.ncells, "results": res,
                       "mixed_speedup_vs_fp64": res["fp64"]["ms_per_step"] / res["mixed"]["ms_per_step"],
                       "mixed_vs_fp64_after_steps": err, "cpu_baseline": cpu}),
           flush=True)

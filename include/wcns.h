@@ -272,6 +272,15 @@ typedef struct {
 int wcns_profile_enable(wcns_handle *h, int capacity);
 int wcns_profile_read(wcns_handle *h, wcns_profile *out);
 
+/* Verification aid (not part of the method; the paper has no
+ * counterpart): q[i] = a[i] / b[i] for n elements of the DEVICE arrays a,
+ * b, q, computed with the FP64 sweeps' own division routine (an FP32
+ * reciprocal seed, one Newton-Raphson step and one remainder correction,
+ * within one unit in the last place of the IEEE quotient; IEEE division
+ * outside its range), so that tests can compare it with CUDA's division.
+ * Asynchronous on `stream` (a cudaStream_t, NULL = default). */
+int wcns_check_division(const double *a, const double *b, double *q, long long n, void *stream);
+
 const char *wcns_strerror(int status);
 void wcns_destroy(wcns_handle *h);
 

@@ -97,11 +97,47 @@ __device__ __forceinline__ bool positive64(double x) {
   return b > 0 && b <= 0x7FF0000000000000ll;
 }
 
+// a / b in FP64 with five FP64-pipe operations (the FP64 pipe is GB300's
+// scarce one; an IEEE division takes about nine): a reciprocal seed y0
+// from the approximate FP32 reciprocal of b's leading mantissa bits, b's
+// exponent and sign applied with integer operations (|y0 b - 1| < 2^-21);
+// one Newton-Raphson step y1 = y0 + y0 (1 - b y0) (relative error below
+// 2^-41); the quotient q0 = a y1; and one correction q1 = q0 + y1 (a - b q0)
+// with the remainder from a fused multiply-add (Markstein, IBM J. Res.
+// Dev. 34 (1990) 111), which leaves q1 within one unit in the last place
+// of a / b.  Operands outside the range where that holds (b zero,
+// subnormal, not finite or above 2^1021; a not finite or below 2^-959, where
+// the remainder would underflow; a / b near the overflow threshold) take the
+// IEEE division, except a zero numerator over a finite nonzero b, whose
+// quotient is the signed zero a * b.
+__device__ __forceinline__ double div_nr(double a, double b) {
+  const unsigned long long ub = (unsigned long long)__double_as_longlong(b);
+  const unsigned long long ua = (unsigned long long)__double_as_longlong(a);
+  const unsigned int eb = (unsigned int)(ub >> 52) & 0x7FFu;
+  const unsigned int ea = (unsigned int)(ua >> 52) & 0x7FFu;
+  if (eb - 1u >= 2044u || ea - 64u >= 1983u || (int)ea - (int)eb > 1020) {
+    if ((ua << 1) == 0 && (ub << 1) != 0 && eb != 0x7FFu) return a * b;
+    return a / b;
+  }
+  // m = b's mantissa in [1, 2) as an FP32 value (leading 24 bits)
+  const float mf = __uint_as_float(0x3F800000u | (unsigned int)((ub >> 29) & 0x7FFFFFull));
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(mf));  // ~1/m in (0.5, 1]
+  const unsigned int rb = __float_as_uint(r);
+  const unsigned long long er = (rb >> 23) & 0xFFu;  // 126 or 127
+  // y0 = sign(b) r 2^-(eb - 1023): FP64 exponent field er - 127 + 1023 - (eb - 1023)
+  const double y0 = __longlong_as_double((long long)((ub & 0x8000000000000000ull) | ((er + 1919ull - eb) << 52) |
+                                                     ((unsigned long long)(rb & 0x7FFFFFu) << 29)));
+  const double y1 = fma(y0, fma(-b, y0, 1.0), y0);
+  const double q0 = a * y1;
+  return fma(y1, fma(-b, q0, a), q0);
+}
+
 template <class R>
 struct Prec;
 template <>
 struct Prec<double> {
-  static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+  static __device__ __forceinline__ double div(double a, double b) { return div_nr(a, b); }
   static __device__ __forceinline__ double clampratio(double r) { return r; }
   static __device__ __forceinline__ double sqrt_(double a) { return sqrt(a); }
 };
@@ -250,7 +286,7 @@ __device__ __forceinline__ double wenois_tail_x4(double s0x3, double s1, double 
   const double den = fma(Q, fma(3.0, A0, A1), Pb * fma(2.0, B2, B3));
   // 1e-280 < den < 1e280, as integer compares (den is a sum of products of non-negative terms)
   const long long db = __double_as_longlong(den);
-  if (db > __double_as_longlong(1e-280) && db < __double_as_longlong(1e280)) return num / den;
+  if (db > __double_as_longlong(1e-280) && db < __double_as_longlong(1e280)) return div_nr(num, den);
   // outside that range: the weights from the ratios tau / b, as printed
   const double r01 = tau / b01;
   const double v0 = 1.0 + (tau / b0) * r01, v1 = 1.0 + (tau / b1) * r01;
@@ -791,7 +827,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
     //   rho c^2 = gbar (p + pbar) = ((Gamma+1) rho e - Pi)/Gamma^2,
     // with one division for 1/rho and one for 1/(Gamma (Gamma+1)).
     const double rho = w[0] + w[1];
-    const double ir = 1.0 / rho;
+    const double ir = div_nr(1.0, rho);
     double v[NDIM], m2 = 0.0;
 #pragma unroll
     for (int j = 0; j < NDIM; ++j) {
@@ -801,7 +837,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
     const double rhoe = w[E] - 0.5 * m2;
     const double Gam = mixGamma(eos, w[A]);
     const double Pi = mixPi(eos, w[A]);
-    const double x = 1.0 / (Gam * (Gam + 1.0));
+    const double x = div_nr(1.0, Gam * (Gam + 1.0));
     const double iG = (Gam + 1.0) * x;
     const double p = (rhoe - Pi) * iG;
     const double c = sqrt(((Gam + 1.0) * rhoe - Pi) * (iG * iG) * ir);
@@ -883,7 +919,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
       const double ar2 = 0.5 * (Wi[1] + Wi1[1]);
       const double rb = ar1 + ar2;
       const double cb = 0.5 * (sm.c[ni] + sm.c[ni1]);
-      const double irc = 1.0 / (rb * cb);
+      const double irc = div_nr(1.0, rb * cb);
       const double ic = irc * rb;  // 1/c without another division
       const double k1 = ar1 * irc * ic, k2 = ar2 * irc * ic;
       double U[6][NF];
@@ -987,7 +1023,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
       for (int side = 0; side < 2; ++side) {
         const double *V = side ? VR : VL;
         const double Gam = mixGamma(eos, V[A]);
-        cs[side] = sqrt(((Gam + 1.0) * V[E] + mixPi(eos, V[A])) / (Gam * (V[0] + V[1])));
+        cs[side] = sqrt(div_nr((Gam + 1.0) * V[E] + mixPi(eos, V[A]), Gam * (V[0] + V[1])));
       }
       hllc<NDIM, DIR, double>(WL, VL + 2, VL[E], VL[0] + VL[1], cs[0], WR, VR + 2, VR[E], VR[0] + VR[1], cs[1],
                               Gt, ut);
@@ -1075,13 +1111,13 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
       // max(|u_d| + c) of the new state (Sec. 3.3) for the next stage:
       // c^2 = ((Gamma+1) rho e - Pi)/(Gamma^2 rho)
       const double rho = w[0] + w[1];
-      const double ir = 1.0 / rho;
+      const double ir = div_nr(1.0, rho);
       double m2 = 0.0;
 #pragma unroll
       for (int j = 0; j < NDIM; ++j) m2 = fma(w[2 + j], w[2 + j], m2);
       const double rhoe = w[E] - 0.5 * m2 * ir;
       const double Gam = mixGamma(eos, w[A]);
-      const double c = sqrt(((Gam + 1.0) * rhoe - mixPi(eos, w[A])) / (Gam * Gam * rho));
+      const double c = sqrt(div_nr((Gam + 1.0) * rhoe - mixPi(eos, w[A]), Gam * Gam * rho));
 #pragma unroll
       for (int j = 0; j < NDIM; ++j) {
         const double sj = fabs(w[2 + j] * ir) + c;
