@@ -786,6 +786,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
     const Line ln = geo.line(l);
     const int n = ln.n;
     const int pos = tile0 - 3 + s;
+    // no needed midpoint reads a node of a line beyond the grid or past the
+    // line's last ghost layer (the last, partial tile of a line)
+    if (!ln.valid || pos > n + 2) continue;
     double w[NF];
     bool dirichlet = false, flip = false;
     int src = pos;
@@ -878,6 +881,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
     const int si = m + 2;  // node i; node i+1 is m + 3
     // Tiles overlap by one midpoint: count limiter events once per midpoint.
     const Line lnm = geo.line(l);
+    // faces past the line's last face (partial tiles) and lines beyond the
+    // grid are used by no updated cell
+    if (!lnm.valid || tile0 + m > lnm.n) continue;
     const int cnt = (m < T::TM - 1 || tile0 + m == lnm.n) && tile0 + m <= lnm.n && lnm.valid;
     const int ni = S::nslot(l, si), ni1 = S::nslot(l, si + 1);
     double Wi[NF], Wi1[NF], vi[NDIM];
