@@ -113,6 +113,41 @@ def test_empty_and_oversized_inputs_are_rejected_without_a_gpu(lib):
     assert L.wcns_rk3_step_noalloc(ctypes.byref(g), ctypes.byref(b), 1.4, 4.4, 6e8, None, None, 1e-7) == E
 
 
+def test_grid_batch_and_division_check_host_rejections(lib):
+    """wcns_batch_create_grids refuses empty or inconsistent problem tables,
+    Dirichlet faces (not provided in batches), symmetry on a problem with
+    fewer than 3 cells, and three dimensions (unsupported);
+    wcns_check_division refuses a negative length or missing arrays.  All
+    before any CUDA call."""
+    from paper_2102_05287_gb300 import wcns
+    L = wcns.load()
+    E = wcns.WCNS_E_INVALID_ARG
+    b = wcns.wcns_bcs()
+    bh = ctypes.c_void_p()
+    n = (ctypes.c_int * 4)(8, 6, 10, 12)
+    lo = (ctypes.c_double * 4)(0.0, 0.0, 0.0, 0.0)
+    hi = (ctypes.c_double * 4)(1.0, 1.0, 1.0, 1.0)
+
+    def create(ndim, nprob, nn=n, lo_=lo, hi_=hi):
+        return L.wcns_batch_create_grids(ndim, nprob, nn, lo_, hi_, ctypes.byref(b), 1.4, 4.4, 6e8, ctypes.byref(bh))
+    assert create(2, 0) == E
+    assert create(2, 2, nn=(ctypes.c_int * 4)(8, 0, 10, 12)) == E
+    assert create(2, 2, hi_=(ctypes.c_double * 4)(1.0, 0.0, 1.0, 1.0)) == E
+    assert create(3, 1, nn=(ctypes.c_int * 3)(4, 4, 4)) == wcns.WCNS_E_UNSUPPORTED
+    b.kind[1][0] = wcns.WCNS_BC_DIRICHLET
+    assert create(2, 2) == E
+    b.kind[1][0] = wcns.WCNS_BC_PERIODIC  # periodic on one face only
+    assert create(2, 2) == E
+    b.kind[1][0] = b.kind[1][1] = wcns.WCNS_BC_SYMMETRY
+    assert create(2, 2, nn=(ctypes.c_int * 4)(8, 2, 10, 12)) == E
+    assert L.wcns_batch_create_grids(2, 2, n, lo, hi, None, 1.4, 4.4, 6e8, ctypes.byref(bh)) == E
+    assert L.wcns_batch_create_grids(2, 2, n, lo, hi, ctypes.byref(b), 5.0, 4.4, 6e8, ctypes.byref(bh)) == E
+    assert not bh.value
+    assert L.wcns_check_division(None, None, None, -1, None) == E
+    assert L.wcns_check_division(None, None, None, 4, None) == E
+    assert L.wcns_check_division(None, None, None, 0, None) == wcns.WCNS_OK
+
+
 def test_plain_c_program_uses_the_boundary(lib, tmp_path):
     """The header is self-contained C99, and a C program linked against the
     library gets the documented answers from its host-side checks."""

@@ -28,12 +28,19 @@ NPROB = 72
 
 @pytest.fixture(scope="module")
 def gb():
+    # at least 3 cells an axis (symmetry faces need them)
     return P.bubble_batch_2d(nprob=NPROB, seed=7, nmin=8, nmax=48)
 
 
+BCS = {"transmissive": (("transmissive", "transmissive"), ("transmissive", "transmissive")),
+       "periodic_x_symmetry_y": (("periodic", "periodic"), ("symmetry", "transmissive"))}
+
+
+@pytest.mark.parametrize("bcs", sorted(BCS))
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_batch2d_equals_single_grid_runs(gb, precision):
-    b = Batch.grids(gb.sizes, gb.lo, gb.hi, gb.bcs, precision=precision, **gb.eos)
+def test_batch2d_equals_single_grid_runs(gb, precision, bcs):
+    bcs = BCS[bcs]
+    b = Batch.grids(gb.sizes, gb.lo, gb.hi, bcs, precision=precision, **gb.eos)
     W = torch.from_numpy(gb.W).cuda()
     t = torch.zeros(NPROB, dtype=torch.float64, device="cuda")
     steps = 6
@@ -47,7 +54,7 @@ def test_batch2d_equals_single_grid_runs(gb, precision):
     worst = 0.0
     for k in range(NPROB):
         nx, ny = (int(v) for v in gb.sizes[k])
-        s = Solver((nx, ny), tuple(gb.lo[k]), tuple(gb.hi[k]), gb.bcs, precision=precision, **gb.eos)
+        s = Solver((nx, ny), tuple(gb.lo[k]), tuple(gb.hi[k]), bcs, precision=precision, **gb.eos)
         Wk = torch.from_numpy(np.ascontiguousarray(gb.problem(k))).cuda()
         tk = s.advance_steps(Wk, steps, cfl=0.5)
         ref = Wk.cpu().numpy()
@@ -58,7 +65,8 @@ def test_batch2d_equals_single_grid_runs(gb, precision):
         assert abs(tt[k] - tk) <= 1e-14 * tk, (k, tt[k], tk)
         s.close()
     b.close()
-    print("2D batch of %d problems vs single grids (%s): worst relative difference %.1e" % (NPROB, precision, worst))
+    print("2D batch of %d problems vs single grids (%s, %s): worst relative difference %.1e" %
+          (NPROB, precision, bcs, worst))
 
 
 def test_batch2d_first_step_against_oracle(gb):
