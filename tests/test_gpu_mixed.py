@@ -98,6 +98,9 @@ CASES = [
     ((40, 36), (("dirichlet", "transmissive"), ("dirichlet", "symmetry"))),
     ((16, 14, 12), (("periodic", "periodic"), ("symmetry", "dirichlet"), ("transmissive", "symmetry"))),
     ((14, 13, 15), (("dirichlet", "symmetry"), ("transmissive", "transmissive"), ("periodic", "periodic"))),
+    # rows of 100 cells: the x sweep takes its 2 x 91 tile here (the 3 x 59
+    # tile needs as many blocks), while the small grids above take 3 x 59
+    ((100, 4, 6), (("transmissive", "symmetry"), ("periodic", "periodic"), ("transmissive", "transmissive"))),
 ]
 
 

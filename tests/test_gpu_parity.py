@@ -151,8 +151,10 @@ def test_rhs_2d_fp64(n, bcs, scheme):
         assert so[k] == sg[k], (k, so[k], sg[k])
 
 
-def test_rhs_3d_fp64():
-    n = (20, 18, 17)
+@pytest.mark.parametrize("n", [(20, 18, 17), (100, 4, 6)])
+def test_rhs_3d_fp64(n):
+    """The x sweep has two tiles, chosen per grid by block count: 3 x 80 for
+    (20, 18, 17), 2 x 123 for rows of 100 cells."""
     bcs = (("transmissive", "transmissive"), ("periodic", "periodic"), ("symmetry", "transmissive"))
     W = P.random_admissible(n, seed=14)
     o, s = pair(n, bcs)
