@@ -52,10 +52,13 @@ struct TileT {
   static constexpr int NN = TL * NS;     // nodes per block
   static constexpr int NM = TL * TM;     // midpoints per block
 };
-// Tile shapes (lines x midpoints, measured on GB300): x tiles 2 x 123
-// midpoints (1 x 123 in 1D), i.e. 256 (128) nodes for 256 (128) threads;
-// y/z tiles 8 x-columns x 59 midpoints in 2D (512 nodes, two per thread)
-// and 16 x 32 in 3D.
+// Tile shapes (lines x midpoints, measured on GB300): x tiles 1 x 123
+// midpoints, 128 nodes for 128 threads, in 1D and 2D, 2 x 123 (256 threads)
+// in 3D; y/z tiles 8 x-columns x 59 midpoints in 2D (512 nodes, two per
+// thread, 256 threads) and 8 x 32 in 3D (296 nodes for 128 threads).
+// 128-thread blocks run two to an SM, so one block's staging and barriers
+// overlap the other's arithmetic (2D x sweep 2 %, 3D y/z sweeps 4 % faster
+// than one 256-thread block of twice the lines).
 #ifndef FP64_TM_X
 #define FP64_TM_X 123
 #endif
@@ -66,9 +69,9 @@ struct TileT {
 #define FP64_3D_TM_X FP64_TM_X
 #endif
 template <int NDIM, int DIR>
-using Tile = TileT<(DIR == 0) ? (NDIM == 1 ? 1 : (NDIM == 3 ? FP64_3D_TL_X : 2)) : (NDIM == 2 ? 8 : 16),
+using Tile = TileT<(DIR == 0) ? (NDIM == 3 ? FP64_3D_TL_X : 1) : 8,
                    (DIR == 0) ? (NDIM == 3 ? FP64_3D_TM_X : FP64_TM_X) : (NDIM == 2 ? 59 : 32),
-                   (DIR == 0) ? (NDIM == 1 ? 128 : 256) : 256>;
+                   (DIR == 0) ? (NDIM == 3 ? 256 : 128) : (NDIM == 2 ? 256 : 128)>;
 
 // Integer tests on FP64 values (no FP64-pipe compare): finite, and
 // finite-and-nonnegative (-0 counts as nonnegative, NaN and infinities
@@ -661,6 +664,124 @@ __device__ int flux_limit(const EosConst &e, const LimTol &t, const double *Wi, 
   return flags;
 }
 
+// ---------------------------------------------------------------------------
+// FP32 certification of the limiter tests of the FP64 sweeps.  Where every
+// threshold test of Algorithms 1-6 passes, the limiters leave states and
+// fluxes as they are (theta = 1).  The functions below decide that in FP32
+// from truncated images of the FP64 operands, with an error bound that
+// covers the truncation, the FP32 evaluation and the FP64 evaluation of the
+// exact test: a test certified here passes in FP64 as well, so a certified
+// midpoint gets exactly the FP64 limiters' result.  Whatever is not
+// certified goes through interp_limit / flux_limit.
+// ---------------------------------------------------------------------------
+
+// FP32 image of an FP64 value from its high word alone (integer operations
+// only): sign, exponent and the leading 20 mantissa bits, truncated toward
+// zero, so |x - t(x)| < 2^-20 |x| and |t(x)| <= |x|.  Zero maps to 0; a
+// value below the FP32 normal range, at or above 2^128, or not finite maps
+// to a NaN, which fails every certification test.
+__device__ __forceinline__ float trunc32(double x) {
+  const unsigned int hi = (unsigned int)__double2hiint(x);
+  const unsigned int mag = hi & 0x7FFFFFFFu;
+  // FP64 exponent field in [897, 1150] <=> FP32 exponent field in [1, 254]
+  if (mag - 0x38100000u < 0x0FE00000u) return __uint_as_float((hi & 0x80000000u) | ((mag - 0x38000000u) << 3));
+  return (__double_as_longlong(x) << 1) == 0 ? 0.0f : __uint_as_float(0x7FC00000u);
+}
+
+// Error allowance 2^-18 m for a quantity of operand magnitude m: at least
+// three times the truncation error (2^-20), the FP32 roundings of the short
+// expressions below and the FP64 roundings of the exact tests together.
+__device__ __forceinline__ float cmargin(float m) { return 3.814697265625e-06f * m; }
+
+// Certify rho ctilde^2 = E - |m|^2 / (2 rho) - Pi / (Gamma + 1) >= eps (Sec.
+// 2) for a conservative state whose every component X_f lies within d[f] of
+// the FP32 value x[f], alpha certified inside [0, 1].  Errors propagated:
+// rho, the kinetic energy (through m and rho), pbar (through alpha, with
+// |d pbar / d alpha| = q1 (r2 + 1) / (Gamma + 1)^2 <= |q1| (|r2| + 1) on
+// [0, 1]; through the FP32 constants and Gamma + 1, whose rounding is
+// bounded by the magnitudes of its two terms) and the FP32 evaluation.
+template <int NDIM>
+__device__ __forceinline__ bool rct2_cert(const EosConst &e, const float *x, const float *d, float eps) {
+  constexpr int E = 2 + NDIM, A = 3 + NDIM;
+  const float rho = x[0] + x[1];
+  const float drho = d[0] + d[1] + cmargin(fabsf(rho));
+  const float rlo = rho - drho;
+  if (!(rlo > 0.0f) || !(rho < 1e30f)) return false;
+  float m2 = 0.0f, dm2 = 0.0f;
+#pragma unroll
+  for (int j = 0; j < NDIM; ++j) {
+    m2 = fmaf(x[2 + j], x[2 + j], m2);
+    dm2 = fmaf(2.0f * fabsf(x[2 + j]) + d[2 + j], d[2 + j], dm2);
+  }
+  const float ke = 0.5f * __fdividef(m2, rho);
+  const float dke = 0.5f * __fdividef(dm2, rlo) + __fdividef(ke * drho, rlo) + cmargin(ke);
+  const float al = x[A];
+  const float g0 = e.r2f + 1.0f, gd = e.drf * al;
+  const float G1 = g0 + gd;  // Gamma + 1 >= 1 for alpha in [0, 1]
+  if (!(G1 > 0.5f) || !(G1 < 1e30f)) return false;
+  const float pb = __fdividef(e.q1f * al, G1);
+  const float dpb = fabsf(e.q1f) * (fabsf(e.r2f) + 1.0f) * d[A] +
+                    cmargin(pb * (1.0f + __fdividef(g0 + fabsf(gd), G1)));
+  const float v = x[E] - ke - pb;
+  return v - (d[E] + dke + dpb + cmargin(fabsf(x[E]) + ke + pb)) >= eps;
+}
+
+// The five threshold tests of a conservative FP64 state W at their
+// tolerances (Algorithms 1-3, the quantities of node or interpolated state),
+// exactly as interp_limit decides them, with rho ctilde^2 certified in FP32
+// first and tested in FP64 only where that fails.
+template <int NDIM>
+__device__ __forceinline__ bool state_passes(const EosConst &e, const LimTol &t, const double *W) {
+  constexpr int NF = NDIM + 4, A = 3 + NDIM;
+  if (below64(W[0], t.eps_ar) || below64(W[1], t.eps_ar) || below64(W[A], t.eps_a) ||
+      below64(1.0 - W[A], t.eps_a))
+    return false;
+  float x[NF], d[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    x[f] = trunc32(W[f]);
+    d[f] = cmargin(fabsf(x[f]));
+  }
+  return rct2_cert<NDIM>(e, x, d, t.cert_rc) || !rct2_below<NDIM>(e, W, t.eps_rc);
+}
+
+// Certify that flux_limit leaves G^-, G^+ unchanged at a midpoint: the four
+// half states W_i - 2 lam (G^{HLLC,-} - F_i), W_{i+1} + 2 lam (G^{HLLC,+} -
+// F_{i+1}), W_i - 2 lam (G^- - F_i), W_{i+1} + 2 lam (G^+ - F_{i+1}) (Sec.
+// 5.2; F^alpha = 0) pass all five threshold tests.  GH / Gh: first- and
+// high-order fluxes, shared components (f < A); the alpha components of the
+// four split fluxes come separately.  l2f: 2 lam in FP32.
+template <int NDIM>
+__device__ __forceinline__ bool flux_certified(const EosConst &e, const LimTol &t, float l2f, const double *Wi,
+                                               const double *Wi1, const double *Fi, const double *Fi1,
+                                               const double *GH, const double *Gh, double GHmA, double GHpA,
+                                               double GmA, double GpA) {
+  constexpr int NF = NDIM + 4, A = 3 + NDIM;
+#pragma unroll
+  for (int st = 0; st < 4; ++st) {
+    const bool right = st & 1;  // W_{i+1} + 2 lam (.) else W_i - 2 lam (.)
+    const double *W = right ? Wi1 : Wi;
+    const double *F = right ? Fi1 : Fi;
+    const double *G = st < 2 ? GH : Gh;
+    const float sl = right ? l2f : -l2f;
+    float x[NF], d[NF];
+#pragma unroll
+    for (int f = 0; f < A; ++f) {
+      const float w = trunc32(W[f]), g = trunc32(G[f]), fl = trunc32(F[f]);
+      x[f] = fmaf(sl, g - fl, w);
+      d[f] = cmargin(fabsf(w) + l2f * (fabsf(g) + fabsf(fl)));
+    }
+    const float wa = trunc32(W[A]);
+    const float ga = trunc32(st == 0 ? GHmA : st == 1 ? GHpA : st == 2 ? GmA : GpA);
+    x[A] = fmaf(sl, ga, wa);
+    d[A] = cmargin(fabsf(wa) + l2f * fabsf(ga));
+    if (!(x[0] - d[0] >= t.cert_ar && x[1] - d[1] >= t.cert_ar && x[A] - d[A] >= t.cert_a &&
+          (1.0f - x[A]) - (d[A] + cmargin(1.0f)) >= t.cert_a && rct2_cert<NDIM>(e, x, d, t.cert_rc)))
+      return false;
+  }
+  return true;
+}
+
 // HCS reconstruction weights (Sec. 4.1, psi = 256/175):
 //   G^ = psi G~ - (101/420)(G_i + G_{i+1}) + (1/105)(G_{i-1} + G_{i+2})
 //        - (1/2100)(G_{i-2} + G_{i+3})
@@ -680,8 +801,11 @@ struct Smem {
   static constexpr int NODE_DOUBLES = 2 * NF + NDIM + 3;
   // per midpoint: shared flux components (NF-1), alpha flux of G^- and G^+
   static constexpr int MID_DOUBLES = NF + 1;
-  static constexpr size_t BYTES = sizeof(double) * (size_t)(NODE_DOUBLES * T::NN + MID_DOUBLES * T::NM);
+  // + per node: whether it passes the limiters' threshold tests
+  static constexpr size_t BYTES =
+      sizeof(double) * (size_t)(NODE_DOUBLES * T::NN + MID_DOUBLES * T::NM) + sizeof(int) * (size_t)T::NN;
   double *W, *vel, *p, *c, *rct, *G, *F, *am, *ap;
+  int *nok;
   __device__ Smem(double *base) {
     W = base;
     vel = W + NF * T::NN;
@@ -692,6 +816,7 @@ struct Smem {
     F = G + NF * T::NN;
     am = F + (NF - 1) * T::NM;
     ap = am + T::NM;
+    nok = (int *)(ap + T::NM);
   }
   // node slot of (line l, node s): consecutive threads get consecutive slots
   static __device__ __forceinline__ int nslot(int l, int s) {
@@ -853,6 +978,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
     sm.p[slot] = p;
     sm.c[slot] = c;
     sm.rct[slot] = rct;
+    if (a.scheme == SCHEME_PP) sm.nok[slot] = state_passes<NDIM>(eos, a.tol, w);
     const double un = v[DIR];
     sm.G[0 * T::NN + slot] = w[0] * un;
     sm.G[1 * T::NN + slot] = w[1] * un;
@@ -871,6 +997,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
 
   const double dt = geo.dt();
   const double lam = geo.lam();
+  const float l2f = (float)(2.0 * lam);  // for the flux-limiter certification
   const double eps4 = 4.0 * a.eps_is;  // IS epsilon for the indicators scaled by 4
 
   // ---- 3: midpoint fluxes ---------------------------------------------------
@@ -998,12 +1125,15 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
         W[E] = fma(V[E], mixGamma(eos, V[A]), mixPi(eos, V[A])) + 0.5 * rho * k2s;
         W[A] = V[A];
       }
-      // Interpolation limiter (Sec. 5.1): left toward W_i, right toward W_{i+1}.
+      // Interpolation limiter (Sec. 5.1): left toward W_i, right toward W_{i+1};
+      // nothing to do where the node and the interpolated state pass every
+      // threshold test (and the hard switch cannot fire after that).
       if (a.scheme == SCHEME_PP) {
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
           double *W = side ? WR : WL;
           double *V = side ? VR : VL;
+          if (a.tol.hs_implied && sm.nok[side ? ni1 : ni] && state_passes<NDIM>(eos, a.tol, W)) continue;
           const int fl = interp_limit<NDIM>(eos, a.tol, side ? Wi1 : Wi, W);
           nlim_i += cnt * (fl & 1);
           nhard_i += cnt * (fl >> 1);
@@ -1048,7 +1178,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
       for (int f = 0; f < NF; ++f) Gm[f] = Gp[f] = Gh[f];
       Gm[A] = Gh[A] - Wi[A] * uh;
       Gp[A] = Gh[A] - Wi1[A] * uh;
-      // Flux limiter (Sec. 5.2).
+      // Flux limiter (Sec. 5.2), unless certified to leave the fluxes as they are.
       if (a.scheme == SCHEME_PP) {
         double Fi[NF], Fi1[NF];
 #pragma unroll
@@ -1058,9 +1188,12 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
         }
         Fi[A] = 0.0;
         Fi1[A] = 0.0;
-        const int fl = flux_limit<NDIM>(eos, a.tol, Wi, Wi1, Fi, Fi1, GHm, GHp, lam, Gm, Gp);
-        nlim_f += cnt * (fl & 1);
-        nhard_f += cnt * (fl >> 1);
+        if (!(a.tol.hs_implied &&
+              flux_certified<NDIM>(eos, a.tol, l2f, Wi, Wi1, Fi, Fi1, GH, Gh, GHm[A], GHp[A], Gm[A], Gp[A]))) {
+          const int fl = flux_limit<NDIM>(eos, a.tol, Wi, Wi1, Fi, Fi1, GHm, GHp, lam, Gm, Gp);
+          nlim_f += cnt * (fl & 1);
+          nhard_f += cnt * (fl >> 1);
+        }
       }
     }
     const int ms = S::mslot(l, m);
@@ -1148,12 +1281,10 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
   if ((tid & 31) == 0 && midpoints_done) atomicAdd(&a.stats->midpoints, (unsigned long long)midpoints_done);
 }
 
-// Resident blocks per SM the FP64 register allocation targets.
-#ifndef FP64_MIN_BLOCKS
-#define FP64_MIN_BLOCKS 1
-#endif
+// Resident blocks per SM the FP64 register allocation targets: two of 128
+// threads (up to 255 registers each), else one.
 template <int NDIM, int DIR, class R, class T>
-__global__ void __launch_bounds__(T::THREADS, FP64_MIN_BLOCKS) sweep_kernel(const SweepArgs a) {
+__global__ void __launch_bounds__(T::THREADS, T::THREADS <= 128 ? 2 : 1) sweep_kernel(const SweepArgs a) {
   extern __shared__ double smem_raw[];
   if (!a.ctl->active) return;  // a finished advance: the step is a no-op
   sweep_body<NDIM, DIR, R, T>(a, GridGeo<NDIM, DIR, T>(a), smem_raw);
