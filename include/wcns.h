@@ -281,6 +281,33 @@ int wcns_profile_read(wcns_handle *h, wcns_profile *out);
  * Asynchronous on `stream` (a cudaStream_t, NULL = default). */
 int wcns_check_division(const double *a, const double *b, double *q, long long n, void *stream);
 
+/* Verification aid (not part of the method): the FP64 sweeps skip the
+ * limiters of Secs. 5.1-5.2 (Algorithms 1-6) where an FP32 test from
+ * truncated operands, with a rigorous error margin, certifies that every
+ * threshold test passes.  This call evaluates that certification and the
+ * FP64 limiter on the same inputs, n cases, NF = ndim + 4 conservative
+ * components (a1r1, a2r2, momentum, E, a1), tolerances eps_ar, eps_a,
+ * eps_rc (hard-switch tolerances equal to them), mixture EOS as in
+ * wcns_create:
+ *   kind 0, interpolation limiter: row i = W_node | W_interp (2 NF
+ *     doubles); exact[i] = 1 if Algorithms 1-3 and the hard switch leave
+ *     W_interp unchanged;
+ *   kind 1, flux limiter: row i = W_i | W_{i+1} | F_i | F_{i+1} |
+ *     G^{HLLC,-} | G^{HLLC,+} | G^- | G^+ | lambda (8 NF + 1 doubles; the
+ *     alpha components of F are taken as 0, the other components of
+ *     G^{HLLC,+} and G^+ from G^{HLLC,-} and G^-, as the sweeps form them);
+ *     exact[i] = 1 if Algorithms 4-6 and the hard switch leave G^-, G^+
+ *     unchanged;
+ *   cert[i] = 1 if the sweeps' certification skips that limiter.
+ * Sound means cert[i] = 1 implies exact[i] = 1.  rows, cert, exact: DEVICE
+ * arrays (n rows; n ints each).  Asynchronous on `stream` (a cudaStream_t,
+ * NULL = default).  Returns WCNS_E_INVALID_ARG for ndim outside 1..3, kind
+ * outside 0..1, n < 0, null arrays with n > 0, tolerances negative or not
+ * finite, or an EOS that wcns_create rejects. */
+int wcns_check_limiter_cert(int ndim, int kind, const double *rows, long long n, double eps_ar, double eps_a,
+                            double eps_rc, double gamma_g, double gamma_l, double pinf_l, int *cert, int *exact,
+                            void *stream);
+
 const char *wcns_strerror(int status);
 void wcns_destroy(wcns_handle *h);
 

@@ -13,8 +13,86 @@ __global__ void division_check_kernel(const double *__restrict__ a, const double
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     q[i] = div_nr(a[i], b[i]);
 }
+
+// One case per thread: the sweeps' certification decision and the FP64
+// limiter's outcome on the same inputs (row layouts as in wcns.h).
+template <int NDIM>
+__global__ void limiter_cert_check_kernel(int kind, const double *__restrict__ rows, long long n, EosConst eos,
+                                          LimTol tol, int *__restrict__ cert, int *__restrict__ exact) {
+  constexpr int NF = NDIM + 4, A = 3 + NDIM;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    auto same = [](const double *x, const double *y) {
+      bool eq = true;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) eq = eq && __double_as_longlong(x[f]) == __double_as_longlong(y[f]);
+      return eq;
+    };
+    if (kind == 0) {
+      const double *r = rows + i * (2 * NF);
+      double Wn[NF], Wt[NF], W0[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        Wn[f] = r[f];
+        Wt[f] = W0[f] = r[NF + f];
+      }
+      cert[i] = tol.hs_implied && state_passes<NDIM>(eos, tol, Wn) && state_passes<NDIM>(eos, tol, Wt);
+      const int fl = interp_limit<NDIM>(eos, tol, Wn, Wt);
+      exact[i] = fl == 0 && same(Wt, W0);
+    } else {
+      const double *r = rows + i * (8 * NF + 1);
+      double Wi[NF], Wi1[NF], Fi[NF], Fi1[NF], GHm[NF], GHp[NF], Gm[NF], Gp[NF], Gm0[NF], Gp0[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        Wi[f] = r[f];
+        Wi1[f] = r[NF + f];
+        Fi[f] = r[2 * NF + f];
+        Fi1[f] = r[3 * NF + f];
+        GHm[f] = r[4 * NF + f];
+        GHp[f] = f == A ? r[5 * NF + f] : GHm[f];
+        Gm[f] = Gm0[f] = r[6 * NF + f];
+        Gp[f] = Gp0[f] = f == A ? r[7 * NF + f] : Gm[f];
+      }
+      Fi[A] = 0.0;
+      Fi1[A] = 0.0;
+      const double lam = r[8 * NF];
+      const float l2f = (float)(2.0 * lam);
+      cert[i] = tol.hs_implied &&
+                flux_certified<NDIM>(eos, tol, l2f, Wi, Wi1, Fi, Fi1, GHm, Gm, GHm[A], GHp[A], Gm[A], Gp[A]);
+      const int fl = flux_limit<NDIM>(eos, tol, Wi, Wi1, Fi, Fi1, GHm, GHp, lam, Gm, Gp);
+      exact[i] = fl == 0 && same(Gm, Gm0) && same(Gp, Gp0);
+    }
+  }
+}
 }  // namespace
 }  // namespace wcns
+
+extern "C" int wcns_check_limiter_cert(int ndim, int kind, const double *rows, long long n, double eps_ar,
+                                       double eps_a, double eps_rc, double gamma_g, double gamma_l, double pinf_l,
+                                       int *cert, int *exact, void *stream) {
+  if (ndim < 1 || ndim > 3 || kind < 0 || kind > 1 || n < 0 || (n > 0 && (!rows || !cert || !exact)))
+    return WCNS_E_INVALID_ARG;
+  if (!(gamma_g > 1.0) || !(gamma_l > 1.0) || !(pinf_l >= 0.0) || !(gamma_g <= gamma_l) || !isfinite(gamma_g) ||
+      !isfinite(gamma_l) || !isfinite(pinf_l))
+    return WCNS_E_INVALID_ARG;
+  const double eps[3] = {eps_ar, eps_a, eps_rc};
+  for (double x : eps)
+    if (!(x >= 0.0) || !(x < 1e300)) return WCNS_E_INVALID_ARG;
+  if (n == 0) return WCNS_OK;
+  wcns::LimTol tol;
+  tol.eps_ar = tol.hs_ar = eps_ar;
+  tol.eps_a = tol.hs_a = eps_a;
+  tol.eps_rc = tol.hs_rc = eps_rc;
+  wcns::set_cert(tol);
+  const wcns::EosConst eos = wcns::make_eos(gamma_g, gamma_l, pinf_l);
+  const long long blocks = (n + 127) / 128 < 152 * 8 ? (n + 127) / 128 : 152 * 8;
+  cudaStream_t st = (cudaStream_t)stream;
+  switch (ndim) {
+    case 1: wcns::limiter_cert_check_kernel<1><<<(int)blocks, 128, 0, st>>>(kind, rows, n, eos, tol, cert, exact); break;
+    case 2: wcns::limiter_cert_check_kernel<2><<<(int)blocks, 128, 0, st>>>(kind, rows, n, eos, tol, cert, exact); break;
+    default: wcns::limiter_cert_check_kernel<3><<<(int)blocks, 128, 0, st>>>(kind, rows, n, eos, tol, cert, exact); break;
+  }
+  return cudaGetLastError() == cudaSuccess ? WCNS_OK : WCNS_E_CUDA;
+}
 
 extern "C" int wcns_check_division(const double *a, const double *b, double *q, long long n, void *stream) {
   if (n < 0 || (n > 0 && (!a || !b || !q))) return WCNS_E_INVALID_ARG;

@@ -511,7 +511,10 @@ __device__ __forceinline__ double rho_ct2(const EosConst &e, const double *W) {
 
 // "rho ctilde^2 < eps" decided without divisions: for rho > 0 and
 // Gamma + 1 > 0, multiply E - m^2/(2 rho) - Pi/(Gamma+1) < eps through by
-// rho (Gamma + 1).  Any other state uses the quotient form.
+// rho (Gamma + 1).  Any other state uses the quotient form.  Every operation
+// is explicitly rounded (no contraction left to the compiler), so all call
+// sites take the same decision for the same state, also where rounding
+// decides it.
 template <int NDIM>
 __device__ __forceinline__ bool rct2_below(const EosConst &e, const double *W, double eps) {
   constexpr int E = 2 + NDIM, A = 3 + NDIM;
@@ -521,7 +524,8 @@ __device__ __forceinline__ bool rct2_below(const EosConst &e, const double *W, d
   double m2 = 0.0;
 #pragma unroll
   for (int j = 0; j < NDIM; ++j) m2 = fma(W[2 + j], W[2 + j], m2);
-  return negative64(((W[E] - eps) * rho - 0.5 * m2) * G1 - mixPi(e, W[A]) * rho);
+  const double s = __fma_rn(__dsub_rn(W[E], eps), rho, __dmul_rn(-0.5, m2));
+  return negative64(__fma_rn(s, G1, -__dmul_rn(mixPi(e, W[A]), rho)));
 }
 
 // theta solving (1-theta) fA + theta fB = eps with the paper's three cases:

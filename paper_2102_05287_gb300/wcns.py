@@ -29,7 +29,7 @@ EXPORTS = [
     "wcns_advance_steps_host", "wcns_get_stats", "wcns_reset_stats", "wcns_nfields", "wcns_ncells",
     "wcns_launch_count", "wcns_rk3_step_noalloc", "wcns_profile_enable", "wcns_profile_read", "wcns_strerror", "wcns_destroy", "wcns_batch_create", "wcns_batch_set_options",
     "wcns_batch_advance", "wcns_batch_tuning", "wcns_batch_get_stats", "wcns_batch_total_cells", "wcns_batch_launch_count",
-    "wcns_batch_destroy", "wcns_batch_create_grids", "wcns_check_division",
+    "wcns_batch_destroy", "wcns_batch_create_grids", "wcns_check_division", "wcns_check_limiter_cert",
 ]
 
 
@@ -112,6 +112,7 @@ def load(path=LIB_PATH):
         "wcns_batch_destroy": ([vp], None),
         "wcns_batch_create_grids": ([i, i, P(i), P(d), P(d), P(wcns_bcs), d, d, d, P(vp)], i),
         "wcns_check_division": ([vp, vp, vp, ll, vp], i),
+        "wcns_check_limiter_cert": ([i, i, vp, ll, d, d, d, d, d, d, vp, vp, vp], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)

@@ -117,8 +117,9 @@ def test_grid_batch_and_division_check_host_rejections(lib):
     """wcns_batch_create_grids refuses empty or inconsistent problem tables,
     Dirichlet faces (not provided in batches), symmetry on a problem with
     fewer than 3 cells, and three dimensions (unsupported);
-    wcns_check_division refuses a negative length or missing arrays.  All
-    before any CUDA call."""
+    wcns_check_division refuses a negative length or missing arrays;
+    wcns_check_limiter_cert refuses bad dimensions, kinds, lengths, arrays,
+    tolerances and EOS parameters.  All before any CUDA call."""
     from paper_2102_05287_gb300 import wcns
     L = wcns.load()
     E = wcns.WCNS_E_INVALID_ARG
@@ -146,6 +147,19 @@ def test_grid_batch_and_division_check_host_rejections(lib):
     assert L.wcns_check_division(None, None, None, -1, None) == E
     assert L.wcns_check_division(None, None, None, 4, None) == E
     assert L.wcns_check_division(None, None, None, 0, None) == wcns.WCNS_OK
+    # wcns_check_limiter_cert: dimension, kind, length, arrays, tolerances, EOS
+    cert = (ctypes.c_int * 1)()
+    ok = (1e-10, 1e-10, 1e-8, 1.4, 4.4, 6e8)
+    assert L.wcns_check_limiter_cert(0, 0, None, 0, *ok, None, None, None) == E
+    assert L.wcns_check_limiter_cert(4, 0, None, 0, *ok, None, None, None) == E
+    assert L.wcns_check_limiter_cert(2, 2, None, 0, *ok, None, None, None) == E
+    assert L.wcns_check_limiter_cert(2, 0, None, -1, *ok, None, None, None) == E
+    assert L.wcns_check_limiter_cert(2, 1, None, 3, *ok, cert, cert, None) == E
+    assert L.wcns_check_limiter_cert(2, 0, None, 0, -1e-10, *ok[1:], None, None, None) == E
+    assert L.wcns_check_limiter_cert(2, 0, None, 0, 1e-10, 1e-10, float("nan"), *ok[3:], None, None, None) == E
+    assert L.wcns_check_limiter_cert(2, 0, None, 0, *ok[:3], 5.0, 4.4, 6e8, None, None, None) == E
+    assert L.wcns_check_limiter_cert(2, 0, None, 0, *ok[:3], 1.4, 4.4, -1.0, None, None, None) == E
+    assert L.wcns_check_limiter_cert(2, 1, None, 0, *ok, None, None, None) == wcns.WCNS_OK
 
 
 def test_plain_c_program_uses_the_boundary(lib, tmp_path):

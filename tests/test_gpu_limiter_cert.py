@@ -1,0 +1,239 @@
+"""The FP64 sweeps' FP32 certification of the limiter threshold tests.
+
+The FP64 sweeps skip the interpolation limiter (Sec. 5.1, Algorithms 1-3)
+and the flux limiter (Sec. 5.2, Algorithms 4-6) at a midpoint when an FP32
+test, formed from operands truncated to 20 mantissa bits with a rigorous
+error margin, shows that every threshold test passes.  That is only correct
+if the FP64 limiter would leave the states and fluxes unchanged too.  Through
+the C ABI (wcns_check_limiter_cert) both run on the same inputs on the
+device:
+
+* soundness: every certified case is one the FP64 limiter leaves unchanged;
+  the cases crowd every threshold (alpha1 rho1, alpha2 rho2, alpha1,
+  1 - alpha1, rho ctilde^2) from both sides, at relative distances from a
+  few ulps to 1e3, with zero, subnormal, huge and non-finite components;
+* liveness: clearly admissible states and half states are certified, so
+  the fast path is the one the sweeps take away from the limiters' work.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2102_05287_gb300 import problems as P  # noqa: E402
+from paper_2102_05287_gb300 import wcns  # noqa: E402
+
+EPS = dict(eps_ar=1e-10, eps_a=1e-10, eps_rc=1e-8)
+EOS = P.WORKLOAD_EOS
+DELTAS = np.array([-1.0, -1e-3, -1e-6, -1e-9, -1e-12, -1e-15, 0.0, 1e-15, 1e-12, 1e-9, 1e-7, 4e-6, 1e-5,
+                   1e-4, 1e-2, 1.0, 1e3])
+
+
+def check(ndim, kind, rows):
+    rows = np.ascontiguousarray(rows, dtype=np.float64)
+    n = rows.shape[0]
+    t = torch.from_numpy(rows).cuda()
+    cert = torch.zeros(n, dtype=torch.int32, device="cuda")
+    exact = torch.zeros(n, dtype=torch.int32, device="cuda")
+    st = wcns.load().wcns_check_limiter_cert(ndim, kind, C.c_void_p(t.data_ptr()), n, EPS["eps_ar"], EPS["eps_a"],
+                                             EPS["eps_rc"], EOS["gamma_g"], EOS["gamma_l"], EOS["pinf_l"],
+                                             C.c_void_p(cert.data_ptr()), C.c_void_p(exact.data_ptr()), None)
+    assert st == wcns.WCNS_OK
+    torch.cuda.synchronize()
+    return cert.cpu().numpy().astype(bool), exact.cpu().numpy().astype(bool)
+
+
+def eos_terms(W, ndim):
+    """Kinetic energy and pbar = Pi / (Gamma + 1) of conservative states
+    (Sec. 2); used only to place test states at a chosen rho ctilde^2."""
+    g1, p1, g2 = EOS["gamma_l"], EOS["pinf_l"], EOS["gamma_g"]
+    r1, r2 = 1.0 / (g1 - 1.0), 1.0 / (g2 - 1.0)
+    q1 = g1 * p1 / (g1 - 1.0)
+    rho = W[0] + W[1]
+    ke = 0.5 * sum(W[2 + j] ** 2 for j in range(ndim)) / rho
+    a = W[3 + ndim]
+    return ke, q1 * a / (r2 + (r1 - r2) * a + 1.0)
+
+
+def random_primitives(rng, n, ndim, extreme=False, pmin=1.0):
+    """Primitive states over the workloads' range: water and air, pmin to
+    1 GPa, speeds up to 1 km/s (up to 30 km/s with extreme)."""
+    a1 = np.where(rng.random(n) < 0.5, rng.uniform(1e-6, 1e-3, n), 1.0 - rng.uniform(1e-6, 1e-3, n))
+    a1 = np.where(rng.random(n) < 0.3, rng.uniform(0.0, 1.0, n), a1)
+    p = 10.0 ** rng.uniform(np.log10(pmin), 9.0, n)
+    vmax = 3e4 if extreme else 1e3
+    vel = [rng.uniform(-vmax, vmax, n) * (rng.random(n) < 0.8) for _ in range(ndim)]
+    return [a1 * 1000.0 * rng.uniform(0.5, 1.5, n), (1 - a1) * rng.uniform(0.5, 2.0, n), vel, p, a1]
+
+
+def random_states(rng, n, ndim, extreme=False, pmin=1.0):
+    """Admissible conservative states (columns)."""
+    return P.conservative(EOS, *random_primitives(rng, n, ndim, extreme, pmin))
+
+
+def nearby_states(rng, prim):
+    """Admissible states within 10 % of given primitives (alpha1 within 10 %
+    of its distance to 0 and 1), as a half step of smooth flow leaves them."""
+    a1r1, a2r2, vel, p, a1 = prim
+    n = p.size
+
+    def f():
+        return rng.uniform(0.9, 1.1, n)
+
+    vs = [v * f() + rng.uniform(-10.0, 10.0, n) for v in vel]
+    a1n = a1 + rng.uniform(-0.1, 0.1, n) * np.minimum(a1, 1.0 - a1)
+    return P.conservative(EOS, a1r1 * f(), a2r2 * f(), vs, p * f(), a1n)
+
+
+def place(W, ndim, which, delta):
+    """Move quantity `which` of states W (columns) to its tolerance times
+    (1 + delta): 0 alpha1 rho1, 1 alpha2 rho2, 2 alpha1, 3 1 - alpha1,
+    4 rho ctilde^2 (through E)."""
+    W = W.copy()
+    A, E = 3 + ndim, 2 + ndim
+    if which == 0:
+        W[0] = EPS["eps_ar"] * (1 + delta)
+    elif which == 1:
+        W[1] = EPS["eps_ar"] * (1 + delta)
+    elif which == 2:
+        W[A] = EPS["eps_a"] * (1 + delta)
+    elif which == 3:
+        W[A] = 1.0 - EPS["eps_a"] * (1 + delta)
+    else:
+        ke, pb = eos_terms(W, ndim)
+        W[E] = ke + pb + EPS["eps_rc"] * (1 + delta)
+    return W
+
+
+def special(rng, W, ndim):
+    """Put zeros, subnormals, huge values and non-finite values into random
+    components of some states."""
+    W = W.copy()
+    nf, n = W.shape
+    vals = np.array([0.0, -0.0, 5e-324, -2e-310, 1e-40, 3e38, 1e39, 1e200, np.inf, -np.inf, np.nan])
+    k = rng.integers(0, n, n // 4)
+    W[rng.integers(0, nf, k.size), k] = vals[rng.integers(0, vals.size, k.size)]
+    return W
+
+
+@pytest.mark.parametrize("ndim", [1, 2, 3])
+def test_interp_certification_is_sound_and_live(ndim):
+    rng = np.random.default_rng(100 + ndim)
+    nf = ndim + 4
+    n = 4000
+    node = random_states(rng, n, ndim, pmin=1e3)
+    interp = random_states(rng, n, ndim, pmin=1e3)
+    # liveness on clearly admissible pairs
+    cert, exact = check(ndim, 0, np.concatenate([node, interp]).T)
+    assert np.all(exact[cert]), "certified a pair the FP64 limiter changes"
+    assert cert.mean() > 0.99, cert.mean()
+    # soundness next to every threshold, for the interpolated and the node state
+    rows = []
+    for which in range(5):
+        for d in DELTAS:
+            m = 300
+            a, b = random_states(rng, m, ndim, extreme=True), random_states(rng, m, ndim, extreme=True)
+            rows.append(np.concatenate([a, place(b, ndim, which, d)]).T)
+            rows.append(np.concatenate([place(a, ndim, which, d), b]).T)
+    rows.append(np.concatenate([special(rng, random_states(rng, n, ndim), ndim),
+                                special(rng, random_states(rng, n, ndim), ndim)]).T)
+    rows = np.concatenate(rows)
+    assert rows.shape[1] == 2 * nf
+    cert, exact = check(ndim, 0, rows)
+    bad = np.flatnonzero(cert & ~exact)
+    assert bad.size == 0, rows[bad[:3]]
+    assert (~exact).sum() > 1000  # the placed states do straddle the thresholds
+    assert cert.sum() > 1000
+
+
+def flux_rows(rng, n, ndim, extreme=False, pmin=1.0):
+    """Midpoint inputs of the flux limiter whose four half states are
+    chosen admissible states near their nodes: W_i - 2 lam (G^- - F_i) = X_i
+    and W_{i+1} + 2 lam (G^- - F_{i+1}) = X_{i+1} fix the node fluxes F for
+    a random high-order flux G^-, and the first-order flux is G^- to within
+    1e-7 (as in smooth flow), so its half states are X to within that."""
+    nf, A = ndim + 4, 3 + ndim
+    pi, pi1 = random_primitives(rng, n, ndim, extreme, pmin), random_primitives(rng, n, ndim, extreme, pmin)
+    Wi, Wi1 = P.conservative(EOS, *pi), P.conservative(EOS, *pi1)
+    Xi, Xi1 = nearby_states(rng, pi), nearby_states(rng, pi1)
+    lam = 10.0 ** rng.uniform(-6.0, -2.0, n)
+    l2 = 2 * lam
+    Gm = rng.uniform(-0.5, 0.5, (nf, n)) * np.maximum(np.abs(Wi), np.abs(Wi1)) / l2
+    Fi = Gm + (Xi - Wi) / l2
+    Fi1 = Gm - (Xi1 - Wi1) / l2
+    Gm[A] = (Wi[A] - Xi[A]) / l2
+    Gp = Gm.copy()
+    Gp[A] = (Xi1[A] - Wi1[A]) / l2
+    GHm = Gm * (1 + rng.uniform(-1e-7, 1e-7, (nf, n)))
+    GHp = GHm.copy()
+    GHp[A] = Gp[A] * (1 + rng.uniform(-1e-7, 1e-7, n))
+    return [Wi, Wi1, Fi, Fi1, GHm, GHp, Gm, Gp], lam
+
+
+def pack(parts, lam):
+    return np.concatenate(parts + [lam[None, :]]).T
+
+
+def place_half(parts, lam, ndim, st, which, delta):
+    """Set half state st (0 W_i - 2 lam (G^{HLLC,-} - F_i), 1 W_{i+1} +
+    2 lam (G^{HLLC,+} - F_{i+1}), 2 and 3 the same with G^-, G^+) so that
+    its quantity `which` sits at its tolerance times (1 + delta), through
+    the flux (shared components of G^{HLLC} / G^- move both half states of
+    that flux; the alpha flux is per side)."""
+    Wi, Wi1, Fi, Fi1, GHm, GHp, Gm, Gp = [x.copy() for x in parts]
+    A, E = 3 + ndim, 2 + ndim
+    right = st & 1
+    W, F = (Wi1, Fi1) if right else (Wi, Fi)
+    G = (GHp if right else GHm) if st < 2 else (Gp if right else Gm)
+    Gshared = GHm if st < 2 else Gm
+    s = 1.0 if right else -1.0
+    l2 = 2 * lam
+    Fa = np.zeros_like(W[0])
+
+    def half(f):
+        g = G[f] if f == A else Gshared[f]
+        return W[f] + s * l2 * (g - (Fa if f == A else F[f]))
+
+    X = np.stack([half(f) for f in range(ndim + 4)])
+    target = place(X, ndim, which, delta)
+    f = {0: 0, 1: 1, 2: A, 3: A, 4: E}[which]
+    if f == A:
+        G[A] = (target[A] - W[A]) / (s * l2)
+    else:
+        Gshared[f] = F[f] + (target[f] - W[f]) / (s * l2)
+    if st < 2:
+        GHp[:A] = GHm[:A]
+    else:
+        Gp[:A] = Gm[:A]
+    return [Wi, Wi1, Fi, Fi1, GHm, GHp, Gm, Gp]
+
+
+@pytest.mark.parametrize("ndim", [1, 2, 3])
+def test_flux_certification_is_sound_and_live(ndim):
+    rng = np.random.default_rng(200 + ndim)
+    nf = ndim + 4
+    parts, lam = flux_rows(rng, 4000, ndim, pmin=1e3)
+    cert, exact = check(ndim, 1, pack(parts, lam))
+    assert np.all(exact[cert]), "certified a midpoint the FP64 limiter changes"
+    assert cert.mean() > 0.99, cert.mean()
+    rows = []
+    for st in range(4):
+        for which in range(5):
+            for d in DELTAS:
+                parts, lam = flux_rows(rng, 120, ndim, extreme=True)
+                rows.append(pack(place_half(parts, lam, ndim, st, which, d), lam))
+    parts, lam = flux_rows(rng, 4000, ndim)
+    rows.append(pack([special(rng, x, ndim) for x in parts], lam))
+    rows = np.concatenate(rows)
+    assert rows.shape[1] == 8 * nf + 1
+    cert, exact = check(ndim, 1, rows)
+    bad = np.flatnonzero(cert & ~exact)
+    assert bad.size == 0, rows[bad[:2]]
+    assert (~exact).sum() > 1000
+    assert cert.sum() > 1000
