@@ -916,26 +916,37 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
 #pragma unroll
         for (int f = 0; f < NF; ++f) a.L[(long long)f * N + idx] = a.l_raw ? diff[f] : diff[f] * idx_;
       } else {
+        // every load of the cell before its stores: the compiler cannot tell
+        // the components apart, and would order each load after the last store
+        double l0[NF];
 #pragma unroll
-        for (int f = 0; f < NF; ++f)
-          a.L[(long long)f * N + idx] = fma(diff[f], geo.accum_scale(), a.L[(long long)f * N + idx]);
+        for (int f = 0; f < NF; ++f) l0[f] = a.L[(long long)f * N + idx];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) a.L[(long long)f * N + idx] = fma(diff[f], geo.accum_scale(), l0[f]);
       }
     } else {
       const int ns = nslot(l, m + 3);
-      double w[NF];
+      double w[NF], wn[NF], lv[NF];
       bool finite = true;
+      // loads first, as above (W_out may be any other array)
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        wn[f] = has_a ? a.Wn[(long long)f * N + idx] : 0.0;
+        lv[f] = a.read_L ? a.L[(long long)f * N + idx] : 0.0;
+      }
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         // a W^n + b W + b dt (L + flux difference / dx) (Sec. 5.3 combine)
         const double diff = f < NF - 1 ? sm.F[f * T::NM + ml] - sm.F[f * T::NM + mr] : sm.ap[ml] - sm.am[mr];
         const double wi = sm.W[f * T::NN + ns];
         double acc = b_one ? wi : a.rk_b * wi;
-        if (has_a) acc = fma(a.rk_a, a.Wn[(long long)f * N + idx], acc);
-        if (a.read_L) acc = fma(bdt, a.L[(long long)f * N + idx], acc);
+        if (has_a) acc = fma(a.rk_a, wn[f], acc);
+        if (a.read_L) acc = fma(bdt, lv[f], acc);
         w[f] = fma(bdt_idx, diff, acc);
         finite = finite && finite64(w[f]);
-        a.W_out[(long long)f * N + idx] = w[f];
       }
+#pragma unroll
+      for (int f = 0; f < NF; ++f) a.W_out[(long long)f * N + idx] = w[f];
       if (!finite) atomicAdd(&a.stats->nonfinite, 1ull);
       // max(|u_d| + c) of the new state for the next stage (FP32 suffices
       // for the directional split, Sec. 3.3)

@@ -1213,9 +1213,11 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
   __syncthreads();
 
   // ---- 4: cell update ------------------------------------------------------
-  double smax_local[NDIM];
+  // Wave-speed maxima as bit patterns: |u_d| + c >= 0 (or NaN), and
+  // non-negative doubles order like their bits, a NaN above every number.
+  unsigned long long smax_local[NDIM];
 #pragma unroll
-  for (int j = 0; j < NDIM; ++j) smax_local[j] = 0.0;
+  for (int j = 0; j < NDIM; ++j) smax_local[j] = 0ull;
   int midpoints_done = 0;
   const double idx_ = geo.inv_dx();
   const bool has_a = (__double_as_longlong(a.rk_a) << 1) != 0;  // a != 0, an integer test
@@ -1236,20 +1238,31 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
 #pragma unroll
       for (int f = 0; f < NF; ++f) a.L[(long long)f * N + idx] = upd[f];
     } else if (a.epilogue == EPI_ACCUM) {
+      // every load of the cell before its stores: the compiler cannot tell
+      // the components apart, and would order each load after the last store
+      double l0[NF];
 #pragma unroll
-      for (int f = 0; f < NF; ++f) a.L[(long long)f * N + idx] += upd[f];
+      for (int f = 0; f < NF; ++f) l0[f] = a.L[(long long)f * N + idx];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) a.L[(long long)f * N + idx] = l0[f] + upd[f];
     } else {
       const int ns = S::nslot(l, m + 3);
-      double w[NF];
+      double w[NF], lv[NF], wn[NF];
       bool finite = true;
+      // loads first, as above (W_out may be any other array)
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
-        const double tot = a.read_L ? a.L[(long long)f * N + idx] + upd[f] : upd[f];
-        const double wn = has_a ? a.Wn[(long long)f * N + idx] : 0.0;
-        w[f] = a.rk_a * wn + a.rk_b * (sm.W[f * T::NN + ns] + dt * tot);
-        finite = finite && finite64(w[f]);
-        a.W_out[(long long)f * N + idx] = w[f];
+        lv[f] = a.read_L ? a.L[(long long)f * N + idx] : 0.0;
+        wn[f] = has_a ? a.Wn[(long long)f * N + idx] : 0.0;
       }
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const double tot = a.read_L ? lv[f] + upd[f] : upd[f];
+        w[f] = a.rk_a * wn[f] + a.rk_b * (sm.W[f * T::NN + ns] + dt * tot);
+        finite = finite && finite64(w[f]);
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f) a.W_out[(long long)f * N + idx] = w[f];
       if (!finite) atomicAdd(&a.stats->nonfinite, 1ull);
       // max(|u_d| + c) of the new state (Sec. 3.3) for the next stage:
       // c^2 = ((Gamma+1) rho e - Pi)/(Gamma^2 rho)
@@ -1263,15 +1276,15 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
       const double c = sqrt(div_nr((Gam + 1.0) * rhoe - mixPi(eos, w[A]), Gam * Gam * rho));
 #pragma unroll
       for (int j = 0; j < NDIM; ++j) {
-        const double sj = fabs(w[2 + j] * ir) + c;
-        smax_local[j] = (sj > smax_local[j] || sj != sj) ? sj : smax_local[j];
+        const unsigned long long sj = (unsigned long long)__double_as_longlong(fabs(w[2 + j] * ir) + c);
+        smax_local[j] = sj > smax_local[j] ? sj : smax_local[j];
       }
     }
   }
   if (a.epilogue == EPI_COMBINE) {
 #pragma unroll
     for (int j = 0; j < NDIM; ++j) {
-      unsigned long long b = __double_as_longlong(smax_local[j]);
+      unsigned long long b = smax_local[j];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long ob = __shfl_xor_sync(0xffffffffu, b, o);
