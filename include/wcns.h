@@ -117,9 +117,9 @@ typedef struct {
   long long nonfinite;       /* cells whose update was not finite */
   long long inadmissible;    /* input cells outside G (Sec. 2) */
   long long midpoints;       /* midpoint fluxes evaluated */
-  long long fp64_fallbacks;  /* mixed precision only: interpolated states and
-                                midpoints whose limiter could not be certified
-                                in FP32 and ran in FP64 */
+  long long fp64_fallbacks;  /* interpolated states and midpoints whose
+                                limiter could not be certified in FP32 and
+                                ran in FP64 (both precisions certify) */
 } wcns_stats;
 
 /* Create a solver for one grid, boundary set and fluid pair.
@@ -292,17 +292,26 @@ int wcns_check_division(const double *a, const double *b, double *q, long long n
  *   kind 0, interpolation limiter: row i = W_node | W_interp (2 NF
  *     doubles); exact[i] = 1 if Algorithms 1-3 and the hard switch leave
  *     W_interp unchanged;
- *   kind 1, flux limiter: row i = W_i | W_{i+1} | F_i | F_{i+1} |
- *     G^{HLLC,-} | G^{HLLC,+} | G^- | G^+ | lambda (8 NF + 1 doubles; the
- *     alpha components of F are taken as 0, the other components of
- *     G^{HLLC,+} and G^+ from G^{HLLC,-} and G^-, as the sweeps form them);
- *     exact[i] = 1 if Algorithms 4-6 and the hard switch leave G^-, G^+
- *     unchanged;
+ *   kind 1, flux limiter with a given first-order flux: row i = W_i |
+ *     W_{i+1} | F_i | F_{i+1} | G^{HLLC,-} | G^{HLLC,+} | G^- | G^+ |
+ *     lambda (8 NF + 1 doubles; the alpha components of F are taken as 0,
+ *     the other components of G^{HLLC,+} and G^+ from G^{HLLC,-} and G^-,
+ *     as the sweeps form them; the certification takes G^HLLC to within
+ *     its FP32 truncation); exact[i] = 1 if Algorithms 4-6 and the hard
+ *     switch leave G^-, G^+ unchanged;
+ *   kind 2, flux limiter from node states, as the sweeps run it: row i =
+ *     node i | node i+1 | F_i | F_{i+1} | G | G^-_alpha | G^+_alpha |
+ *     lambda, a node being W (NF), velocity (ndim), p, c (2 (NF + ndim
+ *     + 2) + 3 NF + 3 doubles; G: the shared components of G^- and G^+,
+ *     its alpha component unused; the flux direction is the last axis).
+ *     The sweeps' certification evaluates the first-order HLLC flux (Sec.
+ *     3.2) in FP32 with error bounds; exact[i] = 1 if the FP64 flux and
+ *     Algorithms 4-6 with the hard switch leave G^-, G^+ unchanged;
  *   cert[i] = 1 if the sweeps' certification skips that limiter.
  * Sound means cert[i] = 1 implies exact[i] = 1.  rows, cert, exact: DEVICE
  * arrays (n rows; n ints each).  Asynchronous on `stream` (a cudaStream_t,
  * NULL = default).  Returns WCNS_E_INVALID_ARG for ndim outside 1..3, kind
- * outside 0..1, n < 0, null arrays with n > 0, tolerances negative or not
+ * outside 0..2, n < 0, null arrays with n > 0, tolerances negative or not
  * finite, or an EOS that wcns_create rejects. */
 int wcns_check_limiter_cert(int ndim, int kind, const double *rows, long long n, double eps_ar, double eps_a,
                             double eps_rc, double gamma_g, double gamma_l, double pinf_l, int *cert, int *exact,

@@ -38,7 +38,7 @@ __global__ void limiter_cert_check_kernel(int kind, const double *__restrict__ r
       cert[i] = tol.hs_implied && state_passes<NDIM>(eos, tol, Wn) && state_passes<NDIM>(eos, tol, Wt);
       const int fl = interp_limit<NDIM>(eos, tol, Wn, Wt);
       exact[i] = fl == 0 && same(Wt, W0);
-    } else {
+    } else if (kind == 1) {
       const double *r = rows + i * (8 * NF + 1);
       double Wi[NF], Wi1[NF], Fi[NF], Fi1[NF], GHm[NF], GHp[NF], Gm[NF], Gp[NF], Gm0[NF], Gp0[NF];
 #pragma unroll
@@ -56,8 +56,54 @@ __global__ void limiter_cert_check_kernel(int kind, const double *__restrict__ r
       Fi1[A] = 0.0;
       const double lam = r[8 * NF];
       const float l2f = (float)(2.0 * lam);
+      // the given first-order flux, known to within its truncation
+      float gH[NF + 1], eH[NF + 1];
+#pragma unroll
+      for (int f = 0; f <= NF; ++f) {
+        gH[f] = trunc32(f < A ? GHm[f] : f == A ? GHm[A] : GHp[A]);
+        eH[f] = 1.9073486328125e-06f * fabsf(gH[f]);
+      }
+      cert[i] = tol.hs_implied && flux_certified<NDIM>(eos, tol, l2f, Wi, Wi1, Fi, Fi1, gH, eH, Gm, Gm[A], Gp[A]);
+      const int fl = flux_limit<NDIM>(eos, tol, Wi, Wi1, Fi, Fi1, GHm, GHp, lam, Gm, Gp);
+      exact[i] = fl == 0 && same(Gm, Gm0) && same(Gp, Gp0);
+    } else {
+      // nodes i, i+1 (W, velocity, p, c), node fluxes, high-order flux, lambda
+      constexpr int NODE = NF + NDIM + 2;
+      const double *r = rows + i * (2 * NODE + 3 * NF + 3);
+      double Wi[NF], Wi1[NF], vi[NDIM], vr[NDIM], Fi[NF], Fi1[NF], Gm[NF], Gp[NF], Gm0[NF], Gp0[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        Wi[f] = r[f];
+        Wi1[f] = r[NODE + f];
+        Fi[f] = r[2 * NODE + f];
+        Fi1[f] = r[2 * NODE + NF + f];
+        Gm[f] = Gp[f] = Gm0[f] = Gp0[f] = r[2 * NODE + 2 * NF + f];
+      }
+#pragma unroll
+      for (int j = 0; j < NDIM; ++j) {
+        vi[j] = r[NF + j];
+        vr[j] = r[NODE + NF + j];
+      }
+      const double pi = r[NF + NDIM], ci = r[NF + NDIM + 1];
+      const double pr = r[NODE + NF + NDIM], cr = r[NODE + NF + NDIM + 1];
+      Gm[A] = Gm0[A] = r[2 * NODE + 3 * NF];
+      Gp[A] = Gp0[A] = r[2 * NODE + 3 * NF + 1];
+      const double lam = r[2 * NODE + 3 * NF + 2];
+      Fi[A] = 0.0;
+      Fi1[A] = 0.0;
+      const float l2f = (float)(2.0 * lam);
+      // the sweeps' two routes: the bounded FP32 first-order flux with the
+      // certification, and the FP64 flux with the FP64 limiter
+      float gH[NF + 1], eH[NF + 1];
       cert[i] = tol.hs_implied &&
-                flux_certified<NDIM>(eos, tol, l2f, Wi, Wi1, Fi, Fi1, GHm, Gm, GHm[A], GHp[A], Gm[A], Gp[A]);
+                hllc1_bound32<NDIM, NDIM - 1>(Wi, vi, pi, ci, Wi1, vr, pr, cr, gH, eH) &&
+                flux_certified<NDIM>(eos, tol, l2f, Wi, Wi1, Fi, Fi1, gH, eH, Gm, Gm[A], Gp[A]);
+      double GH[NF], uH, GHm[NF], GHp[NF];
+      hllc<NDIM, NDIM - 1, double>(Wi, vi, pi, Wi[0] + Wi[1], ci, Wi1, vr, pr, Wi1[0] + Wi1[1], cr, GH, uH);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) GHm[f] = GHp[f] = GH[f];
+      GHm[A] = GH[A] - Wi[A] * uH;
+      GHp[A] = GH[A] - Wi1[A] * uH;
       const int fl = flux_limit<NDIM>(eos, tol, Wi, Wi1, Fi, Fi1, GHm, GHp, lam, Gm, Gp);
       exact[i] = fl == 0 && same(Gm, Gm0) && same(Gp, Gp0);
     }
@@ -69,7 +115,7 @@ __global__ void limiter_cert_check_kernel(int kind, const double *__restrict__ r
 extern "C" int wcns_check_limiter_cert(int ndim, int kind, const double *rows, long long n, double eps_ar,
                                        double eps_a, double eps_rc, double gamma_g, double gamma_l, double pinf_l,
                                        int *cert, int *exact, void *stream) {
-  if (ndim < 1 || ndim > 3 || kind < 0 || kind > 1 || n < 0 || (n > 0 && (!rows || !cert || !exact)))
+  if (ndim < 1 || ndim > 3 || kind < 0 || kind > 2 || n < 0 || (n > 0 && (!rows || !cert || !exact)))
     return WCNS_E_INVALID_ARG;
   if (!(gamma_g > 1.0) || !(gamma_l > 1.0) || !(pinf_l >= 0.0) || !(gamma_g <= gamma_l) || !isfinite(gamma_g) ||
       !isfinite(gamma_l) || !isfinite(pinf_l))

@@ -749,38 +749,176 @@ __device__ __forceinline__ bool state_passes(const EosConst &e, const LimTol &t,
   return rct2_cert<NDIM>(e, x, d, t.cert_rc) || !rct2_below<NDIM>(e, W, t.eps_rc);
 }
 
+// An FP32 value with a bound on its distance to the exact value it stands
+// for (running error analysis).  An operation's bound is the propagated
+// bounds of its operands plus 2^-22 of the result for its own rounding (at
+// least twice an FP32 rounding); a division needs its denominator bounded
+// away from zero.  The bounds are computed in FP32 themselves; the slack
+// of every term (2x or more) covers their own rounding.
+struct EF {
+  float v, e;
+};
+constexpr float EF_U = 2.384185791015625e-07f;  // 2^-22
+// from an FP64 value: the truncated image, within 2^-20 |x| <= 2^-19 |v|
+__device__ __forceinline__ EF ef(double x) {
+  const float v = trunc32(x);
+  return {v, 1.9073486328125e-06f * fabsf(v)};
+}
+__device__ __forceinline__ EF operator+(EF a, EF b) {
+  const float v = a.v + b.v;
+  return {v, a.e + b.e + EF_U * fabsf(v)};
+}
+__device__ __forceinline__ EF operator-(EF a, EF b) {
+  const float v = a.v - b.v;
+  return {v, a.e + b.e + EF_U * fabsf(v)};
+}
+__device__ __forceinline__ EF operator*(EF a, EF b) {
+  const float v = a.v * b.v;
+  return {v, fabsf(a.v) * b.e + fabsf(b.v) * a.e + a.e * b.e + EF_U * fabsf(v)};
+}
+// exact constants: 0.5 and 1 times a value
+__device__ __forceinline__ EF half(EF a) { return {0.5f * a.v, 0.5f * a.e}; }
+__device__ __forceinline__ EF efmin(EF a, EF b) { return {fminf(a.v, b.v), fmaxf(a.e, b.e)}; }
+__device__ __forceinline__ EF efmax(EF a, EF b) { return {fmaxf(a.v, b.v), fmaxf(a.e, b.e)}; }
+// a / b = q: |A/B - q| <= (ea + |q| eb) / (|b| - eb) plus the rounding of
+// the approximate division (2 ulp); ok cleared unless |b| - eb > 0 and b is
+// inside the approximate division's range
+__device__ __forceinline__ EF operator/(EF a, EF b) {
+  const float den = fabsf(b.v) - b.e;
+  const bool good = den > 0.0f && fabsf(b.v) < 1e30f;
+  const float q = __fdividef(a.v, b.v);
+  return {q, good ? __fdividef(a.e + fabsf(q) * b.e, den) + 2.0f * EF_U * fabsf(q) : __int_as_float(0x7FC00000)};
+}
+
+// First-order HLLC flux G^HLLC(W_i, W_{i+1}) (Sec. 3.2, the formulas of
+// hllc above) in FP32 with error bounds, from the FP64 node states W, their
+// velocities, pressures and sound speeds.  gH / eH: the shared components
+// (f < A), then the alpha components of G^{HLLC,-} and G^{HLLC,+} at A and
+// A + 1.  The bounds cover whatever the FP64 flux computes:
+// - where |s*| exceeds its bound, the FP64 flux takes the same star state;
+// - otherwise it takes either star state or their mean (at s* = 0), and
+//   the mean of both FP32 side fluxes with half their difference added to
+//   the bound covers all three;
+// - the alpha components (alpha_K - alpha_i) s*, (alpha_K - alpha_{i+1}) s*
+//   take the alpha differences from FP64, so that their bounds scale with
+//   the jump in alpha, plus an allowance for the FP64 path's own rounding
+//   of alpha_K s* - alpha_i s*.
+// Returns false where a denominator is not bounded away from zero or a
+// bound is not finite.
+template <int NDIM, int DIR>
+__device__ __forceinline__ bool hllc1_bound32(const double *WL, const double *vL, double pL, double cL,
+                                              const double *WR, const double *vR, double pR, double cR, float *gH,
+                                              float *eH) {
+  constexpr int NF = NDIM + 4, E = 2 + NDIM, A = 3 + NDIM;
+  const EF uL = ef(vL[DIR]), uR = ef(vR[DIR]), cl = ef(cL), cr = ef(cR);
+  const EF rL = ef(WL[0]) + ef(WL[1]), rR = ef(WR[0]) + ef(WR[1]);
+  const EF pl = ef(pL), pr = ef(pR);
+  const EF ubar = half(uL + uR), cbar = half(cl + cr);
+  const EF sL = efmin(ubar - cbar, uL - cl);
+  const EF sR = efmax(ubar + cbar, uR + cr);
+  const EF mL = rL * (sL - uL), mR = rR * (sR - uR);
+  const EF ss = (pr - pl + mL * uL - mR * uR) / (mL - mR);
+  if (!(ss.e < 1e30f)) return false;  // also a NaN
+  // one side's flux F_K + s_(-/+) (W*_K - W_K), shared components
+  auto side_flux = [&](bool right, EF *G) {
+    const double *W = right ? WR : WL;
+    const double *v = right ? vR : vL;
+    const EF u = right ? uR : uL, sK = right ? sR : sL, p = right ? pr : pl, rho = right ? rR : rL;
+    const EF sw = right ? EF{fmaxf(0.0f, sR.v), sR.e} : EF{fminf(0.0f, sL.v), sL.e};
+    const EF chim1 = (ss - u) / (sK - ss);
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+      const EF w = ef(W[f]);
+      G[f] = w * u + sw * (chim1 * w);
+    }
+#pragma unroll
+    for (int j = 0; j < NDIM; ++j) {
+      const EF m = ef(W[2 + j]);
+      const EF dm = (j == DIR) ? (rho * sK) * chim1 : chim1 * (rho * ef(v[j]));
+      G[2 + j] = (j == DIR) ? m * u + p + sw * dm : m * u + sw * dm;
+    }
+    const EF Ep = ef(W[E]) + p;
+    const EF dE = chim1 * Ep + ((EF{1.0f, 0.0f} + chim1) * rho) * (ss * (ss - u));
+    G[E] = Ep * u + sw * dE;
+  };
+  // alpha jump between the nodes, from FP64; the FP64 path rounds
+  // alpha_K s* and alpha_K s* - alpha_i s*: 2^-51 (|alpha_K| + |alpha_i|) |s*|
+  const EF da = ef(WR[A] - WL[A]);
+  const float aflux = 4.440892098500626e-16f * (fabsf(trunc32(WL[A])) + fabsf(trunc32(WR[A])) + 1.0f) *
+                      (fabsf(ss.v) + ss.e);
+  EF G[NF - 1];
+  EF Gm, Gp;  // (alpha_K - alpha_i) s*, (alpha_K - alpha_{i+1}) s*
+  if (fabsf(ss.v) > ss.e) {
+    const bool right = ss.v < 0.0f;
+    side_flux(right, G);
+    Gm = right ? da * ss : EF{0.0f, 0.0f};
+    Gp = right ? EF{0.0f, 0.0f} : EF{0.0f, 0.0f} - da * ss;
+  } else {
+    EF GL[NF - 1], GR[NF - 1];
+    side_flux(false, GL);
+    side_flux(true, GR);
+#pragma unroll
+    for (int f = 0; f < NF - 1; ++f) {
+      const float v = 0.5f * (GL[f].v + GR[f].v);
+      G[f] = {v, 0.5f * fabsf(GL[f].v - GR[f].v) + GL[f].e + GR[f].e + EF_U * fabsf(v)};
+    }
+    const EF t = da * ss;  // Gm is 0 or t or t/2, Gp is -t or 0 or -t/2
+    Gm = {0.5f * t.v, 0.5f * fabsf(t.v) + t.e};
+    Gp = {-0.5f * t.v, 0.5f * fabsf(t.v) + t.e};
+  }
+  bool ok = true;
+#pragma unroll
+  for (int f = 0; f < A; ++f) {
+    gH[f] = G[f].v;
+    eH[f] = G[f].e;
+    ok = ok && eH[f] < 1e30f;  // false for a NaN bound too
+  }
+  gH[A] = Gm.v;
+  eH[A] = Gm.e + aflux;
+  gH[A + 1] = Gp.v;
+  eH[A + 1] = Gp.e + aflux;
+  return ok && eH[A] < 1e30f && eH[A + 1] < 1e30f;
+}
+
 // Certify that flux_limit leaves G^-, G^+ unchanged at a midpoint: the four
 // half states W_i - 2 lam (G^{HLLC,-} - F_i), W_{i+1} + 2 lam (G^{HLLC,+} -
 // F_{i+1}), W_i - 2 lam (G^- - F_i), W_{i+1} + 2 lam (G^+ - F_{i+1}) (Sec.
-// 5.2; F^alpha = 0) pass all five threshold tests.  GH / Gh: first- and
-// high-order fluxes, shared components (f < A); the alpha components of the
-// four split fluxes come separately.  l2f: 2 lam in FP32.
+// 5.2; F^alpha = 0) pass all five threshold tests.  gH / eH: the first-order
+// flux in FP32 with error bounds, laid out as hllc1_bound32 gives it; Gh:
+// the FP64 high-order flux (shared components, f < A), GmA / GpA the alpha
+// components of G^- and G^+.  l2f: 2 lam in FP32.
 template <int NDIM>
 __device__ __forceinline__ bool flux_certified(const EosConst &e, const LimTol &t, float l2f, const double *Wi,
                                                const double *Wi1, const double *Fi, const double *Fi1,
-                                               const double *GH, const double *Gh, double GHmA, double GHpA,
-                                               double GmA, double GpA) {
+                                               const float *gH, const float *eH, const double *Gh, double GmA,
+                                               double GpA) {
   constexpr int NF = NDIM + 4, A = 3 + NDIM;
 #pragma unroll
   for (int st = 0; st < 4; ++st) {
     const bool right = st & 1;  // W_{i+1} + 2 lam (.) else W_i - 2 lam (.)
+    const bool first = st < 2;
     const double *W = right ? Wi1 : Wi;
     const double *F = right ? Fi1 : Fi;
-    const double *G = st < 2 ? GH : Gh;
     const float sl = right ? l2f : -l2f;
     float x[NF], d[NF];
 #pragma unroll
     for (int f = 0; f < A; ++f) {
-      const float w = trunc32(W[f]), g = trunc32(G[f]), fl = trunc32(F[f]);
+      const float w = trunc32(W[f]), fl = trunc32(F[f]);
+      const float g = first ? gH[f] : trunc32(Gh[f]);
       x[f] = fmaf(sl, g - fl, w);
-      d[f] = cmargin(fabsf(w) + l2f * (fabsf(g) + fabsf(fl)));
+      d[f] = cmargin(fabsf(w) + l2f * (fabsf(g) + fabsf(fl))) + (first ? 1.001f * l2f * eH[f] : 0.0f);
     }
     const float wa = trunc32(W[A]);
-    const float ga = trunc32(st == 0 ? GHmA : st == 1 ? GHpA : st == 2 ? GmA : GpA);
+    const float ga = first ? gH[A + (right ? 1 : 0)] : trunc32(right ? GpA : GmA);
+    const float eg = first ? 1.001f * l2f * eH[A + (right ? 1 : 0)] : 0.0f;
     x[A] = fmaf(sl, ga, wa);
-    d[A] = cmargin(fabsf(wa) + l2f * fabsf(ga));
+    d[A] = cmargin(fabsf(wa) + l2f * fabsf(ga)) + eg;
+    // 1 - alpha from 1 - W_alpha formed in FP64 (exact for W_alpha >= 1/2),
+    // so that its bound scales with 1 - alpha, not with 1
+    const float om_w = trunc32(1.0 - W[A]);
+    const float om = fmaf(-sl, ga, om_w);
     if (!(x[0] - d[0] >= t.cert_ar && x[1] - d[1] >= t.cert_ar && x[A] - d[A] >= t.cert_a &&
-          (1.0f - x[A]) - (d[A] + cmargin(1.0f)) >= t.cert_a && rct2_cert<NDIM>(e, x, d, t.cert_rc)))
+          om - (cmargin(fabsf(om_w) + l2f * fabsf(ga)) + eg) >= t.cert_a && rct2_cert<NDIM>(e, x, d, t.cert_rc)))
       return false;
   }
   return true;
@@ -1005,7 +1143,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
   const double eps4 = 4.0 * a.eps_is;  // IS epsilon for the indicators scaled by 4
 
   // ---- 3: midpoint fluxes ---------------------------------------------------
-  int nlim_i = 0, nhard_i = 0, nlim_f = 0, nhard_f = 0;
+  int nlim_i = 0, nhard_i = 0, nlim_f = 0, nhard_f = 0, nslow = 0;
   for (int q = tid; q < T::NM; q += T::THREADS) {
     const int l = DIR == 0 ? q / T::TM : q % T::TL;
     const int m = DIR == 0 ? q % T::TM : q / T::TL;
@@ -1027,28 +1165,25 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
     for (int j = 0; j < NDIM; ++j) vi[j] = sm.vel[j * T::NN + ni];
     const double pi_ = sm.p[ni];
 
-    // First-order HLLC flux from the nodes (Sec. 3.2).
-    double GH[NF], uH;
-    {
-      double vr[NDIM];
+    double vr[NDIM];  // velocity of node i+1
 #pragma unroll
-      for (int j = 0; j < NDIM; ++j) vr[j] = sm.vel[j * T::NN + ni1];
+    for (int j = 0; j < NDIM; ++j) vr[j] = sm.vel[j * T::NN + ni1];
+    // First-order HLLC flux from the nodes (Sec. 3.2), split into G^{HLLC,-}
+    // and G^{HLLC,+}; in FP64 where it is used: the first-order scheme and
+    // the flux limiter wherever its FP32 certification fails.
+    auto first_order = [&](double *GHm, double *GHp) {
+      double GH[NF], uH;
       hllc<NDIM, DIR, double>(Wi, vi, pi_, Wi[0] + Wi[1], sm.c[ni], Wi1, vr, sm.p[ni1], Wi1[0] + Wi1[1],
                               sm.c[ni1], GH, uH);
-    }
-    double GHm[NF], GHp[NF];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) GHm[f] = GHp[f] = GH[f];
-    GHm[A] = GH[A] - Wi[A] * uH;
-    GHp[A] = GH[A] - Wi1[A] * uH;
+      for (int f = 0; f < NF; ++f) GHm[f] = GHp[f] = GH[f];
+      GHm[A] = GH[A] - Wi[A] * uH;
+      GHp[A] = GH[A] - Wi1[A] * uH;
+    };
 
     double Gm[NF], Gp[NF];
     if (a.scheme == SCHEME_HLLC1) {
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        Gm[f] = GHm[f];
-        Gp[f] = GHp[f];
-      }
+      first_order(Gm, Gp);
     } else {
       // Steps 1-2: primitive deviations from node i, projected with
       // Rinv_{i+1/2} (App. A; means of a1r1, a2r2, rho and c of nodes i, i+1).
@@ -1138,6 +1273,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
           double *W = side ? WR : WL;
           double *V = side ? VR : VL;
           if (a.tol.hs_implied && sm.nok[side ? ni1 : ni] && state_passes<NDIM>(eos, a.tol, W)) continue;
+          nslow += cnt;
           const int fl = interp_limit<NDIM>(eos, a.tol, side ? Wi1 : Wi, W);
           nlim_i += cnt * (fl & 1);
           nhard_i += cnt * (fl >> 1);
@@ -1182,7 +1318,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
       for (int f = 0; f < NF; ++f) Gm[f] = Gp[f] = Gh[f];
       Gm[A] = Gh[A] - Wi[A] * uh;
       Gp[A] = Gh[A] - Wi1[A] * uh;
-      // Flux limiter (Sec. 5.2), unless certified to leave the fluxes as they are.
+      // Flux limiter (Sec. 5.2), unless certified to leave the fluxes as they
+      // are (the first-order flux then in FP32 with error bounds only).
       if (a.scheme == SCHEME_PP) {
         double Fi[NF], Fi1[NF];
 #pragma unroll
@@ -1192,8 +1329,15 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
         }
         Fi[A] = 0.0;
         Fi1[A] = 0.0;
-        if (!(a.tol.hs_implied &&
-              flux_certified<NDIM>(eos, a.tol, l2f, Wi, Wi1, Fi, Fi1, GH, Gh, GHm[A], GHp[A], Gm[A], Gp[A]))) {
+        float gH[NF + 1], eH[NF + 1];
+        const bool cert =
+            a.tol.hs_implied &&
+            hllc1_bound32<NDIM, DIR>(Wi, vi, pi_, sm.c[ni], Wi1, vr, sm.p[ni1], sm.c[ni1], gH, eH) &&
+            flux_certified<NDIM>(eos, a.tol, l2f, Wi, Wi1, Fi, Fi1, gH, eH, Gh, Gm[A], Gp[A]);
+        if (!cert) {
+          nslow += cnt;
+          double GHm[NF], GHp[NF];
+          first_order(GHm, GHp);
           const int fl = flux_limit<NDIM>(eos, a.tol, Wi, Wi1, Fi, Fi1, GHm, GHp, lam, Gm, Gp);
           nlim_f += cnt * (fl & 1);
           nhard_f += cnt * (fl >> 1);
@@ -1210,6 +1354,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, const Geo &geo, d
   if (nhard_i) atomicAdd(&a.stats->interp_hard, (unsigned long long)nhard_i);
   if (nlim_f) atomicAdd(&a.stats->flux_limited, (unsigned long long)nlim_f);
   if (nhard_f) atomicAdd(&a.stats->flux_hard, (unsigned long long)nhard_f);
+  if (nslow) atomicAdd(&a.stats->fp64_fallbacks, (unsigned long long)nslow);
   __syncthreads();
 
   // ---- 4: cell update ------------------------------------------------------

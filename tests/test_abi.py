@@ -152,7 +152,9 @@ def test_grid_batch_and_division_check_host_rejections(lib):
     ok = (1e-10, 1e-10, 1e-8, 1.4, 4.4, 6e8)
     assert L.wcns_check_limiter_cert(0, 0, None, 0, *ok, None, None, None) == E
     assert L.wcns_check_limiter_cert(4, 0, None, 0, *ok, None, None, None) == E
-    assert L.wcns_check_limiter_cert(2, 2, None, 0, *ok, None, None, None) == E
+    assert L.wcns_check_limiter_cert(2, 3, None, 0, *ok, None, None, None) == E
+    assert L.wcns_check_limiter_cert(2, -1, None, 0, *ok, None, None, None) == E
+    assert L.wcns_check_limiter_cert(2, 2, None, 0, *ok, None, None, None) == wcns.WCNS_OK
     assert L.wcns_check_limiter_cert(2, 0, None, -1, *ok, None, None, None) == E
     assert L.wcns_check_limiter_cert(2, 1, None, 3, *ok, cert, cert, None) == E
     assert L.wcns_check_limiter_cert(2, 0, None, 0, -1e-10, *ok[1:], None, None, None) == E

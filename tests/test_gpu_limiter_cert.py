@@ -237,3 +237,95 @@ def test_flux_certification_is_sound_and_live(ndim):
     assert bad.size == 0, rows[bad[:2]]
     assert (~exact).sum() > 1000
     assert cert.sum() > 1000
+
+
+def node_data(W, ndim):
+    """Velocity, pressure and sound speed of conservative states (Sec. 2:
+    p = (rho e - Pi) / Gamma, rho c^2 = ((Gamma + 1) rho e - Pi) / Gamma^2)
+    and their physical flux along the last axis (alpha component unused)."""
+    g1, p1, g2 = EOS["gamma_l"], EOS["pinf_l"], EOS["gamma_g"]
+    r1, r2 = 1.0 / (g1 - 1.0), 1.0 / (g2 - 1.0)
+    q1 = g1 * p1 / (g1 - 1.0)
+    A, E = 3 + ndim, 2 + ndim
+    rho = W[0] + W[1]
+    v = np.stack([W[2 + j] / rho for j in range(ndim)])
+    rhoe = W[E] - 0.5 * sum(W[2 + j] * v[j] for j in range(ndim))
+    Gam = r2 + (r1 - r2) * W[A]
+    Pi = q1 * W[A]
+    p = (rhoe - Pi) / Gam
+    c = np.sqrt(np.maximum((Gam + 1.0) * rhoe - Pi, 0.0) / (Gam * Gam * rho))
+    u = v[ndim - 1]
+    F = W * u
+    F[2 + ndim - 1] += p
+    F[E] += p * u
+    F[A] = 0.0
+    return v, p, c, F
+
+
+def node_rows(rng, Wi, Wi1, ndim, cfl):
+    """Kind-2 rows: nodes i and i+1, their fluxes, a high-order flux near
+    the central one, and lambda from a CFL number per row."""
+    A = 3 + ndim
+    vi, pi, ci, Fi = node_data(Wi, ndim)
+    vr, pr, cr, Fr = node_data(Wi1, ndim)
+    n = pi.size
+    smax = np.maximum(np.abs(vi[ndim - 1]) + ci, np.abs(vr[ndim - 1]) + cr)
+    lam = cfl / np.maximum(smax, 1e-300)
+    G = 0.5 * (Fi + Fr) * (1 + rng.uniform(-1e-3, 1e-3, Fi.shape))
+    u = 0.5 * (vi[ndim - 1] + vr[ndim - 1])
+    GmA = 0.5 * (Wi1[A] - Wi[A]) * u
+    GpA = 0.5 * (Wi[A] - Wi1[A]) * u
+    parts = [Wi, vi, pi[None], ci[None], Wi1, vr, pr[None], cr[None], Fi, Fr, G, GmA[None], GpA[None], lam[None]]
+    return np.concatenate(parts).T
+
+
+@pytest.mark.parametrize("ndim", [1, 2, 3])
+def test_first_order_flux_certification_is_sound_and_live(ndim):
+    """The sweeps' route through the flux limiter from node states: the
+    first-order HLLC flux in FP32 with running error bounds (star state
+    decided only where |s*| exceeds its bound) against the FP64 flux and
+    limiter."""
+    rng = np.random.default_rng(300 + ndim)
+    nf = ndim + 4
+    # liveness: smooth neighbours at CFL numbers up to 0.45
+    pi = random_primitives(rng, 4000, ndim, pmin=1e3)
+    Wi, Wi1 = P.conservative(EOS, *pi), nearby_states(rng, pi)
+    cert, exact = check(ndim, 2, node_rows(rng, Wi, Wi1, ndim, rng.uniform(0.02, 0.45, 4000)))
+    assert np.all(exact[cert]), "certified a midpoint the FP64 limiter changes"
+    assert cert.mean() > 0.98, cert.mean()
+    rows = []
+    m = 3000
+    # unrelated neighbours (water next to air, pressure jumps of nine decades,
+    # 30 km/s) at CFL numbers up to 3: many first-order states leave G
+    for _ in range(4):
+        a, b = random_states(rng, m, ndim, extreme=True), random_states(rng, m, ndim, extreme=True)
+        rows.append(node_rows(rng, a, b, ndim, 10.0 ** rng.uniform(-2.0, 0.5, m)))
+    # mirrored neighbours: s* = 0, and within 1e-12 .. 1e-3 of it
+    for eps in (0.0, 1e-12, 1e-9, 1e-6, 1e-3):
+        pa = random_primitives(rng, m, ndim)
+        a1r1, a2r2, vel, p, a1 = pa
+        vb = [v.copy() for v in vel]
+        vb[ndim - 1] = -vel[ndim - 1] * (1 + eps * rng.uniform(-1, 1, m))
+        a = P.conservative(EOS, a1r1, a2r2, vel, p, a1)
+        b = P.conservative(EOS, a1r1, a2r2, vb, p, a1)
+        rows.append(node_rows(rng, a, b, ndim, 10.0 ** rng.uniform(-2.0, 0.5, m)))
+    # neighbours next to every threshold
+    for which in range(5):
+        for d in DELTAS:
+            a = random_states(rng, 200, ndim)
+            b = place(random_states(rng, 200, ndim), ndim, which, d)
+            rows.append(node_rows(rng, a, b, ndim, rng.uniform(0.02, 0.9, 200)))
+            rows.append(node_rows(rng, b, a, ndim, rng.uniform(0.02, 0.9, 200)))
+    spec = node_rows(rng, random_states(rng, m, ndim), random_states(rng, m, ndim), ndim, rng.uniform(0.02, 1.0, m))
+    k = rng.integers(0, m, m // 3)
+    vals = np.array([0.0, -0.0, 5e-324, 1e-40, 3e38, 1e200, np.inf, -np.inf, np.nan])
+    spec[k, rng.integers(0, spec.shape[1] - 1, k.size)] = vals[rng.integers(0, vals.size, k.size)]
+    rows.append(spec)
+    rows = np.concatenate(rows)
+    assert rows.shape[1] == 2 * (nf + ndim + 2) + 3 * nf + 3
+    with np.errstate(all="ignore"):
+        cert, exact = check(ndim, 2, rows)
+    bad = np.flatnonzero(cert & ~exact)
+    assert bad.size == 0, rows[bad[:2]]
+    assert (~exact).sum() > 1000
+    assert cert.sum() > 1000
