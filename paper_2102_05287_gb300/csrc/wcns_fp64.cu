@@ -61,7 +61,7 @@ __global__ void limiter_cert_check_kernel(int kind, const double *__restrict__ r
 #pragma unroll
       for (int f = 0; f <= NF; ++f) {
         gH[f] = trunc32(f < A ? GHm[f] : f == A ? GHm[A] : GHp[A]);
-        eH[f] = 1.9073486328125e-06f * fabsf(gH[f]);
+        eH[f] = 1.9073486328125e-06f * fabsf(gH[f]) + CTINY;
       }
       cert[i] = tol.hs_implied && flux_certified<NDIM>(eos, tol, l2f, Wi, Wi1, Fi, Fi1, gH, eH, Gm, Gm[A], Gp[A]);
       const int fl = flux_limit<NDIM>(eos, tol, Wi, Wi1, Fi, Fi1, GHm, GHp, lam, Gm, Gp);

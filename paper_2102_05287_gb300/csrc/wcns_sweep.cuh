@@ -681,16 +681,18 @@ __device__ int flux_limit(const EosConst &e, const LimTol &t, const double *Wi, 
 
 // FP32 image of an FP64 value from its high word alone (integer operations
 // only): sign, exponent and the leading 20 mantissa bits, truncated toward
-// zero, so |x - t(x)| < 2^-20 |x| and |t(x)| <= |x|.  Zero maps to 0; a
-// value below the FP32 normal range, at or above 2^128, or not finite maps
-// to a NaN, which fails every certification test.
+// zero, so |x - t(x)| < 2^-20 |x| and |t(x)| <= |x|.  A value below the
+// FP32 normal range maps to 0 (absolute error below 2^-126: the bounds below
+// add CTINY for it); a value at or above 2^128 or not finite maps to a NaN,
+// which fails every certification test.
 __device__ __forceinline__ float trunc32(double x) {
   const unsigned int hi = (unsigned int)__double2hiint(x);
   const unsigned int mag = hi & 0x7FFFFFFFu;
   // FP64 exponent field in [897, 1150] <=> FP32 exponent field in [1, 254]
   if (mag - 0x38100000u < 0x0FE00000u) return __uint_as_float((hi & 0x80000000u) | ((mag - 0x38000000u) << 3));
-  return (__double_as_longlong(x) << 1) == 0 ? 0.0f : __uint_as_float(0x7FC00000u);
+  return mag < 0x38100000u ? 0.0f : __uint_as_float(0x7FC00000u);
 }
+constexpr float CTINY = 2.350988701644575e-38f;  // 2^-125: twice trunc32's absolute error on tiny values
 
 // Error allowance 2^-18 m for a quantity of operand magnitude m: at least
 // three times the truncation error (2^-20), the FP32 roundings of the short
@@ -744,7 +746,7 @@ __device__ __forceinline__ bool state_passes(const EosConst &e, const LimTol &t,
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
     x[f] = trunc32(W[f]);
-    d[f] = cmargin(fabsf(x[f]));
+    d[f] = cmargin(fabsf(x[f])) + CTINY;
   }
   return rct2_cert<NDIM>(e, x, d, t.cert_rc) || !rct2_below<NDIM>(e, W, t.eps_rc);
 }
@@ -760,9 +762,10 @@ struct EF {
 };
 constexpr float EF_U = 2.384185791015625e-07f;  // 2^-22
 // from an FP64 value: the truncated image, within 2^-20 |x| <= 2^-19 |v|
+// (within 2^-126 for a value below the FP32 normal range)
 __device__ __forceinline__ EF ef(double x) {
   const float v = trunc32(x);
-  return {v, 1.9073486328125e-06f * fabsf(v)};
+  return {v, 1.9073486328125e-06f * fabsf(v) + CTINY};
 }
 __device__ __forceinline__ EF operator+(EF a, EF b) {
   const float v = a.v + b.v;
@@ -893,6 +896,7 @@ __device__ __forceinline__ bool flux_certified(const EosConst &e, const LimTol &
                                                const float *gH, const float *eH, const double *Gh, double GmA,
                                                double GpA) {
   constexpr int NF = NDIM + 4, A = 3 + NDIM;
+  const float tiny = CTINY * (1.0f + 2.0f * l2f);  // operands truncated to 0
 #pragma unroll
   for (int st = 0; st < 4; ++st) {
     const bool right = st & 1;  // W_{i+1} + 2 lam (.) else W_i - 2 lam (.)
@@ -906,11 +910,11 @@ __device__ __forceinline__ bool flux_certified(const EosConst &e, const LimTol &
       const float w = trunc32(W[f]), fl = trunc32(F[f]);
       const float g = first ? gH[f] : trunc32(Gh[f]);
       x[f] = fmaf(sl, g - fl, w);
-      d[f] = cmargin(fabsf(w) + l2f * (fabsf(g) + fabsf(fl))) + (first ? 1.001f * l2f * eH[f] : 0.0f);
+      d[f] = cmargin(fabsf(w) + l2f * (fabsf(g) + fabsf(fl))) + (first ? 1.001f * l2f * eH[f] : 0.0f) + tiny;
     }
     const float wa = trunc32(W[A]);
     const float ga = first ? gH[A + (right ? 1 : 0)] : trunc32(right ? GpA : GmA);
-    const float eg = first ? 1.001f * l2f * eH[A + (right ? 1 : 0)] : 0.0f;
+    const float eg = (first ? 1.001f * l2f * eH[A + (right ? 1 : 0)] : 0.0f) + tiny;
     x[A] = fmaf(sl, ga, wa);
     d[A] = cmargin(fabsf(wa) + l2f * fabsf(ga)) + eg;
     // 1 - alpha from 1 - W_alpha formed in FP64 (exact for W_alpha >= 1/2),
