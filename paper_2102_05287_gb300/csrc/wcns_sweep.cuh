@@ -40,8 +40,8 @@ namespace wcns {
 
 // ---------------------------------------------------------------------------
 // Tile shapes: TL lines x TM midpoints, THREADS threads per block.  The
-// x sweep takes rows of 128 midpoints (coalesced along x); the y/z sweeps
-// take 32 consecutive x columns per block (coalesced across lines).
+// x sweep takes whole rows of midpoints (coalesced along x); the y/z sweeps
+// take a few neighbouring x columns per block.
 // ---------------------------------------------------------------------------
 template <int TL_, int TM_, int THREADS_>
 struct TileT {
@@ -52,13 +52,16 @@ struct TileT {
   static constexpr int NN = TL * NS;     // nodes per block
   static constexpr int NM = TL * TM;     // midpoints per block
 };
-// Tile shapes (lines x midpoints, measured on GB300): x tiles 1 x 123
-// midpoints, 128 nodes for 128 threads, in 1D and 2D, 2 x 123 (256 threads)
-// in 3D; y/z tiles 8 x-columns x 59 midpoints in 2D (512 nodes, two per
-// thread, 256 threads) and 8 x 32 in 3D (296 nodes for 128 threads).
-// 128-thread blocks run two to an SM, so one block's staging and barriers
-// overlap the other's arithmetic (2D x sweep 2 %, 3D y/z sweeps 4 % faster
-// than one 256-thread block of twice the lines).
+// Tile shapes (lines x midpoints, measured on GB300), 128 threads and two
+// blocks per SM except in the 3D x sweep:
+// - x in 1D and 2D: 1 x 123 midpoints, 128 nodes, one per thread;
+// - y in 2D: 2 x-columns x 64 midpoints, one midpoint per thread (8 % faster
+//   than 8 x 59 at 256 threads; the column loads are uncoalesced, but the
+//   neighbouring columns' blocks find the sectors in L2);
+// - y/z in 3D: 4 x 32 (1 % faster than 8 x 32, 4 % faster than 2 x 64);
+// - x in 3D: 2 x 123 at 256 threads, or 3 x 80 (below).
+// Two 128-thread blocks per SM overlap one block's staging and barriers
+// with the other's arithmetic.
 #ifndef FP64_TM_X
 #define FP64_TM_X 123
 #endif
@@ -69,9 +72,9 @@ struct TileT {
 #define FP64_3D_TM_X FP64_TM_X
 #endif
 template <int NDIM, int DIR>
-using Tile = TileT<(DIR == 0) ? (NDIM == 3 ? FP64_3D_TL_X : 1) : 8,
-                   (DIR == 0) ? (NDIM == 3 ? FP64_3D_TM_X : FP64_TM_X) : (NDIM == 2 ? 59 : 32),
-                   (DIR == 0) ? (NDIM == 3 ? 256 : 128) : (NDIM == 2 ? 256 : 128)>;
+using Tile = TileT<(DIR == 0) ? (NDIM == 3 ? FP64_3D_TL_X : 1) : (NDIM == 2 ? 2 : 4),
+                   (DIR == 0) ? (NDIM == 3 ? FP64_3D_TM_X : FP64_TM_X) : (NDIM == 2 ? 64 : 32),
+                   (DIR == 0 && NDIM == 3) ? 256 : 128>;
 
 // Integer tests on FP64 values (no FP64-pipe compare): finite, and
 // finite-and-nonnegative (-0 counts as nonnegative, NaN and infinities

@@ -136,6 +136,8 @@ def test_rhs_1d_dirichlet_and_limiter_counts():
 @pytest.mark.parametrize("n,bcs", [
     ((150, 40), (("transmissive", "transmissive"), ("symmetry", "transmissive"))),
     ((64, 33), (("periodic", "periodic"), ("periodic", "periodic"))),
+    # several y tiles of 63 cells and a ragged tail
+    ((40, 150), (("symmetry", "transmissive"), ("transmissive", "symmetry"))),
 ])
 @pytest.mark.parametrize("scheme", ["pp-wcns-is", "hllc1"])
 def test_rhs_2d_fp64(n, bcs, scheme):
