@@ -59,22 +59,17 @@ struct TileT {
 //   than 8 x 59 at 256 threads; the column loads are uncoalesced, but the
 //   neighbouring columns' blocks find the sectors in L2);
 // - y/z in 3D: 4 x 32 (1 % faster than 8 x 32, 4 % faster than 2 x 64);
-// - x in 3D: 2 x 123 at 256 threads, or 3 x 80 (below).
+// - x in 3D: 2 x 59 (128 nodes; 4 % faster on the 384^3 bubble collapse than
+//   3 x 80 at 256 threads, whose 79-cell tiles fit 384-cell rows better,
+//   and 3 % faster than 1 x 123).
 // Two 128-thread blocks per SM overlap one block's staging and barriers
 // with the other's arithmetic.
 #ifndef FP64_TM_X
 #define FP64_TM_X 123
 #endif
-#ifndef FP64_3D_TL_X
-#define FP64_3D_TL_X 2
-#endif
-#ifndef FP64_3D_TM_X
-#define FP64_3D_TM_X FP64_TM_X
-#endif
 template <int NDIM, int DIR>
-using Tile = TileT<(DIR == 0) ? (NDIM == 3 ? FP64_3D_TL_X : 1) : (NDIM == 2 ? 2 : 4),
-                   (DIR == 0) ? (NDIM == 3 ? FP64_3D_TM_X : FP64_TM_X) : (NDIM == 2 ? 64 : 32),
-                   (DIR == 0 && NDIM == 3) ? 256 : 128>;
+using Tile = TileT<(DIR == 0) ? (NDIM == 3 ? 2 : 1) : (NDIM == 2 ? 2 : 4),
+                   (DIR == 0) ? (NDIM == 3 ? 59 : FP64_TM_X) : (NDIM == 2 ? 64 : 32), 128>;
 
 // Integer tests on FP64 values (no FP64-pipe compare): finite, and
 // finite-and-nonnegative (-0 counts as nonnegative, NaN and infinities
@@ -1492,23 +1487,13 @@ cudaError_t launch_sweep_t(const SweepArgs &a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// The 3D x sweep has two tiles: 2 x 123 (Tile<3, 0>) and 3 x 80 (255
-// nodes); each grid takes the one that needs fewer blocks, i.e. that
-// covers its rows with the least idle tile length (a 384-cell row takes
-// five 79-cell tiles, 97 % used, against four 122-cell ones, 79 %: 5 %
-// faster per x sweep on the 384^3 bubble collapse).
-using Tile3X3 = TileT<3, 80, 256>;
-
 template <class R>
 cudaError_t launch_sweep_any(int ndim, int dir, const SweepArgs &a, cudaStream_t s) {
   switch (ndim * 4 + dir) {
     case 4: return launch_sweep_t<1, 0, R>(a, s);
     case 8: return launch_sweep_t<2, 0, R>(a, s);
     case 9: return launch_sweep_t<2, 1, R>(a, s);
-    case 12:
-      if (grid_blocks<Tile3X3>(sweep_grid<0, Tile3X3>(a)) < grid_blocks<Tile<3, 0>>(sweep_grid<0, Tile<3, 0>>(a)))
-        return launch_sweep_t<3, 0, R, Tile3X3>(a, s);
-      return launch_sweep_t<3, 0, R>(a, s);
+    case 12: return launch_sweep_t<3, 0, R>(a, s);
     case 13: return launch_sweep_t<3, 1, R>(a, s);
     case 14: return launch_sweep_t<3, 2, R>(a, s);
     default: return cudaErrorInvalidValue;

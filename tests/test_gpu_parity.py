@@ -155,8 +155,9 @@ def test_rhs_2d_fp64(n, bcs, scheme):
 
 @pytest.mark.parametrize("n", [(20, 18, 17), (100, 4, 6)])
 def test_rhs_3d_fp64(n):
-    """The x sweep has two tiles, chosen per grid by block count: 3 x 80 for
-    (20, 18, 17), 2 x 123 for rows of 100 cells."""
+    """x tiles of 2 rows x 58 cells: one partial tile for (20, 18, 17), two
+    tiles (58 + 42 cells) for rows of 100 cells; y/z tiles of 4 lines x 31
+    cells."""
     bcs = (("transmissive", "transmissive"), ("periodic", "periodic"), ("symmetry", "transmissive"))
     W = P.random_admissible(n, seed=14)
     o, s = pair(n, bcs)
