@@ -10,11 +10,7 @@ cudaError_t launch_sweep_mixed(int ndim, int dir, const SweepArgs &a, cudaStream
     case 4: return launch_sweep_mixed_t<1, 0>(a, s);
     case 8: return launch_sweep_mixed_t<2, 0>(a, s);
     case 9: return launch_sweep_mixed_t<2, 1>(a, s);
-    case 12:
-      if (grid_blocks<TileMixed3X3>(sweep_grid<0, TileMixed3X3>(a)) <
-          grid_blocks<TileMixed<3, 0>>(sweep_grid<0, TileMixed<3, 0>>(a)))
-        return launch_sweep_mixed_t<3, 0, TileMixed3X3>(a, s);
-      return launch_sweep_mixed_t<3, 0>(a, s);
+    case 12: return launch_sweep_mixed_t<3, 0>(a, s);
     case 13: return launch_sweep_mixed_t<3, 1>(a, s);
     case 14: return launch_sweep_mixed_t<3, 2>(a, s);
     default: return cudaErrorInvalidValue;

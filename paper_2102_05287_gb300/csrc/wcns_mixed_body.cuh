@@ -28,7 +28,8 @@ namespace wcns {
 
 // Resident blocks per SM the register allocation targets: 3 in 2D (256
 // threads, 80 registers; three 2D tiles fit in shared memory), 3 in 3D (192
-// threads, 96 registers), 2 in 1D (128 threads).
+// threads, 96 registers; 5 for the 128-thread x tiles), 2 in 1D (128
+// threads).
 #ifndef MIXED_MIN_BLOCKS
 #define MIXED_MIN_BLOCKS 2
 #endif
@@ -64,18 +65,13 @@ using TileMixed2 = TileT<(DIR == 0) ? (NDIM == 1 ? 1 : MIXED_TL_X) : MIXED_TL_Y,
                          (DIR == 0) ? (NDIM == 1 ? MIXED_TM_1D : MIXED_TM_X) : MIXED_TM_Y,
                          (DIR == 0) ? (NDIM == 1 ? 128 : 256) : 256>;
 // 3D tiles (seven fields a node, 232 bytes of shared memory per node) have
-// their own shape: 192 threads, x tiles 2 x 91 (192 nodes), y/z tiles
-// 8 x 24 (192 midpoints), 57 / 67 KB, so that three blocks fit an SM
-// (measured on the 3D bubble collapse: 10 % faster than 256-thread tiles
-// at two blocks per SM).
+// their own shape: y/z tiles 8 x 24 (192 midpoints) with 192 threads, 67 KB,
+// three blocks per SM (measured on the 3D bubble collapse: 10 % faster than
+// 256-thread tiles at two blocks per SM); x tiles 2 x 59 (128 nodes) with
+// 128 threads, five blocks per SM (4 % faster there than 3 x 59 or 2 x 91
+// at 192 threads; 2 x 59 y/z tiles measured 30 % slower).
 #ifndef MIXED3_THREADS
 #define MIXED3_THREADS 192
-#endif
-#ifndef MIXED3_TL_X
-#define MIXED3_TL_X 2
-#endif
-#ifndef MIXED3_TM_X
-#define MIXED3_TM_X (MIXED3_THREADS / MIXED3_TL_X - 5)
 #endif
 #ifndef MIXED3_TL_Y
 #define MIXED3_TL_Y 8
@@ -86,7 +82,7 @@ using TileMixed2 = TileT<(DIR == 0) ? (NDIM == 1 ? 1 : MIXED_TL_X) : MIXED_TL_Y,
 template <int NDIM, int DIR>
 using TileMixed = typename std::conditional<
     NDIM == 3,
-    TileT<DIR == 0 ? MIXED3_TL_X : MIXED3_TL_Y, DIR == 0 ? MIXED3_TM_X : MIXED3_TM_Y, MIXED3_THREADS>,
+    typename std::conditional<DIR == 0, TileT<2, 59, 128>, TileT<MIXED3_TL_Y, MIXED3_TM_Y, MIXED3_THREADS>>::type,
     TileMixed2<NDIM, DIR>>::type;
 
 // value = hi + lo: hi keeps the leading 24 bits of the double (truncated),
@@ -997,7 +993,9 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
 
 template <int NDIM, int DIR, class T>
 __global__ void __launch_bounds__(T::THREADS,
-                                  NDIM == 2 ? MIXED_MIN_BLOCKS_2D : (NDIM == 3 ? MIXED_MIN_BLOCKS_3D : MIXED_MIN_BLOCKS))
+                                  NDIM == 2 ? MIXED_MIN_BLOCKS_2D
+                                            : (NDIM == 3 ? (T::THREADS <= 128 ? 5 : MIXED_MIN_BLOCKS_3D)
+                                                         : MIXED_MIN_BLOCKS))
     sweep_kernel_mixed(const SweepArgs a) {
   extern __shared__ double smem_raw[];
   if (!a.ctl->active) return;
@@ -1021,10 +1019,5 @@ cudaError_t launch_sweep_mixed_t(const SweepArgs &a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// The mixed 3D x sweep's second tile: 3 x 59 (192 nodes, like the 2 x 91
-// default); each grid takes the one that needs fewer blocks (on the
-// 384^3 bubble collapse seven 58-cell tiles cover a row 95 %, against five
-// 90-cell ones 85 %: 9 % faster per x sweep).
-using TileMixed3X3 = TileT<3, MIXED3_THREADS / 3 - 5, MIXED3_THREADS>;
 
 }  // namespace wcns

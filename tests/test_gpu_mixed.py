@@ -98,8 +98,8 @@ CASES = [
     ((40, 36), (("dirichlet", "transmissive"), ("dirichlet", "symmetry"))),
     ((16, 14, 12), (("periodic", "periodic"), ("symmetry", "dirichlet"), ("transmissive", "symmetry"))),
     ((14, 13, 15), (("dirichlet", "symmetry"), ("transmissive", "transmissive"), ("periodic", "periodic"))),
-    # rows of 100 cells: the x sweep takes its 2 x 91 tile here (the 3 x 59
-    # tile needs as many blocks), while the small grids above take 3 x 59
+    # rows of 100 cells: two x tiles of 58 cells (58 + 42), while the small
+    # grids above fit one
     ((100, 4, 6), (("transmissive", "symmetry"), ("periodic", "periodic"), ("transmissive", "transmissive"))),
 ]
 
