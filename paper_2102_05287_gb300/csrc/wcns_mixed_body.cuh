@@ -41,10 +41,12 @@ namespace wcns {
 #endif
 
 // Tile shapes (lines x midpoints): x sweeps 2 x 123 with 256 threads,
-// 1D 1 x 123 with 128 threads and y/z sweeps 8 x 27 (x-columns x
+// 1D 1 x 123 with 128 threads and 2D y sweeps 4 x 59 (x-columns x
 // midpoints) with 256 threads, so that the node stage (midpoints + 5 nodes
-// a line) is exactly one node per thread (8 x 27 measured 1.6 % faster per
-// step than 8 x 32, whose 296 nodes take two rounds for 40 threads).
+// a line) is exactly one node per thread.  4 x 59 has 8 % halo nodes
+// against 19 % for 8 x 27 and measured 3 % faster per y sweep (2 x 123:
+// 3 % slower; 8 x 32, whose 296 nodes take two rounds: 1.6 % slower per
+// step than 8 x 27).
 #ifndef MIXED_TL_X
 #define MIXED_TL_X 2
 #endif
@@ -55,7 +57,7 @@ namespace wcns {
 #define MIXED_TM_1D 123
 #endif
 #ifndef MIXED_TL_Y
-#define MIXED_TL_Y 8
+#define MIXED_TL_Y 4
 #endif
 #ifndef MIXED_TM_Y
 #define MIXED_TM_Y (256 / MIXED_TL_Y - 5)

@@ -96,6 +96,8 @@ CASES = [
     ((48, 40), (("periodic", "periodic"), ("symmetry", "transmissive"))),
     ((45, 38), (("symmetry", "dirichlet"), ("periodic", "periodic"))),
     ((40, 36), (("dirichlet", "transmissive"), ("dirichlet", "symmetry"))),
+    # several y tiles of 58 cells and a ragged tail
+    ((30, 130), (("transmissive", "symmetry"), ("symmetry", "transmissive"))),
     ((16, 14, 12), (("periodic", "periodic"), ("symmetry", "dirichlet"), ("transmissive", "symmetry"))),
     ((14, 13, 15), (("dirichlet", "symmetry"), ("transmissive", "transmissive"), ("periodic", "periodic"))),
     # rows of 100 cells: two x tiles of 58 cells (58 + 42), while the small
