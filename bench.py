@@ -301,23 +301,36 @@ def _cfl_dt(sm, pr):
 def run_reference(args, world, rank):
     if rank != 0:
         return
+    import numpy as np
     from oracle import Oracle
     from paper_2102_05287_gb300 import problems as P
     pr = P.shock_bubble_2d(args.nx, args.ny, seed=SEED)
-    o = Oracle(pr.n, pr.lo, pr.hi, pr.bcs, **pr.eos)
-    W = pr.W
-    for _ in range(min(args.warmup, 1)):
-        o.rhs(W, 1e-9)
-    # each timed step is one SSPRK3 step of the full workload (3 RHS)
-    steps = max(1, min(args.steps, 3))
+    # each step is a bounded sample of the workload: one SSPRK3 step of its
+    # lowest eighth of rows (the strip along the symmetry plane, with the
+    # workload's initial state and boundary conditions), so that all of
+    # --warmup W and --steps K run in well under a minute a step
+    rows = max(1, pr.n[1] // 8)
+    hi = (pr.hi[0], pr.lo[1] + (pr.hi[1] - pr.lo[1]) * rows / pr.n[1])
+    o = Oracle((pr.n[0], rows), pr.lo, hi, pr.bcs, **pr.eos)
+    W = np.ascontiguousarray(pr.W[:, :rows, :])
+    ncell = pr.n[0] * rows
+
+    def step(W):
+        sm = o.max_wavespeed(W)
+        dt = 0.5 / (sm[0] * pr.n[0] / (hi[0] - pr.lo[0]) + sm[1] * rows / (hi[1] - pr.lo[1]))
+        return o.rk3_step(W, dt)
+
+    for _ in range(args.warmup):
+        W = step(W)
+    steps = args.steps
     t0 = time.perf_counter()
     for _ in range(steps):
-        W = o.rk3_step(W, _cfl_dt(o.max_wavespeed(W), pr))
+        W = step(W)
     el = time.perf_counter() - t0
-    value = 3 * pr.ncells * steps / el
+    value = 3 * ncell * steps / el
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": steps, "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * el / steps,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD if (args.nx, args.ny) == (2048, 1024) else
@@ -326,8 +339,9 @@ def run_reference(args, world, rank):
                    "step": "one SSPRK3 step (3 RHS evaluations)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(),
                          "kind": "oracle",
-                         "sample": "%d SSPRK3 steps of the full %dx%d workload, single thread" %
-                                   (steps, pr.n[0], pr.n[1])},
+                         "sample": "%d SSPRK3 steps, each of a %dx%d strip of the %dx%d workload (its "
+                                   "lowest eighth of rows, initial state and boundary conditions), single "
+                                   "thread" % (steps, pr.n[0], rows, pr.n[0], pr.n[1])},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
