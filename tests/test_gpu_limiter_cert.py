@@ -329,3 +329,35 @@ def test_first_order_flux_certification_is_sound_and_live(ndim):
     assert bad.size == 0, rows[bad[:2]]
     assert (~exact).sum() > 1000
     assert cert.sum() > 1000
+
+
+@pytest.mark.parametrize("name,make,steps", [
+    ("shock_bubble_2d", lambda: P.shock_bubble_2d(256, 128, seed=2), 20),
+    ("bubble_collapse_3d", lambda: P.bubble_collapse_3d(32), 5),
+])
+def test_fp64_sweeps_certify_smooth_and_still_flow(name, make, steps):
+    """In the sweeps themselves: on the bubble workloads (still liquid at
+    alpha1 = 1 - 1e-6, decayed velocities, smooth flow) no limiter needs its
+    FP64 path (`fp64_fallbacks` counts the limiters that ran in FP64), so
+    the certification is what the FP64 sweeps run there."""
+    pr = make()
+    s = wcns.Solver(pr.n, pr.lo, pr.hi, pr.bcs, precision="fp64", **pr.eos)
+    W = torch.from_numpy(pr.W).cuda()
+    s.advance_steps(W, steps, cfl=0.5)
+    st = s.stats()
+    assert st["midpoints"] > 0 and st["nonfinite"] == 0 and st["inadmissible"] == 0, st
+    assert st["fp64_fallbacks"] == 0, st
+    s.close()
+
+
+def test_fp64_fallbacks_stay_rare_where_limiters_fire():
+    """On the Mach 10 water cylinder the limiters fire, and the FP64 path
+    runs only near them: well under 1 % of the midpoints."""
+    pr = P.mach10_water_cylinder(288, 192)
+    s = wcns.Solver(pr.n, pr.lo, pr.hi, pr.bcs, precision="fp64", **pr.eos)
+    W = torch.from_numpy(pr.W).cuda()
+    s.advance_steps(W, 100, cfl=0.5)
+    st = s.stats()
+    assert st["flux_limited"] > 0, st
+    assert 0 < st["fp64_fallbacks"] < 0.01 * st["midpoints"], st
+    s.close()
