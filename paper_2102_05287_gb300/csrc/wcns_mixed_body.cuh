@@ -26,15 +26,19 @@
 
 namespace wcns {
 
-// Resident blocks per SM the register allocation targets: 3 in 2D (256
-// threads, 80 registers; three 2D tiles fit in shared memory), 3 in 3D (192
-// threads, 96 registers; 5 for the 128-thread x tiles), 2 in 1D (128
-// threads).
+// Resident blocks per SM the register allocation targets: 4 in 2D (256
+// threads, 64 registers), 3 in 3D (192 threads, 96 registers) and 8 for the
+// 3D 128-thread x tiles (64 registers), 2 in 1D (128 threads).  Shared
+// memory holds three 2D tiles and six 3D x tiles per SM, so the 2D and the
+// 3D x budgets are tighter than the residency needs: measured, the 64-
+// register builds run faster than 80 (2D: 3 % per sweep) or 96 registers
+// (3D x: 10 %) despite their spills; 48 registers (2D) and 51 (3D x) run
+// slower again.
 #ifndef MIXED_MIN_BLOCKS
 #define MIXED_MIN_BLOCKS 2
 #endif
 #ifndef MIXED_MIN_BLOCKS_2D
-#define MIXED_MIN_BLOCKS_2D 3
+#define MIXED_MIN_BLOCKS_2D 4
 #endif
 #ifndef MIXED_MIN_BLOCKS_3D
 #define MIXED_MIN_BLOCKS_3D 3
@@ -70,7 +74,7 @@ using TileMixed2 = TileT<(DIR == 0) ? (NDIM == 1 ? 1 : MIXED_TL_X) : MIXED_TL_Y,
 // their own shape: y/z tiles 8 x 24 (192 midpoints) with 192 threads, 67 KB,
 // three blocks per SM (measured on the 3D bubble collapse: 10 % faster than
 // 256-thread tiles at two blocks per SM); x tiles 2 x 59 (128 nodes) with
-// 128 threads, five blocks per SM (4 % faster there than 3 x 59 or 2 x 91
+// 128 threads, six blocks per SM (4 % faster there than 3 x 59 or 2 x 91
 // at 192 threads; 2 x 59 y/z tiles measured 30 % slower).
 #ifndef MIXED3_THREADS
 #define MIXED3_THREADS 192
@@ -996,7 +1000,7 @@ __device__ __forceinline__ void sweep_body_mixed(const SweepArgs &a, const Geo &
 template <int NDIM, int DIR, class T>
 __global__ void __launch_bounds__(T::THREADS,
                                   NDIM == 2 ? MIXED_MIN_BLOCKS_2D
-                                            : (NDIM == 3 ? (T::THREADS <= 128 ? 5 : MIXED_MIN_BLOCKS_3D)
+                                            : (NDIM == 3 ? (T::THREADS <= 128 ? 8 : MIXED_MIN_BLOCKS_3D)
                                                          : MIXED_MIN_BLOCKS))
     sweep_kernel_mixed(const SweepArgs a) {
   extern __shared__ double smem_raw[];
