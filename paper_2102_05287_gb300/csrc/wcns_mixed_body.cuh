@@ -29,11 +29,12 @@ namespace wcns {
 // Resident blocks per SM the register allocation targets: 4 in 2D (256
 // threads, 64 registers), 3 in 3D (192 threads, 96 registers) and 8 for the
 // 3D 128-thread x tiles (64 registers), 2 in 1D (128 threads).  Shared
-// memory holds three 2D tiles and six 3D x tiles per SM, so the 2D and the
-// 3D x budgets are tighter than the residency needs: measured, the 64-
-// register builds run faster than 80 (2D: 3 % per sweep) or 96 registers
-// (3D x: 10 %) despite their spills; 48 registers (2D) and 51 (3D x) run
-// slower again.
+// memory holds three 2D tiles and six 3D x tiles per SM.  In 2D the 64-
+// register build keeps the same three blocks and still runs 3 % faster per
+// sweep than 80 registers, despite its spills; the 3D x tiles at 64
+// registers reach the six blocks that shared memory allows (five at 96
+// registers), 10 % faster.  48 registers (2D) and 51 (3D x) run slower
+// again.
 #ifndef MIXED_MIN_BLOCKS
 #define MIXED_MIN_BLOCKS 2
 #endif
